@@ -1,0 +1,238 @@
+/*
+ * vmc.h - C ABI of the GB300 many-variable VMC hot path.
+ *
+ * The library samples a Gutzwiller-Jastrow projected anti-parallel Pfaffian
+ * wave function  psi(x) = P_G P_J <x|phi_AP-Pf>  (mVMC paper, Sec. 2.2:
+ * Eqs. Pf, AP-Pf and the correlation factors of Sec. 2.2.3) with many
+ * Metropolis walkers (Sec. 2.1.1-2.1.2), measures the local energy and the
+ * log-derivatives O_k (Eq. MC, Sec. 2.3.1), and performs stochastic
+ * reconfiguration steps (Eq. SR_equation_system, Sec. 2.3.2, Algorithm 1).
+ * One GPU; every numerical step runs in the library's own CUDA kernels.
+ *
+ * Conventions
+ *  - Sites i = 0..Ns-1; electrons: Ne = 2N with S^z = 0; ele[n] (n < N) is
+ *    the site of up electron n, ele[N+m] the site of down electron m.
+ *    Labels are kept through every move.
+ *  - Hamiltonian (Sec. 2.1, Eq. GHam and the Hubbard / Spin models):
+ *      H = sum_k -t_k c^dag_{i_k s} c_{j_k s}  (each directed term, both spins)
+ *        + sum_i U_i n_i,up n_i,dn + sum_k V_k n_{i_k} n_{j_k}
+ *        + sum_k J_k S_{i_k} . S_{j_k}.
+ *  - Parameters: one real vector [g (n_g) | v (n_v) | f (n_f)]:
+ *      g_i  = p[g_idx[i]]                (0 where g_idx = -1)
+ *      v_ij = p[n_g + v_idx[i*Ns+j]]     (v_idx symmetric, -1 = absent)
+ *      f_ij = f_sign[i*Ns+j] * p[n_g + n_v + f_idx[i*Ns+j]]
+ *    (sublattice classes and anti-periodic signs, Sec. 2.2.1 and App. A).
+ *  - Ownership: every pointer argument is a HOST pointer owned by the caller
+ *    and only read (or written, for outputs) during the call; the library
+ *    copies what it keeps.  Device memory is allocated by the library in
+ *    vmc_create and released by vmc_destroy.
+ *  - Every call returns VMC_OK (0) or a negative error code; on error the
+ *    context is left as it was before the call, except after VMC_ECUDA
+ *    (the CUDA context may be unusable) and VMC_ENUMERIC / VMC_ESINGULAR
+ *    from vmc_sample (the affected walkers are flagged, see vmc_measure).
+ *  - Calls on one context are not thread-safe; all work is ordered on the
+ *    stream given in vmc_opts.
+ */
+#ifndef VMC_H
+#define VMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  VMC_OK = 0,
+  VMC_EINVAL = -1,     /* bad argument or size */
+  VMC_ENOMEM = -2,     /* device or host allocation failed */
+  VMC_ECUDA = -3,      /* a CUDA call failed */
+  VMC_ESINGULAR = -4,  /* an initial configuration has Pf(X) = 0 */
+  VMC_ENUMERIC = -5,   /* NaN/Inf or a vanishing ratio denominator */
+  VMC_ETIMEOUT = -6,   /* a bounded device wait expired */
+  VMC_ESTATE = -7      /* call not valid in the current state */
+};
+
+enum { VMC_FP64 = 0, VMC_MIXED = 1 };
+enum { VMC_SOLVE_CHOLESKY = 0, VMC_SOLVE_CG = 1 };
+
+typedef struct vmc_ctx vmc_ctx;
+
+/* Lattice and Hamiltonian of one system (host arrays, copied). */
+typedef struct {
+  int32_t Ns;
+  int32_t n_hop;                 /* directed hopping terms -t c^dag_i c_j */
+  const int32_t *hop_i, *hop_j;
+  const double *hop_t;
+  const double *U;               /* [Ns] on-site U_i (may be NULL = 0) */
+  int32_t n_V;                   /* off-site V n_i n_j terms */
+  const int32_t *V_i, *V_j;
+  const double *V_val;
+  int32_t n_J;                   /* Heisenberg bonds J S_i.S_j, each once */
+  const int32_t *J_i, *J_j;
+  const double *J_val;
+  int32_t local_spin;            /* 1: no doublons (g -> -inf), exchange moves only */
+} vmc_model;
+
+/* Variational-parameter layout of one system (host arrays, copied). */
+typedef struct {
+  int32_t n_g, n_v, n_f;
+  const int32_t *g_idx;          /* [Ns] */
+  const int32_t *v_idx;          /* [Ns*Ns], symmetric, diagonal -1 */
+  const int32_t *f_idx;          /* [Ns*Ns] */
+  const int8_t *f_sign;          /* [Ns*Ns], +1 / -1 */
+} vmc_layout;
+
+typedef struct {
+  int32_t n_walkers;             /* walkers per system (>= 1) */
+  uint64_t seed;                 /* Philox4x32-10 key */
+  int32_t precision;             /* VMC_FP64 or VMC_MIXED */
+  int32_t delay_k;               /* mixed: delayed-update depth (0 = default) */
+  int32_t recompute_every;       /* FP64 from-scratch inverse inside the sweep once a
+                                    walker has this many accepted moves since the
+                                    last one; 0 = default (mixed: 64, FP64: never),
+                                    -1 = never */
+  int32_t max_samples;           /* sample rows kept per walker (>= 1) */
+  void *stream;                  /* cudaStream_t; NULL = default stream */
+} vmc_opts;
+
+typedef struct {
+  double energy;                 /* mean local energy over the stored samples */
+  double variance;               /* sample variance of E_loc */
+  double stderr_walkers;         /* standard error from per-walker means */
+  double acceptance;             /* accepted / proposals, cumulative */
+  int64_t n_proposals, n_accepted;
+  int32_t n_samples;             /* stored rows (walkers x samples) */
+  int32_t n_flagged;             /* walkers with a numerical fault */
+  double max_drift;              /* max |Minv_updated - Minv_fresh| / max |Minv_fresh|
+                                    seen at the in-sweep FP64 recomputes */
+  int64_t n_hop_tested;          /* valid hop proposals whose ratio was computed */
+  int64_t n_exchange_tested;     /* valid exchange proposals whose ratio was computed */
+  int64_t n_hop_accepted;
+  int64_t n_exchange_accepted;
+  int64_t n_recomputes;          /* in-sweep FP64 from-scratch inverses */
+  int64_t n_measured_hops;       /* hop ratios evaluated for E_loc */
+  int64_t n_measured_exchanges;  /* exchange ratios evaluated for E_loc */
+  int64_t n_measurements;        /* E_loc / O_k rows measured */
+} vmc_stats;
+
+typedef struct {
+  double dtau;                   /* Delta tau of Eq. SR_equation_system */
+  double shift_rel;              /* S~_kk = S_kk (1 + shift_rel) + shift_abs */
+  double shift_abs;
+  int32_t solver;                /* VMC_SOLVE_CHOLESKY or VMC_SOLVE_CG */
+  double cg_eps;                 /* Algorithm 1: stop when |r|^2 < eps^2 |b|^2 */
+  int32_t cg_kmax;               /* Algorithm 1: iteration limit */
+} vmc_sr_opts;
+
+typedef struct {
+  double energy;                 /* <H> of the samples used */
+  double norm_g;                 /* |g|_2 */
+  double norm_dalpha;            /* |Delta alpha|_2 */
+  int32_t cg_iters;              /* iterations used (CG), 0 for Cholesky */
+  int32_t n_params;
+} vmc_sr_report;
+
+/* Create a context for one system (Sec. 2.1-2.2 problem statement).
+ * params: initial parameter vector [n_g + n_v + n_f].  p_exchange: the
+ * probability that a proposal is an exchange (Sec. 2.1.2); forced to 1 when
+ * local_spin.  Walker configurations start from a seeded random placement;
+ * vmc_set_configs replaces them.
+ * Errors: VMC_EINVAL (sizes, Ne odd, Ne/2 > 128, Ns > 4096, index out of
+ * range), VMC_ENOMEM, VMC_ECUDA. */
+int vmc_create(vmc_ctx **out, const vmc_model *model, int32_t Ne,
+               const vmc_layout *layout, const double *params,
+               double p_exchange, const vmc_opts *opts);
+
+/* Batched form: n_systems independent systems (uneven sizes allowed) sampled
+ * by one persistent launch.  Arrays are indexed by system. */
+int vmc_create_batch(vmc_ctx **out, int32_t n_systems, const vmc_model *models,
+                     const int32_t *Ne, const vmc_layout *layouts,
+                     const double *const *params, const double *p_exchange,
+                     const vmc_opts *opts);
+
+void vmc_destroy(vmc_ctx *ctx);
+const char *vmc_strerror(int code);
+
+/* Replace the walkers' configurations of one system: ele [n_walkers*Ne]
+ * (label order, see above), counters [n_walkers] Philox proposal counters
+ * (NULL = keep).  Inverses are rebuilt from scratch (FP64) on the next
+ * vmc_sample.  Errors: VMC_EINVAL (out-of-range or doubly occupied spin
+ * orbital; doublon under local_spin). */
+int vmc_set_configs(vmc_ctx *ctx, int32_t system, const int32_t *ele,
+                    const uint64_t *counters);
+int vmc_get_configs(vmc_ctx *ctx, int32_t system, int32_t *ele,
+                    uint64_t *counters);
+
+/* Markov chains (Sec. 2.1.1-2.1.2): every walker makes n_warmup sweeps,
+ * then n_samples times (sweeps_between sweeps, then a measurement of E_loc
+ * and the O_k row).  One sweep = Ne proposals.  Replaces the stored
+ * samples (n_samples <= max_samples).  Errors: VMC_EINVAL, VMC_ESINGULAR
+ * (a walker's X is singular), VMC_ENUMERIC, VMC_ECUDA. */
+int vmc_sample(vmc_ctx *ctx, int32_t n_warmup, int32_t n_samples,
+               int32_t sweeps_between);
+
+/* Statistics of the stored samples of one system (Eq. MC) and counters. */
+int vmc_measure(vmc_ctx *ctx, int32_t system, vmc_stats *out);
+
+/* Copy the stored samples of one system to host buffers: E [rows],
+ * O [rows * Np] row-major, row = walker * n_samples + sample.  Either
+ * pointer may be NULL. */
+int vmc_get_samples(vmc_ctx *ctx, int32_t system, double *E, double *O);
+
+/* Replace the stored samples of one system with caller data (rows x Np,
+ * row-major); rows <= n_walkers * max_samples.  vmc_sr_step then uses them. */
+int vmc_set_samples(vmc_ctx *ctx, int32_t system, int32_t rows,
+                    const double *E, const double *O);
+
+/* One SR step on the stored samples of one system (Sec. 2.3.1-2.3.2):
+ * S_km = <O_k O_m> - <O_k><O_m>, g_m = <E O_m> - <E><O_m>,
+ * S~ = S with diagonal shift, solve S~ x = g by Cholesky (S~ = L L^T) or by
+ * CG with the SR-CG product (Algorithm 1), alpha += -dtau x.  Walker
+ * inverses are rebuilt on the next vmc_sample.  Errors: VMC_EINVAL,
+ * VMC_ESTATE (no samples), VMC_ESINGULAR (S~ not positive definite),
+ * VMC_ENUMERIC (CG breakdown), VMC_ECUDA. */
+int vmc_sr_step(vmc_ctx *ctx, int32_t system, const vmc_sr_opts *opts,
+                vmc_sr_report *report);
+
+/* S~ (Np x Np, row-major, FP64) and g (Np) of the stored samples, as built
+ * by vmc_sr_step's dense path (for checks).  Either pointer may be NULL. */
+int vmc_get_sr_matrices(vmc_ctx *ctx, int32_t system, double shift_rel,
+                        double shift_abs, double *S, double *g);
+
+int vmc_get_params(vmc_ctx *ctx, int32_t system, double *params);
+int vmc_set_params(vmc_ctx *ctx, int32_t system, const double *params);
+int vmc_num_params(vmc_ctx *ctx, int32_t system);
+
+/* Pfaffian-ratio check hook (Sec. 2.1.2 fast update): for walker w of a
+ * system, psi(x')/psi(x) of n_moves candidate moves of its current
+ * configuration, each moves[3k..3k+2] = {kind, a, b}: kind 0 = hop of
+ * electron a to site b; kind 1 = exchange of up electron a with down
+ * electron b.  Invalid moves give 0.  Uses the same device routines as the
+ * sampler, on the walker's current inverse.  ratios: host [n_moves]. */
+int vmc_eval_ratios(vmc_ctx *ctx, int32_t system, int32_t walker,
+                    int32_t n_moves, const int32_t *moves, double *ratios);
+
+/* Walker inverse check hook: M^-1 (N x N, row-major, FP64 copy) of walker w,
+ * M_nm = f(r_n,up, r_m,dn); log|det M| and its sign from the last
+ * from-scratch factorisation. */
+int vmc_get_inverse(vmc_ctx *ctx, int32_t system, int32_t walker,
+                    double *minv, double *logabsdet, int32_t *sign);
+
+/* Number of kernels this context has launched since creation. */
+int64_t vmc_kernel_launches(vmc_ctx *ctx);
+
+/* Kernel timing with CUDA events on the context's stream (no counterpart in
+ * the paper; used to report achieved throughput).  vmc_enable_timing(ctx, 1)
+ * starts recording; vmc_kernel_times writes the accumulated milliseconds and
+ * launch counts since the last reset into ms[3] and count[3], indexed by
+ * 0 = sweep/measure kernel, 1 = from-scratch inverse kernel, 2 = SR step
+ * (all its kernels), and resets them.  Synchronises the stream. */
+int vmc_enable_timing(vmc_ctx *ctx, int32_t on);
+int vmc_kernel_times(vmc_ctx *ctx, double *ms, int64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VMC_H */

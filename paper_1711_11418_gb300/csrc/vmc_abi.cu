@@ -1,0 +1,855 @@
+// C ABI of the library (include/vmc.h): context, validation, memory, and the
+// orchestration of the kernels in vmc_walker.cu and vmc_sr.cu.
+#include "../../include/vmc.h"
+#include "vmc_common.cuh"
+
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+namespace {
+
+struct SysHost {
+  int Ns = 0, Ne = 0, N = 0, ldm = 0, Np = 0, n_g = 0, n_v = 0, n_f = 0, ldO = 0;
+  int W = 0, max_samples = 0;
+  int rows = 0;              // stored sample rows (W * n_samples or set_samples rows)
+  int n_samples = 0;         // samples per walker of the stored rows
+  bool dirty = true;         // inverses must be rebuilt before sampling
+  double p_exchange = 0.0;
+  SysDev dev{};              // host copy of the device descriptor
+  SrWork sr{};
+  bool sr_alloc = false;
+  bool S_alloc = false;
+};
+
+}  // namespace
+
+struct vmc_ctx {
+  int n_sys = 0;
+  int precision = 0;
+  uint64_t seed = 0;
+  cudaStream_t st = nullptr;
+  std::vector<SysHost> sys;
+  std::vector<void *> allocs;
+  SysDev *d_sys = nullptr;
+  int2 *d_work = nullptr;
+  int n_work = 0;
+  int *d_work_ctr = nullptr;
+  size_t smem_sample = 0, smem_init = 0;
+  int grid_sample = 0;
+  long long n_launch = 0;
+  double *d_scalar = nullptr;
+  int recompute_every = 0;
+  // timing (CUDA events on st): 0 sweep, 1 init, 2 SR
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
+  double ms[3] = {0, 0, 0};
+  long long cnt[3] = {0, 0, 0};
+};
+
+namespace {
+
+void ctx_free(vmc_ctx *c) {
+  if (!c) return;
+  for (void *p : c->allocs) cudaFree(p);
+  c->allocs.clear();
+}
+
+template <typename P>
+int dalloc(vmc_ctx *c, P **out, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return VMC_ENOMEM;
+  }
+  c->allocs.push_back(p);
+  *out = (P *)p;
+  return VMC_OK;
+}
+
+template <typename P>
+int dupload(vmc_ctx *c, P **out, const P *src, size_t count) {
+  int e = dalloc(c, out, sizeof(P) * count);
+  if (e) return e;
+  if (count && src) {
+    if (cudaMemcpyAsync(*out, src, sizeof(P) * count, cudaMemcpyHostToDevice, c->st) != cudaSuccess)
+      return VMC_ECUDA;
+  } else if (count) {
+    if (cudaMemsetAsync(*out, 0, sizeof(P) * count, c->st) != cudaSuccess) return VMC_ECUDA;
+  }
+  return VMC_OK;
+}
+
+#define CK(x)                       \
+  do {                              \
+    int _e = (x);                   \
+    if (_e != VMC_OK) return _e;    \
+  } while (0)
+#define CKC(x)                                   \
+  do {                                           \
+    if ((x) != cudaSuccess) return VMC_ECUDA;    \
+  } while (0)
+
+// splitmix64: seeded initial placements (not part of the Markov chain).
+uint64_t splitmix(uint64_t &s) {
+  uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+void random_placement(int Ns, int Ne, bool local_spin, uint64_t &state, int32_t *ele) {
+  const int N = Ne / 2;
+  std::vector<int> perm(Ns);
+  auto shuffle = [&]() {
+    for (int i = 0; i < Ns; ++i) perm[i] = i;
+    for (int i = Ns - 1; i > 0; --i) {
+      const int j = (int)(splitmix(state) % (uint64_t)(i + 1));
+      std::swap(perm[i], perm[j]);
+    }
+  };
+  shuffle();
+  if (local_spin) {
+    for (int k = 0; k < Ne; ++k) ele[k] = perm[k];
+    return;
+  }
+  for (int k = 0; k < N; ++k) ele[k] = perm[k];
+  shuffle();
+  for (int k = 0; k < N; ++k) ele[N + k] = perm[k];
+}
+
+int validate_configs(const SysHost &s, bool local_spin, const int32_t *ele, int W) {
+  std::vector<int> occ(2 * s.Ns);
+  for (int w = 0; w < W; ++w) {
+    std::fill(occ.begin(), occ.end(), 0);
+    for (int k = 0; k < s.Ne; ++k) {
+      const int site = ele[(size_t)w * s.Ne + k];
+      if (site < 0 || site >= s.Ns) return VMC_EINVAL;
+      const int sp = k >= s.N;
+      if (occ[sp * s.Ns + site]) return VMC_EINVAL;
+      occ[sp * s.Ns + site] = 1;
+    }
+    if (local_spin)
+      for (int i = 0; i < s.Ns; ++i)
+        if (occ[i] && occ[s.Ns + i]) return VMC_EINVAL;
+  }
+  return VMC_OK;
+}
+
+int validate_system(const vmc_model *m, int32_t Ne, const vmc_layout *l, const double *params) {
+  if (!m || !l || !params) return VMC_EINVAL;
+  const int Ns = m->Ns;
+  if (Ns < 2 || Ns > 4096) return VMC_EINVAL;
+  if (Ne < 2 || Ne % 2 || Ne / 2 > VMC_MAX_N || Ne / 2 > Ns) return VMC_EINVAL;
+  if (m->local_spin && Ne != Ns) return VMC_EINVAL;
+  if (m->n_hop < 0 || m->n_V < 0 || m->n_J < 0) return VMC_EINVAL;
+  if (m->n_hop && (!m->hop_i || !m->hop_j || !m->hop_t)) return VMC_EINVAL;
+  if (m->n_V && (!m->V_i || !m->V_j || !m->V_val)) return VMC_EINVAL;
+  if (m->n_J && (!m->J_i || !m->J_j || !m->J_val)) return VMC_EINVAL;
+  for (int k = 0; k < m->n_hop; ++k)
+    if (m->hop_i[k] < 0 || m->hop_i[k] >= Ns || m->hop_j[k] < 0 || m->hop_j[k] >= Ns ||
+        m->hop_i[k] == m->hop_j[k])
+      return VMC_EINVAL;
+  for (int k = 0; k < m->n_V; ++k)
+    if (m->V_i[k] < 0 || m->V_i[k] >= Ns || m->V_j[k] < 0 || m->V_j[k] >= Ns) return VMC_EINVAL;
+  for (int k = 0; k < m->n_J; ++k)
+    if (m->J_i[k] < 0 || m->J_i[k] >= Ns || m->J_j[k] < 0 || m->J_j[k] >= Ns ||
+        m->J_i[k] == m->J_j[k])
+      return VMC_EINVAL;
+  if (l->n_g < 0 || l->n_v < 0 || l->n_f < 1) return VMC_EINVAL;
+  if (!l->f_idx || !l->f_sign) return VMC_EINVAL;
+  if (l->n_g && !l->g_idx) return VMC_EINVAL;
+  if (l->n_v && !l->v_idx) return VMC_EINVAL;
+  if (l->n_g)
+    for (int i = 0; i < Ns; ++i)
+      if (l->g_idx[i] < -1 || l->g_idx[i] >= l->n_g) return VMC_EINVAL;
+  const size_t n2 = (size_t)Ns * Ns;
+  if (l->n_v)
+    for (size_t q = 0; q < n2; ++q) {
+      const int i = (int)(q / Ns), j = (int)(q % Ns);
+      if (l->v_idx[q] < -1 || l->v_idx[q] >= l->n_v) return VMC_EINVAL;
+      if (l->v_idx[q] != l->v_idx[(size_t)j * Ns + i]) return VMC_EINVAL;
+    }
+  for (size_t q = 0; q < n2; ++q) {
+    if (l->f_idx[q] < -1 || l->f_idx[q] >= l->n_f) return VMC_EINVAL;
+    if (l->f_sign[q] != 1 && l->f_sign[q] != -1 && l->f_idx[q] >= 0) return VMC_EINVAL;
+  }
+  const int Np = l->n_g + l->n_v + l->n_f;
+  for (int k = 0; k < Np; ++k)
+    if (!isfinite(params[k])) return VMC_EINVAL;
+  return VMC_OK;
+}
+
+// Event pair around a region of kernels on the context stream.
+struct TimedRegion {
+  vmc_ctx *c;
+  int k;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedRegion(vmc_ctx *c_, int k_) : c(c_), k(k_) {
+    if (c->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+      cudaEventRecord(a, c->st);
+  }
+  ~TimedRegion() {
+    if (a && b) {
+      cudaEventRecord(b, c->st);
+      c->ev[k].push_back({a, b});
+    }
+  }
+};
+
+void collect_times(vmc_ctx *c) {
+  for (int k = 0; k < 3; ++k) {
+    for (auto &p : c->ev[k]) {
+      float t = 0.f;
+      if (cudaEventSynchronize(p.second) == cudaSuccess &&
+          cudaEventElapsedTime(&t, p.first, p.second) == cudaSuccess) {
+        c->ms[k] += t;
+        c->cnt[k] += 1;
+      }
+      cudaEventDestroy(p.first);
+      cudaEventDestroy(p.second);
+    }
+    c->ev[k].clear();
+  }
+}
+
+int upload_sysdesc(vmc_ctx *c) {
+  std::vector<SysDev> h(c->n_sys);
+  for (int s = 0; s < c->n_sys; ++s) h[s] = c->sys[s].dev;
+  CKC(cudaMemcpyAsync(c->d_sys, h.data(), sizeof(SysDev) * c->n_sys, cudaMemcpyHostToDevice, c->st));
+  return VMC_OK;
+}
+
+// Rebuild the walkers' inverses from scratch (FP64) where needed; returns
+// VMC_ESINGULAR if any walker's M is singular.
+int ensure_init(vmc_ctx *c, bool redraw_illcond = false) {
+  bool any = false;
+  for (auto &s : c->sys) any |= s.dirty;
+  if (!any) return VMC_OK;
+  CK(upload_sysdesc(c));
+  {
+    TimedRegion tr(c, 1);
+    CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 0, 0, c->smem_init, c->st,
+                        &c->n_launch));
+  }
+  int bad = 0;
+  for (auto &s : c->sys) {
+    std::vector<int> st(s.W);
+    CKC(cudaMemcpyAsync(st.data(), s.dev.status, sizeof(int) * s.W, cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    for (int w = 0; w < s.W; ++w) bad |= st[w];
+    s.dirty = false;
+  }
+  if ((bad & VMC_ST_SINGULAR) || (redraw_illcond && (bad & VMC_ST_ILLCOND))) {
+    for (auto &s : c->sys) s.dirty = true;
+    return VMC_ESINGULAR;
+  }
+  return VMC_OK;
+}
+
+int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
+  const int rows_cap = s.W * s.max_samples;
+  if (!s.sr_alloc) {
+    SrWork &w = s.sr;
+    const int Np = s.Np;
+    CK(dalloc(c, &w.obar, sizeof(double) * Np));
+    CK(dalloc(c, &w.ebar, sizeof(double) * 8));
+    CK(dalloc(c, &w.g, sizeof(double) * Np));
+    CK(dalloc(c, &w.diagS, sizeof(double) * Np));
+    CK(dalloc(c, &w.x, sizeof(double) * Np));
+    CK(dalloc(c, &w.r, sizeof(double) * 2 * Np));
+    CK(dalloc(c, &w.p, sizeof(double) * Np));
+    CK(dalloc(c, &w.w, sizeof(double) * Np));
+    CK(dalloc(c, &w.t, sizeof(double) * rows_cap));
+    CK(dalloc(c, &w.scal, sizeof(double) * 8));
+    CK(dalloc(c, &w.info, sizeof(int) * 4));
+    const size_t nparts = (size_t)(rows_cap + 2047) / 2048;
+    CK(dalloc(c, &w.part, sizeof(double) * nparts * Np));
+    s.sr_alloc = true;
+  }
+  if (need_S && !s.S_alloc) {
+    CK(dalloc(c, &s.sr.S, sizeof(double) * (size_t)s.Np * s.Np));
+    s.S_alloc = true;
+  }
+  s.sr.Np = s.Np;
+  s.sr.rows = s.rows;
+  s.sr.ldO = s.ldO;
+  s.sr.precision = c->precision;
+  s.sr.O = s.dev.O;
+  s.sr.E = s.dev.E;
+  return VMC_OK;
+}
+
+int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t *Ne,
+                const vmc_layout *layouts, const double *const *params, const double *pex,
+                const vmc_opts *o) {
+  if (!out || n_sys < 1 || !models || !Ne || !layouts || !params || !o) return VMC_EINVAL;
+  *out = nullptr;
+  if (o->n_walkers < 1 || o->max_samples < 1) return VMC_EINVAL;
+  if (o->precision != VMC_FP64 && o->precision != VMC_MIXED) return VMC_EINVAL;
+  for (int s = 0; s < n_sys; ++s) {
+    CK(validate_system(&models[s], Ne[s], &layouts[s], params[s]));
+    if (pex && (!(pex[s] >= 0.0) || pex[s] > 1.0)) return VMC_EINVAL;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return VMC_ECUDA;
+  }
+  vmc_ctx *c = new (std::nothrow) vmc_ctx();
+  if (!c) return VMC_ENOMEM;
+  c->n_sys = n_sys;
+  c->precision = o->precision;
+  c->seed = o->seed;
+  c->st = (cudaStream_t)o->stream;
+  c->sys.resize(n_sys);
+  const int esize = o->precision == VMC_FP64 ? 8 : 4;
+  int rc = VMC_OK;
+  size_t smem64 = 0, smem32 = 0;
+  int maxN = 1;
+  auto fail = [&](int e) {
+    ctx_free(c);
+    delete c;
+    return e;
+  };
+  for (int si = 0; si < n_sys; ++si) {
+    const vmc_model &m = models[si];
+    const vmc_layout &l = layouts[si];
+    SysHost &s = c->sys[si];
+    s.Ns = m.Ns;
+    s.Ne = Ne[si];
+    s.N = s.Ne / 2;
+    s.ldm = (s.N % 2) ? s.N : s.N + 1;
+    s.n_g = l.n_g;
+    s.n_v = l.n_v;
+    s.n_f = l.n_f;
+    s.Np = l.n_g + l.n_v + l.n_f;
+    s.ldO = (s.Np + 3) / 4 * 4;
+    s.W = o->n_walkers;
+    s.max_samples = o->max_samples;
+    s.p_exchange = m.local_spin ? 1.0 : (pex ? pex[si] : 0.0);
+    maxN = std::max(maxN, s.N);
+    SysDev &d = s.dev;
+    d.Ns = s.Ns;
+    d.Ne = s.Ne;
+    d.N = s.N;
+    d.ldm = s.ldm;
+    d.n_hop = m.n_hop;
+    d.n_V = m.n_V;
+    d.n_J = m.n_J;
+    d.local_spin = m.local_spin ? 1 : 0;
+    {
+      const double t = s.p_exchange * 4294967296.0;
+      d.pex = t >= 4294967296.0 ? 4294967296ull : (unsigned long long)t;
+    }
+    d.Np = s.Np;
+    d.n_g = s.n_g;
+    d.n_v = s.n_v;
+    d.n_f = s.n_f;
+    d.ldO = s.ldO;
+    d.W = s.W;
+    d.sys_index = si;
+    d.n_samples = s.max_samples;
+    const size_t Ns = s.Ns, n2 = Ns * Ns;
+    std::vector<double> Uz(Ns, 0.0);
+    const int *hi = nullptr, *hj = nullptr;
+    const double *ht = nullptr;
+    if ((rc = dupload(c, (int **)&hi, m.hop_i, m.n_hop))) return fail(rc);
+    if ((rc = dupload(c, (int **)&hj, m.hop_j, m.n_hop))) return fail(rc);
+    if ((rc = dupload(c, (double **)&ht, m.hop_t, m.n_hop))) return fail(rc);
+    d.hop_i = hi;
+    d.hop_j = hj;
+    d.hop_t = ht;
+    if ((rc = dupload(c, (double **)&d.U, m.U ? m.U : Uz.data(), Ns))) return fail(rc);
+    if ((rc = dupload(c, (int **)&d.V_i, m.V_i, m.n_V))) return fail(rc);
+    if ((rc = dupload(c, (int **)&d.V_j, m.V_j, m.n_V))) return fail(rc);
+    if ((rc = dupload(c, (double **)&d.V_val, m.V_val, m.n_V))) return fail(rc);
+    if ((rc = dupload(c, (int **)&d.J_i, m.J_i, m.n_J))) return fail(rc);
+    if ((rc = dupload(c, (int **)&d.J_j, m.J_j, m.n_J))) return fail(rc);
+    if ((rc = dupload(c, (double **)&d.J_val, m.J_val, m.n_J))) return fail(rc);
+    std::vector<int> gneg(Ns, -1), vneg;
+    if ((rc = dupload(c, (int **)&d.g_idx, l.n_g ? l.g_idx : gneg.data(), Ns))) return fail(rc);
+    if (!l.n_v) vneg.assign(n2, -1);
+    if ((rc = dupload(c, (int **)&d.v_idx, l.n_v ? l.v_idx : vneg.data(), n2))) return fail(rc);
+    if ((rc = dupload(c, (int **)&d.f_idx, l.f_idx, n2))) return fail(rc);
+    if ((rc = dupload(c, (signed char **)&d.f_sign, (const signed char *)l.f_sign, n2))) return fail(rc);
+    if ((rc = dupload(c, (double **)&d.params, params[si], s.Np))) return fail(rc);
+    if ((rc = dalloc(c, &d.f64, sizeof(double) * n2))) return fail(rc);
+    if ((rc = dalloc(c, &d.fT64, sizeof(double) * n2))) return fail(rc);
+    if ((rc = dalloc(c, &d.f32, sizeof(float) * n2))) return fail(rc);
+    if ((rc = dalloc(c, &d.fT32, sizeof(float) * n2))) return fail(rc);
+    if ((rc = dalloc(c, &d.vmat, sizeof(double) * n2))) return fail(rc);
+    if ((rc = dalloc(c, &d.gsite, sizeof(double) * Ns))) return fail(rc);
+    const size_t W = s.W;
+    const size_t mb = ((size_t)s.N * s.ldm * esize + 127) / 128 * 128;
+    if ((rc = dalloc(c, &d.ele, sizeof(int) * W * s.Ne))) return fail(rc);
+    if ((rc = dalloc(c, &d.occ, sizeof(int) * W * 2 * Ns))) return fail(rc);
+    if ((rc = dalloc(c, &d.minv, mb * W))) return fail(rc);
+    if ((rc = dalloc(c, &d.jf, sizeof(double) * W * Ns))) return fail(rc);
+    if ((rc = dupload(c, &d.ctr, (const unsigned long long *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.logdet, (const double *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.detsign, (const int *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.n_prop, (const long long *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.n_acc, (const long long *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.cnt, (const long long *)nullptr, 8 * W))) return fail(rc);
+    if ((rc = dupload(c, &d.n_rec, (const long long *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.acc_since, (const int *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.status, (const int *)nullptr, W))) return fail(rc);
+    if ((rc = dupload(c, &d.drift, (const double *)nullptr, W))) return fail(rc);
+    const size_t rows_cap = W * s.max_samples;
+    if ((rc = dupload(c, &d.E, (const double *)nullptr, rows_cap))) return fail(rc);
+    if ((rc = dalloc(c, &d.O, (size_t)esize * rows_cap * s.ldO))) return fail(rc);
+    int acc_len = 0;
+    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, &acc_len));
+    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, &acc_len));
+    d.acc_len = acc_len;
+    c->smem_init = std::max(c->smem_init, vmc_init_smem(s.N, s.Ns));
+    if (vmc_launch_expand(&d, c->st, &c->n_launch) != cudaSuccess) return fail(VMC_ECUDA);
+    // seeded random placement
+    std::vector<int32_t> ele(W * s.Ne);
+    uint64_t state = o->seed ^ (0xA0761D6478BD642Full * (uint64_t)(si + 1));
+    for (size_t w = 0; w < W; ++w)
+      random_placement(s.Ns, s.Ne, m.local_spin != 0, state, ele.data() + w * s.Ne);
+    if (cudaMemcpyAsync(d.ele, ele.data(), sizeof(int32_t) * ele.size(), cudaMemcpyHostToDevice,
+                        c->st) != cudaSuccess)
+      return fail(VMC_ECUDA);
+  }
+  c->smem_sample = (c->precision == VMC_FP64) ? smem64 : smem32;
+  if (vmc_walker_set_smem_limits(smem64, smem32, c->smem_init) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(VMC_EINVAL);  // does not fit in shared memory
+  }
+  // work list: (system, walker), larger N first
+  std::vector<int2> work;
+  std::vector<int> order(n_sys);
+  for (int s = 0; s < n_sys; ++s) order[s] = s;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return c->sys[a].N > c->sys[b].N; });
+  for (int s : order)
+    for (int w = 0; w < c->sys[s].W; ++w) work.push_back(make_int2(s, w));
+  c->n_work = (int)work.size();
+  if ((rc = dupload(c, &c->d_work, work.data(), work.size()))) return fail(rc);
+  if ((rc = dalloc(c, &c->d_work_ctr, sizeof(int) * 4))) return fail(rc);
+  if ((rc = dalloc(c, &c->d_sys, sizeof(SysDev) * n_sys))) return fail(rc);
+  if ((rc = dalloc(c, &c->d_scalar, sizeof(double) * 8))) return fail(rc);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int occ = std::max(1, vmc_sample_occupancy(c->precision, c->smem_sample));
+  c->grid_sample = std::min(c->n_work, nsm * occ);
+  c->recompute_every = o->recompute_every > 0 ? o->recompute_every
+                       : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 64 : 0;
+  // Initial inverses; re-draw placements whose M is singular (bounded).
+  uint64_t state = o->seed ^ 0x5851F42D4C957F2Dull;
+  for (int attempt = 0;; ++attempt) {
+    rc = ensure_init(c, true);
+    if (rc == VMC_OK) break;
+    if (rc != VMC_ESINGULAR || attempt >= 20) return fail(rc);
+    for (int si = 0; si < n_sys; ++si) {
+      SysHost &s = c->sys[si];
+      std::vector<int> st(s.W);
+      std::vector<int32_t> ele((size_t)s.W * s.Ne);
+      if (cudaMemcpy(st.data(), s.dev.status, sizeof(int) * s.W, cudaMemcpyDeviceToHost) ||
+          cudaMemcpy(ele.data(), s.dev.ele, sizeof(int32_t) * ele.size(), cudaMemcpyDeviceToHost))
+        return fail(VMC_ECUDA);
+      for (int w = 0; w < s.W; ++w)
+        if (st[w] & (VMC_ST_SINGULAR | VMC_ST_ILLCOND))
+          random_placement(s.Ns, s.Ne, models[si].local_spin != 0, state, ele.data() + (size_t)w * s.Ne);
+      std::vector<int> zero(s.W, 0);
+      if (cudaMemcpy(s.dev.ele, ele.data(), sizeof(int32_t) * ele.size(), cudaMemcpyHostToDevice) ||
+          cudaMemcpy(s.dev.status, zero.data(), sizeof(int) * s.W, cudaMemcpyHostToDevice))
+        return fail(VMC_ECUDA);
+    }
+  }
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(VMC_ECUDA);
+  *out = c;
+  return VMC_OK;
+}
+
+bool sys_ok(vmc_ctx *c, int s) { return c && s >= 0 && s < c->n_sys; }
+
+
+
+}  // namespace
+
+extern "C" {
+
+const char *vmc_strerror(int code) {
+  switch (code) {
+    case VMC_OK: return "ok";
+    case VMC_EINVAL: return "invalid argument";
+    case VMC_ENOMEM: return "out of memory";
+    case VMC_ECUDA: return "CUDA error";
+    case VMC_ESINGULAR: return "singular matrix (Pf(X) = 0 or S not positive definite)";
+    case VMC_ENUMERIC: return "numerical fault (NaN/Inf or breakdown)";
+    case VMC_ETIMEOUT: return "bounded device wait expired";
+    case VMC_ESTATE: return "call not valid in the current state";
+    default: return "unknown error";
+  }
+}
+
+int vmc_create(vmc_ctx **out, const vmc_model *model, int32_t Ne, const vmc_layout *layout,
+               const double *params, double p_exchange, const vmc_opts *opts) {
+  const double *pp[1] = {params};
+  return create_impl(out, 1, model, &Ne, layout, pp, &p_exchange, opts);
+}
+
+int vmc_create_batch(vmc_ctx **out, int32_t n_systems, const vmc_model *models, const int32_t *Ne,
+                     const vmc_layout *layouts, const double *const *params,
+                     const double *p_exchange, const vmc_opts *opts) {
+  return create_impl(out, n_systems, models, Ne, layouts, params, p_exchange, opts);
+}
+
+void vmc_destroy(vmc_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  else cudaDeviceSynchronize();
+  collect_times(ctx);
+  ctx_free(ctx);
+  delete ctx;
+}
+
+int vmc_set_configs(vmc_ctx *c, int32_t system, const int32_t *ele, const uint64_t *counters) {
+  if (!sys_ok(c, system) || !ele) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  CK(validate_configs(s, s.dev.local_spin != 0, ele, s.W));
+  CKC(cudaMemcpyAsync(s.dev.ele, ele, sizeof(int32_t) * (size_t)s.W * s.Ne, cudaMemcpyHostToDevice, c->st));
+  if (counters)
+    CKC(cudaMemcpyAsync(s.dev.ctr, counters, sizeof(uint64_t) * s.W, cudaMemcpyHostToDevice, c->st));
+  CKC(cudaMemsetAsync(s.dev.status, 0, sizeof(int) * s.W, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  s.dirty = true;
+  return VMC_OK;
+}
+
+int vmc_get_configs(vmc_ctx *c, int32_t system, int32_t *ele, uint64_t *counters) {
+  if (!sys_ok(c, system)) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (ele)
+    CKC(cudaMemcpyAsync(ele, s.dev.ele, sizeof(int32_t) * (size_t)s.W * s.Ne, cudaMemcpyDeviceToHost, c->st));
+  if (counters)
+    CKC(cudaMemcpyAsync(counters, s.dev.ctr, sizeof(uint64_t) * s.W, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  return VMC_OK;
+}
+
+int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_between) {
+  if (!c || n_warmup < 0 || n_samples < 0 || sweeps_between < 0) return VMC_EINVAL;
+  for (auto &s : c->sys)
+    if (n_samples > s.max_samples) return VMC_EINVAL;
+  CK(ensure_init(c));
+  for (auto &s : c->sys) {
+    s.dev.n_samples = n_samples > 0 ? n_samples : s.max_samples;
+    if (n_samples > 0) {
+      s.n_samples = n_samples;
+      s.rows = s.W * n_samples;
+    }
+  }
+  CK(upload_sysdesc(c));
+  auto sweep = [&](int n_first, int ns, int sb, int base) -> int {
+    TimedRegion tr(c, 0);
+    CKC(vmc_launch_sample(c->d_sys, c->d_work, c->n_work, c->d_work_ctr, c->precision, c->seed,
+                          n_first, ns, sb, base, c->grid_sample, c->smem_sample, c->st,
+                          &c->n_launch));
+    return VMC_OK;
+  };
+  if (c->recompute_every <= 0) {
+    CK(sweep(n_warmup, n_samples, sweeps_between, 0));
+  } else {
+    // Periodic FP64 from-scratch inverses (fast updates accumulate rounding):
+    // after every sweep launch, walkers with at least recompute_every
+    // accepted moves since their last inverse are rebuilt.
+    auto recompute = [&]() -> int {
+      TimedRegion tr(c, 1);
+      CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 1, c->recompute_every,
+                          c->smem_init, c->st, &c->n_launch));
+      return VMC_OK;
+    };
+    for (int k = 0; k < n_warmup; ++k) {
+      CK(sweep(1, 0, 0, 0));
+      CK(recompute());
+    }
+    for (int k = 0; k < n_samples; ++k) {
+      CK(sweep(0, 1, sweeps_between, k));
+      CK(recompute());
+    }
+  }
+  int bad = 0;
+  for (auto &s : c->sys) {
+    std::vector<int> st(s.W);
+    CKC(cudaMemcpyAsync(st.data(), s.dev.status, sizeof(int) * s.W, cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    for (int w = 0; w < s.W; ++w) bad |= st[w];
+  }
+  if (bad & VMC_ST_SINGULAR) return VMC_ESINGULAR;
+  if (bad & VMC_ST_NUMERIC) return VMC_ENUMERIC;
+  return VMC_OK;
+}
+
+int vmc_measure(vmc_ctx *c, int32_t system, vmc_stats *out) {
+  if (!sys_ok(c, system) || !out) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  memset(out, 0, sizeof(*out));
+  std::vector<long long> np(s.W), na(s.W);
+  std::vector<int> st(s.W);
+  std::vector<double> dr(s.W);
+  CKC(cudaMemcpyAsync(np.data(), s.dev.n_prop, sizeof(long long) * s.W, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaMemcpyAsync(na.data(), s.dev.n_acc, sizeof(long long) * s.W, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaMemcpyAsync(st.data(), s.dev.status, sizeof(int) * s.W, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaMemcpyAsync(dr.data(), s.dev.drift, sizeof(double) * s.W, cudaMemcpyDeviceToHost, c->st));
+  std::vector<long long> cn(8 * (size_t)s.W), nr(s.W);
+  CKC(cudaMemcpyAsync(cn.data(), s.dev.cnt, sizeof(long long) * cn.size(), cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaMemcpyAsync(nr.data(), s.dev.n_rec, sizeof(long long) * s.W, cudaMemcpyDeviceToHost, c->st));
+  std::vector<double> E(s.rows);
+  if (s.rows)
+    CKC(cudaMemcpyAsync(E.data(), s.dev.E, sizeof(double) * s.rows, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  for (int w = 0; w < s.W; ++w) {
+    out->n_proposals += np[w];
+    out->n_accepted += na[w];
+    out->n_flagged += (st[w] & (VMC_ST_SINGULAR | VMC_ST_NUMERIC)) != 0;
+    out->max_drift = std::max(out->max_drift, dr[w]);
+    out->n_hop_tested += cn[8 * w + 0];
+    out->n_exchange_tested += cn[8 * w + 1];
+    out->n_hop_accepted += cn[8 * w + 2];
+    out->n_exchange_accepted += cn[8 * w + 3];
+    out->n_measured_hops += cn[8 * w + 4];
+    out->n_measured_exchanges += cn[8 * w + 5];
+    out->n_measurements += cn[8 * w + 6];
+    out->n_recomputes += nr[w];
+  }
+  out->acceptance = out->n_proposals ? (double)out->n_accepted / out->n_proposals : 0.0;
+  out->n_samples = s.rows;
+  if (s.rows) {
+    double sum = 0.0;
+    for (double e : E) sum += e;
+    const double mean = sum / s.rows;
+    double var = 0.0;
+    for (double e : E) var += (e - mean) * (e - mean);
+    out->energy = mean;
+    out->variance = s.rows > 1 ? var / (s.rows - 1) : 0.0;
+    const int per = s.n_samples > 0 ? s.n_samples : 1;
+    const int nw = s.rows / per;
+    if (nw > 1) {
+      double m1 = 0.0, m2 = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        double a = 0.0;
+        for (int k = 0; k < per; ++k) a += E[(size_t)w * per + k];
+        a /= per;
+        m1 += a;
+        m2 += a * a;
+      }
+      m1 /= nw;
+      const double vw = (m2 / nw - m1 * m1) * nw / (nw - 1);
+      out->stderr_walkers = sqrt(std::max(vw, 0.0) / nw);
+    }
+  }
+  return VMC_OK;
+}
+
+int vmc_get_samples(vmc_ctx *c, int32_t system, double *E, double *O) {
+  if (!sys_ok(c, system)) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (!s.rows) return VMC_ESTATE;
+  if (E) CKC(cudaMemcpyAsync(E, s.dev.E, sizeof(double) * s.rows, cudaMemcpyDeviceToHost, c->st));
+  if (O) {
+    if (c->precision == VMC_FP64) {
+      CKC(cudaMemcpy2DAsync(O, sizeof(double) * s.Np, s.dev.O, sizeof(double) * s.ldO,
+                            sizeof(double) * s.Np, s.rows, cudaMemcpyDeviceToHost, c->st));
+    } else {
+      std::vector<float> tmp((size_t)s.rows * s.ldO);
+      CKC(cudaMemcpyAsync(tmp.data(), s.dev.O, sizeof(float) * tmp.size(), cudaMemcpyDeviceToHost, c->st));
+      CKC(cudaStreamSynchronize(c->st));
+      for (size_t r = 0; r < (size_t)s.rows; ++r)
+        for (int k = 0; k < s.Np; ++k) O[r * s.Np + k] = tmp[r * s.ldO + k];
+    }
+  }
+  CKC(cudaStreamSynchronize(c->st));
+  return VMC_OK;
+}
+
+int vmc_set_samples(vmc_ctx *c, int32_t system, int32_t rows, const double *E, const double *O) {
+  if (!sys_ok(c, system) || !E || !O) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (rows < 1 || rows > s.W * s.max_samples) return VMC_EINVAL;
+  CKC(cudaMemcpyAsync(s.dev.E, E, sizeof(double) * rows, cudaMemcpyHostToDevice, c->st));
+  if (c->precision == VMC_FP64) {
+    CKC(cudaMemcpy2DAsync(s.dev.O, sizeof(double) * s.ldO, O, sizeof(double) * s.Np,
+                          sizeof(double) * s.Np, rows, cudaMemcpyHostToDevice, c->st));
+  } else {
+    std::vector<float> tmp((size_t)rows * s.ldO, 0.0f);
+    for (size_t r = 0; r < (size_t)rows; ++r)
+      for (int k = 0; k < s.Np; ++k) tmp[r * s.ldO + k] = (float)O[r * s.Np + k];
+    CKC(cudaMemcpyAsync(s.dev.O, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+  }
+  CKC(cudaStreamSynchronize(c->st));
+  s.rows = rows;
+  s.n_samples = 1;
+  return VMC_OK;
+}
+
+int vmc_get_sr_matrices(vmc_ctx *c, int32_t system, double shift_rel, double shift_abs, double *S,
+                        double *g) {
+  if (!sys_ok(c, system)) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (!s.rows) return VMC_ESTATE;
+  CK(sr_alloc(c, s, S != nullptr));
+  CKC(vmc_sr_means(s.sr, c->st, &c->n_launch));
+  CKC(vmc_sr_build_g(s.sr, c->st, &c->n_launch));
+  if (S) {
+    CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, c->st, &c->n_launch));
+    CKC(cudaMemcpyAsync(S, s.sr.S, sizeof(double) * (size_t)s.Np * s.Np, cudaMemcpyDeviceToHost, c->st));
+  }
+  if (g) CKC(cudaMemcpyAsync(g, s.sr.g, sizeof(double) * s.Np, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  return VMC_OK;
+}
+
+int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report *rep) {
+  if (!sys_ok(c, system) || !o) return VMC_EINVAL;
+  if (!(o->dtau > 0.0) || o->shift_rel < 0.0 || o->shift_abs < 0.0) return VMC_EINVAL;
+  if (o->solver != VMC_SOLVE_CHOLESKY && o->solver != VMC_SOLVE_CG) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (!s.rows) return VMC_ESTATE;
+  const bool chol = o->solver == VMC_SOLVE_CHOLESKY;
+  CK(sr_alloc(c, s, chol));
+  SrWork &w = s.sr;
+  TimedRegion tr(c, 2);
+  CKC(vmc_sr_means(w, c->st, &c->n_launch));
+  CKC(vmc_sr_build_g(w, c->st, &c->n_launch));
+  int iters = 0;
+  if (chol) {
+    CKC(vmc_sr_build_S(w, o->shift_rel, o->shift_abs, c->st, &c->n_launch));
+    const int rc = vmc_sr_cholesky_solve(w, c->st, &c->n_launch);
+    if (rc) return rc;
+  } else {
+    CKC(vmc_sr_diag(w, c->st, &c->n_launch));
+    const double eps = o->cg_eps > 0.0 ? o->cg_eps : 1e-10;
+    const int kmax = o->cg_kmax > 0 ? o->cg_kmax : 1000;
+    const int rc = vmc_sr_cg_solve(w, o->shift_rel, o->shift_abs, eps, kmax, &iters, c->st, &c->n_launch);
+    if (rc) return rc;
+  }
+  double gg = 0.0, xx = 0.0, eb = 0.0;
+  CKC(vmc_dot_host(w.g, w.g, s.Np, &gg, c->d_scalar, c->st, &c->n_launch));
+  CKC(vmc_dot_host(w.x, w.x, s.Np, &xx, c->d_scalar, c->st, &c->n_launch));
+  CKC(cudaMemcpyAsync(&eb, w.ebar, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  if (!isfinite(xx)) return VMC_ENUMERIC;
+  CKC(vmc_sr_update_params((double *)s.dev.params, w.x, o->dtau, s.Np, c->st, &c->n_launch));
+  CKC(vmc_launch_expand(&s.dev, c->st, &c->n_launch));
+  CKC(cudaStreamSynchronize(c->st));
+  s.dirty = true;
+  if (rep) {
+    rep->energy = eb;
+    rep->norm_g = sqrt(gg);
+    rep->norm_dalpha = o->dtau * sqrt(xx);
+    rep->cg_iters = iters;
+    rep->n_params = s.Np;
+  }
+  return VMC_OK;
+}
+
+int vmc_get_params(vmc_ctx *c, int32_t system, double *params) {
+  if (!sys_ok(c, system) || !params) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  CKC(cudaMemcpyAsync(params, s.dev.params, sizeof(double) * s.Np, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  return VMC_OK;
+}
+
+int vmc_set_params(vmc_ctx *c, int32_t system, const double *params) {
+  if (!sys_ok(c, system) || !params) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  for (int k = 0; k < s.Np; ++k)
+    if (!isfinite(params[k])) return VMC_EINVAL;
+  CKC(cudaMemcpyAsync((double *)s.dev.params, params, sizeof(double) * s.Np, cudaMemcpyHostToDevice, c->st));
+  CKC(vmc_launch_expand(&s.dev, c->st, &c->n_launch));
+  CKC(cudaStreamSynchronize(c->st));
+  s.dirty = true;
+  return VMC_OK;
+}
+
+int vmc_num_params(vmc_ctx *c, int32_t system) {
+  if (!sys_ok(c, system)) return VMC_EINVAL;
+  return c->sys[system].Np;
+}
+
+int vmc_eval_ratios(vmc_ctx *c, int32_t system, int32_t walker, int32_t n_moves,
+                    const int32_t *moves, double *ratios) {
+  if (!sys_ok(c, system) || n_moves < 1 || !moves || !ratios) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (walker < 0 || walker >= s.W) return VMC_EINVAL;
+  CK(ensure_init(c));
+  CK(upload_sysdesc(c));
+  int *dm = nullptr;
+  double *dout = nullptr;
+  if (cudaMalloc(&dm, sizeof(int) * 3 * n_moves) != cudaSuccess) return VMC_ENOMEM;
+  if (cudaMalloc(&dout, sizeof(double) * n_moves) != cudaSuccess) {
+    cudaFree(dm);
+    return VMC_ENOMEM;
+  }
+  int rc = VMC_OK;
+  if (cudaMemcpyAsync(dm, moves, sizeof(int) * 3 * n_moves, cudaMemcpyHostToDevice, c->st) ||
+      vmc_launch_eval_ratios(c->d_sys, system, walker, c->precision, n_moves, dm, dout,
+                             c->smem_sample, c->st, &c->n_launch) ||
+      cudaMemcpyAsync(ratios, dout, sizeof(double) * n_moves, cudaMemcpyDeviceToHost, c->st) ||
+      cudaStreamSynchronize(c->st))
+    rc = VMC_ECUDA;
+  cudaFree(dm);
+  cudaFree(dout);
+  return rc;
+}
+
+int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, double *logabsdet,
+                    int32_t *sign) {
+  if (!sys_ok(c, system)) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (walker < 0 || walker >= s.W) return VMC_EINVAL;
+  CK(ensure_init(c));
+  const int esize = c->precision == VMC_FP64 ? 8 : 4;
+  const size_t mb = ((size_t)s.N * s.ldm * esize + 127) / 128 * 128;
+  std::vector<unsigned char> buf(mb);
+  CKC(cudaMemcpyAsync(buf.data(), (unsigned char *)s.dev.minv + mb * walker, mb, cudaMemcpyDeviceToHost, c->st));
+  double ld = 0.0;
+  int sg = 0;
+  CKC(cudaMemcpyAsync(&ld, s.dev.logdet + walker, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaMemcpyAsync(&sg, s.dev.detsign + walker, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  if (minv)
+    for (int r = 0; r < s.N; ++r)
+      for (int k = 0; k < s.N; ++k)
+        minv[(size_t)r * s.N + k] = esize == 8 ? ((double *)buf.data())[(size_t)r * s.ldm + k]
+                                               : ((float *)buf.data())[(size_t)r * s.ldm + k];
+  if (logabsdet) *logabsdet = ld;
+  if (sign) *sign = sg;
+  return VMC_OK;
+}
+
+int64_t vmc_kernel_launches(vmc_ctx *c) { return c ? c->n_launch : -1; }
+
+int vmc_enable_timing(vmc_ctx *c, int32_t on) {
+  if (!c) return VMC_EINVAL;
+  collect_times(c);
+  c->timing = on != 0;
+  return VMC_OK;
+}
+
+int vmc_kernel_times(vmc_ctx *c, double *ms, int64_t *count) {
+  if (!c || !ms || !count) return VMC_EINVAL;
+  collect_times(c);
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = c->ms[k];
+    count[k] = c->cnt[k];
+    c->ms[k] = 0.0;
+    c->cnt[k] = 0;
+  }
+  return VMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Shared declarations of the CUDA path (device structures, Philox, launch
+// wrappers).  Used only by the library's own translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define VMC_NT 128          // threads per walker CTA (one per row of M^-1)
+#define VMC_MAX_N 128       // N = Ne/2 limit of the walker kernels
+#define VMC_ACC_MAX 2048    // O-row accumulator kept in shared memory up to this Np
+
+// Per-walker status bits.
+#define VMC_ST_SINGULAR 1
+#define VMC_ST_NUMERIC 2
+#define VMC_ST_ILLCOND 4     // min/max |pivot| of the last from-scratch inverse below 1e-12
+
+// One system of a (possibly batched) context, as the kernels see it.  All
+// pointers are device pointers.
+struct SysDev {
+  int Ns, Ne, N, ldm;          // ldm: row stride of M^-1 (odd, >= N)
+  int n_hop, n_V, n_J, local_spin;
+  unsigned long long pex;      // exchange iff r0 < pex (pex <= 2^32)
+  int Np, n_g, n_v, n_f, ldO;
+  int W;                       // walkers
+  int sys_index;               // system index (Philox counter word 3)
+  int n_samples;               // sample rows per walker in the buffers
+  int acc_len;                 // O-row accumulator length in shared memory (0 = global)
+  const int *hop_i, *hop_j;
+  const double *hop_t;
+  const double *U;
+  const int *V_i, *V_j;
+  const double *V_val;
+  const int *J_i, *J_j;
+  const double *J_val;
+  const int *g_idx, *v_idx, *f_idx;
+  const signed char *f_sign;
+  const double *params;
+  double *f64, *fT64;          // expanded f_ij and its transpose [Ns*Ns]
+  float *f32, *fT32;
+  double *vmat;                // v_ij [Ns*Ns]
+  double *gsite;               // g_i [Ns]
+  // walker state
+  int *ele;                    // [W*Ne]
+  int *occ;                    // [W*2*Ns]: occ[s*Ns + i] = label or -1
+  void *minv;                  // [W*N*ldm] (double or float)
+  double *jf;                  // [W*Ns] Jastrow field sum_{j != i} v_ij (n_j - 1)
+  unsigned long long *ctr;     // [W] Philox proposal counters
+  double *logdet;              // [W]
+  int *detsign;                // [W]
+  double *E;                   // [W*n_samples]
+  void *O;                     // [W*n_samples*ldO] (double or float)
+  long long *n_prop, *n_acc;   // [W]
+  long long *cnt;              // [W*8]: valid hops, valid exchanges, accepted hops, accepted
+                               // exchanges, measured hop ratios, measured exchange ratios, samples
+  long long *n_rec;            // [W] periodic from-scratch inverses
+  int *acc_since;              // [W] accepted moves since the last FP64 inverse
+  int *status;                 // [W]
+  double *drift;               // [W]
+  int recompute_every;         // accepted moves between FP64 from-scratch inverses (0 = never)
+  int pad_;
+};
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its published
+// definition: ten rounds of two 32x32->64 multiplies with a Weyl key schedule.
+__device__ __forceinline__ uint4 vmc_philox(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ int vmc_mulhi(uint32_t r, int n) {
+  return (int)(((unsigned long long)r * (unsigned long long)n) >> 32);
+}
+
+// ---- launch wrappers (defined in vmc_walker.cu / vmc_sr.cu) ----
+// All return cudaError_t from the launch; they count launches in *n_launch.
+cudaError_t vmc_launch_expand(const SysDev *h_sys, cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work,
+                            int precision, int only_due, int due_threshold,
+                            size_t smem, cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_sample(const SysDev *d_sys, const int2 *d_work, int n_work,
+                              int *d_work_ctr, int precision, uint64_t seed,
+                              int n_first, int n_samples, int sweeps_between,
+                              int sample_base, int grid, size_t smem,
+                              cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker,
+                                   int precision, int n_moves, const int *d_moves,
+                                   double *d_out, size_t smem, cudaStream_t st,
+                                   long long *n_launch);
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int *acc_len);
+size_t vmc_init_smem(int N, int Ns);
+int vmc_sample_occupancy(int precision, size_t smem);
+cudaError_t vmc_walker_set_smem_limits(size_t smem_sample64, size_t smem_sample32,
+                                       size_t smem_init);
+
+// SR (vmc_sr.cu)
+struct SrWork {
+  int Np, rows, ldO;
+  int precision;               // layout of O: 0 double, 1 float
+  const void *O;
+  const double *E;
+  double *obar;                // [Np]
+  double *ebar;                // [1] (+ scratch)
+  double *S;                   // [Np*Np]
+  double *g;                   // [Np]
+  double *diagS;               // [Np]
+  double *x, *r, *p, *w, *t;   // CG vectors (t: [rows])
+  double *scal;                // device scalars
+  int *info;                   // device status
+  double *part;                // column-reduction partials [ceil(rows/2048) * Np]
+};
+cudaError_t vmc_sr_means(const SrWork &w, cudaStream_t st, long long *nl);
+cudaError_t vmc_sr_build_S(const SrWork &w, double shift_rel, double shift_abs,
+                           cudaStream_t st, long long *nl);
+cudaError_t vmc_sr_build_g(const SrWork &w, cudaStream_t st, long long *nl);
+cudaError_t vmc_sr_diag(const SrWork &w, cudaStream_t st, long long *nl);
+int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl);
+int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
+                    int kmax, int *iters, cudaStream_t st, long long *nl);
+cudaError_t vmc_sr_update_params(double *params, const double *x, double dtau, int Np,
+                                 cudaStream_t st, long long *nl);
+cudaError_t vmc_dot_host(const double *a, const double *b, int n, double *out_host,
+                         double *d_scratch, cudaStream_t st, long long *nl);

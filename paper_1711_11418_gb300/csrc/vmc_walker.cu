@@ -1,0 +1,992 @@
+// Walker kernels: parameter expansion, from-scratch inverse (FP64 Gauss-Jordan),
+// the Metropolis sweep with fast Pfaffian-ratio updates, and the per-sample
+// measurement of E_loc and the O_k row.
+//
+// Wave function (mVMC paper, Sec. 2.2): psi(x) = P_G P_J <x|phi_AP-Pf>.  For
+// S^z = 0 and the anti-parallel form (Eq. AP-Pf) the Ne x Ne skew matrix X of
+// Sec. 2.2.1 is block off-diagonal, X = [[0, M], [-M^T, 0]] with
+// M_nm = f(r_n,up, r_m,dn), so Pf X = (-1)^{N(N-1)/2} det M and
+// X^-1 = [[0, -M^-T], [M^-1, 0]].  Each walker keeps M^-1 (N x N).
+//
+// Fast updates (Sec. 2.1.2, "Sherman-Morrison-type update"): a hop of up
+// electron n replaces row n of M, a hop of down electron m replaces column m;
+// an exchange replaces both (rank-2).  Ratios are det M'/det M from the
+// matrix-determinant lemma; the inverse follows by Sherman-Morrison
+// (rank 1) or Woodbury (rank 2).
+#include "vmc_common.cuh"
+
+#include <math.h>
+
+namespace {
+
+constexpr int NT = VMC_NT;
+constexpr int NWARP = NT / 32;
+
+template <typename T> __device__ __forceinline__ const T *ftab(const SysDev &s);
+template <> __device__ __forceinline__ const double *ftab<double>(const SysDev &s) { return s.f64; }
+template <> __device__ __forceinline__ const float *ftab<float>(const SysDev &s) { return s.f32; }
+template <typename T> __device__ __forceinline__ const T *fTtab(const SysDev &s);
+template <> __device__ __forceinline__ const double *fTtab<double>(const SysDev &s) { return s.fT64; }
+template <> __device__ __forceinline__ const float *fTtab<float>(const SysDev &s) { return s.fT32; }
+
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Global-memory stride of one walker's M^-1 (bytes, 128-aligned).
+__host__ __device__ __forceinline__ size_t minv_bytes(int N, int ldm, int esize) {
+  return align_up((size_t)N * ldm * esize, 128);
+}
+
+// Shared-memory carve-up of one walker.
+template <typename T>
+struct WSmem {
+  T *minv;      // N x ldm
+  T *vec;       // 8 x VMC_MAX_N: block vectors vA..vD, or 2 per warp
+  T *acc;       // O-row accumulator (acc_len)
+  T *red;       // 2 buffers x 8
+  T *bc;        // 2 broadcast scalars (double-buffered like red)
+  double *jf;   // Ns
+  double *dred; // 2 buffers x 8 (double reductions)
+  int *ele;     // Ne
+  int *occ;     // 2 Ns
+  int *ilist;   // Ns
+  int *misc;    // 8
+};
+
+template <typename T>
+__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, unsigned char *base, WSmem<T> *sm) {
+  const int ldm = (N % 2) ? N : N + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return o; };
+  const size_t o_minv = take(minv_bytes(N, ldm, sizeof(T)));
+  const size_t o_vec = take(sizeof(T) * 8 * VMC_MAX_N);
+  const size_t o_acc = take(sizeof(T) * (size_t)acc_len);
+  const size_t o_red = take(sizeof(T) * 16);
+  const size_t o_bc = take(sizeof(T) * 2);
+  const size_t o_jf = take(sizeof(double) * Ns);
+  const size_t o_dred = take(sizeof(double) * 16);
+  const size_t o_ele = take(sizeof(int) * 2 * N);
+  const size_t o_occ = take(sizeof(int) * 2 * Ns);
+  const size_t o_il = take(sizeof(int) * Ns);
+  const size_t o_misc = take(sizeof(int) * 8);
+  if (sm) {
+    sm->minv = (T *)(base + o_minv);
+    sm->vec = (T *)(base + o_vec);
+    sm->acc = (T *)(base + o_acc);
+    sm->red = (T *)(base + o_red);
+    sm->bc = (T *)(base + o_bc);
+    sm->jf = (double *)(base + o_jf);
+    sm->dred = (double *)(base + o_dred);
+    sm->ele = (int *)(base + o_ele);
+    sm->occ = (int *)(base + o_occ);
+    sm->ilist = (int *)(base + o_il);
+    sm->misc = (int *)(base + o_misc);
+  }
+  return off;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);   // lane 0's value: identical in every lane
+}
+
+// Block sum with a double-buffered partial array: every thread returns the
+// same value (same partials, same order).  One __syncthreads.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red, int &buf) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) red[buf * 8 + warp] = v;
+  __syncthreads();
+  const T *r = red + buf * 8;
+  T s = r[0];
+#pragma unroll
+  for (int k = 1; k < NWARP; ++k) s += r[k];
+  buf ^= 1;
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ void block_sum2(T a, T b, T *red, int &buf, T &A, T &B) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[buf * 8 + warp] = a;
+    red[buf * 8 + 4 + warp] = b;
+  }
+  __syncthreads();
+  const T *r = red + buf * 8;
+  A = r[0];
+  B = r[4];
+#pragma unroll
+  for (int k = 1; k < NWARP; ++k) {
+    A += r[k];
+    B += r[4 + k];
+  }
+  buf ^= 1;
+}
+
+// log of the correlation-factor ratio P(x')/P(x) for a hop of a spin-s
+// electron from site r to site t (Sec. 2.2.3): Gutzwiller g_t n_t,-s - g_r n_r,-s
+// and Jastrow h_t - h_r - v_rt with h_i = sum_{j != i} v_ij (n_j - 1).
+__device__ __forceinline__ double corr_hop(const SysDev &S, const int *occ, const double *jf,
+                                           int s, int r, int t) {
+  const int Ns = S.Ns;
+  const int o = (1 - s) * Ns;
+  double d = jf[t] - jf[r] - S.vmat[(size_t)r * Ns + t];
+  d += (occ[o + t] >= 0 ? S.gsite[t] : 0.0) - (occ[o + r] >= 0 ? S.gsite[r] : 0.0);
+  return d;
+}
+
+template <typename T> __device__ __forceinline__ T corr_factor(double dlog);
+template <> __device__ __forceinline__ double corr_factor<double>(double dlog) { return exp(dlog); }
+template <> __device__ __forceinline__ float corr_factor<float>(double dlog) { return expf((float)dlog); }
+
+// ---------------------------------------------------------------------------
+// Pfaffian ratios (block-wide; every thread returns the same value)
+// ---------------------------------------------------------------------------
+// Hop of electron e to empty site t: det M'/det M = sum_l R_l (M^-1)_{l n}
+// (up electron n = e, new row R_l = f(t, r_l,dn)) or
+// sum_k (M^-1)_{m k} C_k (down electron m = e - N, new column C_k = f(r_k,up, t)).
+// fval receives this thread's entry of the new row/column.
+template <typename T>
+__device__ __forceinline__ T hop_pf_ratio(const SysDev &S, const WSmem<T> &sm, int e, int t,
+                                          T &fval, int &buf) {
+  const int N = S.N, Ns = S.Ns, tid = threadIdx.x;
+  T prod = (T)0;
+  fval = (T)0;
+  if (tid < N) {
+    if (e < N) {
+      fval = ftab<T>(S)[(size_t)t * Ns + sm.ele[N + tid]];
+      prod = sm.minv[tid * S.ldm + e] * fval;
+    } else {
+      fval = fTtab<T>(S)[(size_t)t * Ns + sm.ele[tid]];
+      prod = sm.minv[(e - N) * S.ldm + tid] * fval;
+    }
+  }
+  return block_sum(prod, sm.red, buf);
+}
+
+// Exchange of up electron n (site i) with down electron m (site j):
+// M' = M + e_n a^T + b e_m^T with a = R - M[n,:] (new row R_l = f(j, r_l,dn),
+// R_m = f(j, i)) and b = C - M[:,m] with b_n = 0 (new column
+// C_k = f(r'_k,up, i), r'_n = j).  det M'/det M = det(I_2 + V^T M^-1 U),
+// U = [e_n, b], V = [a, e_m]:
+//   K11 = (R^T M^-1)_n, K12 = sum_{k != n} (R^T M^-1)_k b_k,
+//   K21 = (M^-1)_{mn},  K22 = sum_k (M^-1)_{mk} C'_k (C'_n = M_nm).
+// On return vB holds w = R^T M^-1, vC holds C, K[0..3] the 2x2 matrix.
+template <typename T>
+__device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m, int i, int j,
+                               int &buf, T *K) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
+  const T *F = ftab<T>(S);
+  const T *FT = fTtab<T>(S);
+  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N;
+  if (tid < N) vA[tid] = (tid == m) ? F[(size_t)j * Ns + i] : F[(size_t)j * Ns + sm.ele[N + tid]];
+  __syncthreads();
+  T a22 = (T)0, a12 = (T)0;
+  if (tid < N) {
+    T w = (T)0;
+    for (int l = 0; l < N; ++l) w += vA[l] * sm.minv[l * ldm + tid];
+    vB[tid] = w;
+    const int site = (tid == n) ? j : sm.ele[tid];
+    const T c = FT[(size_t)i * Ns + site];
+    const T mkm = FT[(size_t)j * Ns + sm.ele[tid]];
+    vC[tid] = c;
+    const T mrow = sm.minv[m * ldm + tid];
+    if (tid == n) {
+      a22 = mrow * mkm;
+    } else {
+      a22 = mrow * c;
+      a12 = w * (c - mkm);
+    }
+  }
+  T A22, A12;
+  block_sum2(a22, a12, sm.red, buf, A22, A12);
+  const T A11 = vB[n];
+  const T A21 = sm.minv[m * ldm + n];
+  K[0] = A11;
+  K[1] = A12;
+  K[2] = A21;
+  K[3] = A22;
+  return A11 * A22 - A12 * A21;
+}
+
+// ---------------------------------------------------------------------------
+// Inverse updates on acceptance
+// ---------------------------------------------------------------------------
+// Row n replaced by the row in vA (up-electron hop): with w = R^T M^-1,
+// M'^-1 = M^-1 - M^-1[:,n] (w - e_n)^T / w_n.
+template <typename T>
+__device__ void row_update(const SysDev &S, const WSmem<T> &sm, int n) {
+  const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
+  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N;
+  if (tid < N) {
+    T w = (T)0;
+    for (int l = 0; l < N; ++l) w += vA[l] * sm.minv[l * ldm + tid];
+    vB[tid] = w;
+  }
+  __syncthreads();
+  const T inv = (T)1 / vB[n];
+  if (tid < N) {
+    T *row = sm.minv + tid * ldm;
+    const T c = row[n] * inv;
+    for (int k = 0; k < N; ++k) row[k] -= c * vB[k];
+    row[n] = c;
+  }
+  __syncthreads();
+}
+
+// Column m replaced by the column in vA (down-electron hop): with v = M^-1 C,
+// M'^-1 = M^-1 - (v - e_m) M^-1[m,:] / v_m.
+template <typename T>
+__device__ void col_update(const SysDev &S, const WSmem<T> &sm, int m) {
+  const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
+  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N;
+  if (tid < N) {
+    const T *row = sm.minv + tid * ldm;
+    T v = (T)0;
+    for (int k = 0; k < N; ++k) v += row[k] * vA[k];
+    vB[tid] = v;
+    vC[tid] = sm.minv[m * ldm + tid];
+  }
+  __syncthreads();
+  const T inv = (T)1 / vB[m];
+  if (tid < N) {
+    T *row = sm.minv + tid * ldm;
+    if (tid == m) {
+      for (int k = 0; k < N; ++k) row[k] = vC[k] * inv;
+    } else {
+      const T c = vB[tid] * inv;
+      for (int k = 0; k < N; ++k) row[k] -= c * vC[k];
+    }
+  }
+  __syncthreads();
+}
+
+// Rank-2 (Woodbury) update after an accepted exchange; vB = w, vC = C and K
+// from exchange_pf_ratio.  M'^-1 = M^-1 - [p q] K^-1 [w - e_n; z] with
+// p = M^-1[:,n], q = M^-1 b, z = M^-1[m,:].
+template <typename T>
+__device__ void exchange_update(const SysDev &S, const WSmem<T> &sm, int n, int m, int j,
+                                const T *K, T det) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
+  const T *FT = fTtab<T>(S);
+  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N,
+    *vD = sm.vec + 3 * VMC_MAX_N;
+  if (tid < N) {
+    vA[tid] = (tid == n) ? (T)0 : vC[tid] - FT[(size_t)j * Ns + sm.ele[tid]];
+    vD[tid] = sm.minv[m * ldm + tid];
+  }
+  __syncthreads();
+  if (tid < N) {
+    T *row = sm.minv + tid * ldm;
+    T q = (T)0;
+    for (int k = 0; k < N; ++k) q += row[k] * vA[k];
+    const T p = row[n];
+    const T inv = (T)1 / det;
+    const T c1 = (p * K[3] - q * K[2]) * inv;
+    const T c2 = (q * K[0] - p * K[1]) * inv;
+    for (int k = 0; k < N; ++k) row[k] -= c1 * vB[k] + c2 * vD[k];
+    row[n] += c1;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// One Metropolis proposal (Sec. 2.1.2).  Every thread runs it; decisions are
+// uniform across the block.
+// ---------------------------------------------------------------------------
+struct MoveCounts {
+  long long hop_t = 0, ex_t = 0, hop_a = 0, ex_a = 0;
+  long long meas_hop = 0, meas_ex = 0, samples = 0;
+};
+
+template <typename T>
+__device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t walker,
+                        unsigned long long &ctr, MoveCounts &mc, int &acc_since, int &buf) {
+  const int N = S.N, Ns = S.Ns, Ne = S.Ne, tid = threadIdx.x;
+  const uint4 r = vmc_philox(make_uint4((uint32_t)ctr, (uint32_t)(ctr >> 32), walker,
+                                        (uint32_t)S.sys_index), key);
+  ctr++;
+  const T u = (T)(r.w >> 8) * (T)(1.0 / 16777216.0);
+  if ((unsigned long long)r.x < S.pex) {
+    const int n = vmc_mulhi(r.y, N);
+    const int m = N + vmc_mulhi(r.z, N);
+    const int i = sm.ele[n], j = sm.ele[m];
+    if (i == j || sm.occ[Ns + i] >= 0 || sm.occ[j] >= 0) return;
+    mc.ex_t++;
+    T K[4];
+    const T ratio = exchange_pf_ratio(S, sm, n, m - N, i, j, buf, K);
+    if (u < ratio * ratio) {
+      exchange_update(S, sm, n, m - N, j, K, ratio);
+      if (tid == 0) {
+        sm.ele[n] = j;
+        sm.ele[m] = i;
+        sm.occ[i] = -1;
+        sm.occ[j] = n;
+        sm.occ[Ns + j] = -1;
+        sm.occ[Ns + i] = m;
+      }
+      __syncthreads();
+      mc.ex_a++;
+      acc_since++;
+    }
+    return;
+  }
+  const int e = vmc_mulhi(r.y, Ne);
+  const int t = vmc_mulhi(r.z, Ns);
+  const int s = (e >= N) ? 1 : 0;
+  if (sm.occ[s * Ns + t] >= 0) return;
+  if (S.local_spin && sm.occ[(1 - s) * Ns + t] >= 0) return;
+  const int rs = sm.ele[e];
+  mc.hop_t++;
+  // P(x')/P(x): one thread evaluates it; the barrier inside hop_pf_ratio publishes it.
+  const int slot = buf;
+  if (tid == 0) sm.bc[slot] = corr_factor<T>(corr_hop(S, sm.occ, sm.jf, s, rs, t));
+  T fval;
+  const T rpf = hop_pf_ratio(S, sm, e, t, fval, buf);
+  const T ratio = rpf * sm.bc[slot];
+  if (!(u < ratio * ratio)) return;
+  if (tid < N) sm.vec[tid] = fval;
+  __syncthreads();
+  if (s == 0) row_update(S, sm, e);
+  else col_update(S, sm, e - N);
+  // Jastrow field: h_x += v_{x t} - v_{x r}.
+  for (int x = tid; x < Ns; x += NT)
+    sm.jf[x] += S.vmat[(size_t)t * Ns + x] - S.vmat[(size_t)rs * Ns + x];
+  if (tid == 0) {
+    sm.ele[e] = t;
+    sm.occ[s * Ns + rs] = -1;
+    sm.occ[s * Ns + t] = e;
+  }
+  __syncthreads();
+  mc.hop_a++;
+  acc_since++;
+}
+
+// ---------------------------------------------------------------------------
+// Measurement: E_loc (Eq. MC with A = H) and the O_k row (Sec. 2.3.1)
+// ---------------------------------------------------------------------------
+// Warp-level exchange ratio (same formula as exchange_pf_ratio) for the
+// Heisenberg S+S- terms of E_loc.  R, Wp: per-warp scratch vectors.
+template <typename T>
+__device__ T exchange_pf_ratio_warp(const SysDev &S, const WSmem<T> &sm, int n, int m, int i,
+                                    int j, T *R, T *Wp) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, lane = threadIdx.x & 31;
+  const T *F = ftab<T>(S);
+  const T *FT = fTtab<T>(S);
+  for (int l = lane; l < N; l += 32)
+    R[l] = (l == m) ? F[(size_t)j * Ns + i] : F[(size_t)j * Ns + sm.ele[N + l]];
+  __syncwarp();
+  T a22 = (T)0, a12 = (T)0;
+  for (int k = lane; k < N; k += 32) {
+    T w = (T)0;
+    for (int l = 0; l < N; ++l) w += R[l] * sm.minv[l * ldm + k];
+    Wp[k] = w;
+    const int site = (k == n) ? j : sm.ele[k];
+    const T c = FT[(size_t)i * Ns + site];
+    const T mkm = FT[(size_t)j * Ns + sm.ele[k]];
+    const T mrow = sm.minv[m * ldm + k];
+    if (k == n) {
+      a22 += mrow * mkm;
+    } else {
+      a22 += mrow * c;
+      a12 += w * (c - mkm);
+    }
+  }
+  a22 = warp_sum(a22);
+  a12 = warp_sum(a12);
+  __syncwarp();
+  const T r = Wp[n] * a22 - a12 * sm.minv[m * ldm + n];
+  __syncwarp();
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ void acc_add(T *p, T v) { atomicAdd(p, v); }
+
+template <typename T>
+__device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int &buf,
+                        MoveCounts &mc) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const T *F = ftab<T>(S);
+  const T *FT = fTtab<T>(S);
+  // --- diagonal terms
+  double ed = 0.0;
+  for (int i = tid; i < Ns; i += NT) {
+    const int up = sm.occ[i] >= 0, dn = sm.occ[Ns + i] >= 0;
+    ed += S.U[i] * (double)(up * dn);
+  }
+  for (int k = tid; k < S.n_V; k += NT) {
+    const int a = S.V_i[k], b = S.V_j[k];
+    const int na = (sm.occ[a] >= 0) + (sm.occ[Ns + a] >= 0);
+    const int nb = (sm.occ[b] >= 0) + (sm.occ[Ns + b] >= 0);
+    ed += S.V_val[k] * (double)(na * nb);
+  }
+  for (int k = tid; k < S.n_J; k += NT) {
+    const int a = S.J_i[k], b = S.J_j[k];
+    const double sa = 0.5 * ((sm.occ[a] >= 0) - (sm.occ[Ns + a] >= 0));
+    const double sb = 0.5 * ((sm.occ[b] >= 0) - (sm.occ[Ns + b] >= 0));
+    ed += S.J_val[k] * sa * sb;
+  }
+  // --- hopping: one thread per (term, spin); each valid one is a dot product
+  // of the new row (column) of M with a column (row) of M^-1 (Green-function
+  // ratio), times the correlation-factor ratio.
+  double eo = 0.0;
+  for (int q = tid; q < 2 * S.n_hop; q += NT) {
+    const int k = q >> 1, s = q & 1;
+    const int i = S.hop_i[k], j = S.hop_j[k];
+    const int e = sm.occ[s * Ns + j];
+    if (e < 0 || sm.occ[s * Ns + i] >= 0) continue;
+    T a0 = (T)0, a1 = (T)0;
+    if (s == 0) {
+      const T *Fi = F + (size_t)i * Ns;
+      int m = 0;
+      for (; m + 1 < N; m += 2) {
+        a0 += sm.minv[m * ldm + e] * Fi[sm.ele[N + m]];
+        a1 += sm.minv[(m + 1) * ldm + e] * Fi[sm.ele[N + m + 1]];
+      }
+      if (m < N) a0 += sm.minv[m * ldm + e] * Fi[sm.ele[N + m]];
+    } else {
+      const T *Fi = FT + (size_t)i * Ns;
+      const T *row = sm.minv + (e - N) * ldm;
+      int n = 0;
+      for (; n + 1 < N; n += 2) {
+        a0 += row[n] * Fi[sm.ele[n]];
+        a1 += row[n + 1] * Fi[sm.ele[n + 1]];
+      }
+      if (n < N) a0 += row[n] * Fi[sm.ele[n]];
+    }
+    eo += -S.hop_t[k] * (double)(a0 + a1) * (double)corr_factor<T>(corr_hop(S, sm.occ, sm.jf, s, j, i));
+    mc.meas_hop++;
+  }
+  // --- Heisenberg exchange: J/2 (S+_a S-_b + S-_a S+_b) = -J/2 x (labelled swap ratio)
+  T *R = sm.vec + (2 * warp) * VMC_MAX_N;
+  T *Wp = sm.vec + (2 * warp + 1) * VMC_MAX_N;
+  __syncthreads();   // vec area switches from proposal use to per-warp use
+  for (int k = warp; k < S.n_J; k += NWARP) {
+    int a = S.J_i[k], b = S.J_j[k];
+    int nu = sm.occ[a], md = sm.occ[Ns + b];
+    bool ok = nu >= 0 && md >= 0 && sm.occ[Ns + a] < 0 && sm.occ[b] < 0;
+    if (!ok) {
+      const int a2 = b, b2 = a;
+      nu = sm.occ[a2];
+      md = sm.occ[Ns + b2];
+      ok = nu >= 0 && md >= 0 && sm.occ[Ns + a2] < 0 && sm.occ[b2] < 0;
+      a = a2;
+      b = b2;
+    }
+    if (!ok || a == b) continue;
+    const T r = exchange_pf_ratio_warp(S, sm, nu, md - N, a, b, R, Wp);
+    if (lane == 0) {
+      eo += -0.5 * S.J_val[k] * (double)r;
+      mc.meas_ex++;
+    }
+  }
+  const double etot = block_sum(ed + eo, sm.dred, buf);
+  if (tid == 0) S.E[(size_t)w * S.n_samples + row] = etot;
+
+  // --- O_k row
+  T *Orow = (T *)S.O + ((size_t)w * S.n_samples + row) * S.ldO;
+  const bool sh = S.acc_len > 0;
+  T *acc = sh ? sm.acc : Orow;
+  const int len = sh ? S.acc_len : S.ldO;
+  for (int k = tid; k < len; k += NT) acc[k] = (T)0;
+  if (tid == 0) sm.misc[0] = 0;
+  __syncthreads();
+  if (S.n_g > 0) {
+    for (int i = tid; i < Ns; i += NT)
+      if (sm.occ[i] >= 0 && sm.occ[Ns + i] >= 0 && S.g_idx[i] >= 0) acc_add(acc + S.g_idx[i], (T)1);
+  }
+  if (S.n_v > 0) {
+    for (int i = tid; i < Ns; i += NT) {
+      const int mi = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
+      if (mi != 0) sm.ilist[atomicAdd(&sm.misc[0], 1)] = i;
+    }
+    __syncthreads();
+    const int K = sm.misc[0];
+    for (int p = tid; p < K * K; p += NT) {
+      const int a = p / K, b = p - a * K;
+      if (a >= b) continue;
+      const int i = sm.ilist[a], j = sm.ilist[b];
+      const int cls = S.v_idx[(size_t)i * Ns + j];
+      if (cls < 0) continue;
+      const int mi = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
+      const int mj = (sm.occ[j] >= 0) + (sm.occ[Ns + j] >= 0) - 1;
+      acc_add(acc + S.n_g + cls, (T)(mi * mj));
+    }
+  }
+  // Pair orbital: d ln Pf / d f_ab = (M^-1)_{mn} for a = r_n,up, b = r_m,dn
+  // (= -(X^-1)_{n, N+m}, Eq. DiffPf / Appendix C), times the class sign.
+  const int base = S.n_g + S.n_v;
+  for (int p = tid; p < N * N; p += NT) {
+    const int m = p / N, n = p - m * N;
+    const size_t ab = (size_t)sm.ele[n] * Ns + sm.ele[N + m];
+    const int cls = S.f_idx[ab];
+    if (cls < 0) continue;
+    const T v = sm.minv[m * ldm + n];
+    acc_add(acc + base + cls, S.f_sign[ab] > 0 ? v : -v);
+  }
+  __syncthreads();
+  if (sh)
+    for (int k = tid; k < S.ldO; k += NT) Orow[k] = (k < S.acc_len) ? acc[k] : (T)0;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// From-scratch inverse: FP64 Gauss-Jordan with partial pivoting, in place on
+// an N x N row-major matrix (row stride lda) in shared or global memory.
+// Column-parallel elimination (coalesced / bank-conflict free).
+// ---------------------------------------------------------------------------
+struct GJShared {
+  double val[NWARP];
+  double amax[NWARP];
+  int idx[NWARP];
+  int piv;
+  int bad;
+  int sign;
+  double logdet;
+  double pmin, pmax;   // smallest / largest |pivot|
+};
+
+__device__ __noinline__ void gj_invert(double *A, int lda, int N, int *perm, GJShared &g) {
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    g.logdet = 0.0;
+    g.sign = 1;
+    g.bad = 0;
+    g.pmin = 1e300;
+    g.pmax = 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    double v = -1.0;
+    int vi = N;
+    for (int i = k + tid; i < N; i += NT) {
+      const double a = fabs(A[(size_t)i * lda + k]);
+      if (a > v) {
+        v = a;
+        vi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+      if (ov > v || (ov == v && oi < vi)) {
+        v = ov;
+        vi = oi;
+      }
+    }
+    if ((tid & 31) == 0) {
+      g.val[tid >> 5] = v;
+      g.idx[tid >> 5] = vi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = g.val[0];
+      int bi = g.idx[0];
+      for (int q = 1; q < NWARP; ++q)
+        if (g.val[q] > bv || (g.val[q] == bv && g.idx[q] < bi)) {
+          bv = g.val[q];
+          bi = g.idx[q];
+        }
+      if (!(bv > 0.0) || bi >= N) {
+        g.bad = 1;
+        bi = k;
+      }
+      g.piv = bi;
+      perm[k] = bi;
+    }
+    __syncthreads();
+    if (g.bad) return;
+    const int p = g.piv;
+    if (p != k) {
+      for (int c = tid; c < N; c += NT) {
+        const double t0 = A[(size_t)k * lda + c];
+        A[(size_t)k * lda + c] = A[(size_t)p * lda + c];
+        A[(size_t)p * lda + c] = t0;
+      }
+      __syncthreads();
+    }
+    const double piv = A[(size_t)k * lda + k];
+    const double ipiv = 1.0 / piv;
+    if (tid == 0) {
+      g.logdet += log(fabs(piv));
+      g.pmin = fmin(g.pmin, fabs(piv));
+      g.pmax = fmax(g.pmax, fabs(piv));
+      if ((piv < 0.0) != (p != k)) g.sign = -g.sign;
+    }
+    __syncthreads();
+    for (int c = tid; c < N; c += NT)
+      if (c != k) A[(size_t)k * lda + c] *= ipiv;
+    __syncthreads();
+    for (int c = tid; c < N; c += NT) {
+      if (c == k) continue;
+      const double rkc = A[(size_t)k * lda + c];
+      for (int i = 0; i < N; ++i)
+        if (i != k) A[(size_t)i * lda + c] -= A[(size_t)i * lda + k] * rkc;
+    }
+    __syncthreads();
+    for (int i = tid; i < N; i += NT)
+      A[(size_t)i * lda + k] = (i == k) ? ipiv : -A[(size_t)i * lda + k] * ipiv;
+    __syncthreads();
+  }
+  for (int k = N - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int r = tid; r < N; r += NT) {
+        const double t0 = A[(size_t)r * lda + k];
+        A[(size_t)r * lda + k] = A[(size_t)r * lda + p];
+        A[(size_t)r * lda + p] = t0;
+      }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+__device__ void load_sys(SysDev *dst, const SysDev *src) {
+  const int nw = sizeof(SysDev) / sizeof(int);
+  const int *s = (const int *)src;
+  int *d = (int *)dst;
+  for (int k = threadIdx.x; k < nw; k += blockDim.x) d[k] = s[k];
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2 *work, int n_work,
+                                               int *work_ctr, uint2 key, int n_first, int n_samples,
+                                               int sweeps_between, int sample_base) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SysDev S;
+  __shared__ int s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_work) break;
+    const int2 wk = work[item];
+    load_sys(&S, systems + wk.x);
+    const int w = wk.y;
+    const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
+    WSmem<T> sm;
+    walker_layout<T>(N, Ns, S.acc_len, smem_raw, &sm);
+    // --- load the walker (M^-1 block, configuration, Jastrow field)
+    {
+      const size_t nb = minv_bytes(N, ldm, sizeof(T));
+      const int4 *src = (const int4 *)((const unsigned char *)S.minv + (size_t)w * nb);
+      int4 *dst = (int4 *)sm.minv;
+      for (size_t k = tid; k < nb / 16; k += NT) dst[k] = src[k];
+      for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
+      for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
+      for (int k = tid; k < Ns; k += NT) sm.jf[k] = S.jf[(size_t)w * Ns + k];
+    }
+    unsigned long long ctr = S.ctr[w];
+    MoveCounts mc;
+    int acc_since = S.acc_since[w];
+    int buf = 0;
+    const uint32_t key_w = (uint32_t)w;
+    __syncthreads();
+    const long long props_first = (long long)n_first * Ne;
+    for (long long p = 0; p < props_first; ++p) propose(S, sm, key, key_w, ctr, mc, acc_since, buf);
+    for (int s = 0; s < n_samples; ++s) {
+      const long long props = (long long)sweeps_between * Ne;
+      for (long long p = 0; p < props; ++p) propose(S, sm, key, key_w, ctr, mc, acc_since, buf);
+      __syncthreads();
+      measure(S, sm, w, sample_base + s, buf, mc);
+      mc.samples++;
+    }
+    if (mc.meas_hop) atomicAdd((unsigned long long *)&S.cnt[8 * w + 4], (unsigned long long)mc.meas_hop);
+    if (mc.meas_ex) atomicAdd((unsigned long long *)&S.cnt[8 * w + 5], (unsigned long long)mc.meas_ex);
+    __syncthreads();
+    // --- store the walker back
+    {
+      const size_t nb = minv_bytes(N, ldm, sizeof(T));
+      int4 *dst = (int4 *)((unsigned char *)S.minv + (size_t)w * nb);
+      const int4 *src = (const int4 *)sm.minv;
+      for (size_t k = tid; k < nb / 16; k += NT) dst[k] = src[k];
+      for (int k = tid; k < Ne; k += NT) S.ele[(size_t)w * Ne + k] = sm.ele[k];
+      for (int k = tid; k < 2 * Ns; k += NT) S.occ[(size_t)w * 2 * Ns + k] = sm.occ[k];
+      for (int k = tid; k < Ns; k += NT) S.jf[(size_t)w * Ns + k] = sm.jf[k];
+      if (tid == 0) {
+        const long long total = props_first + (long long)n_samples * sweeps_between * Ne;
+        S.ctr[w] = ctr;
+        S.n_prop[w] += total;
+        S.n_acc[w] += mc.hop_a + mc.ex_a;
+        S.cnt[8 * w + 0] += mc.hop_t;
+        S.cnt[8 * w + 1] += mc.ex_t;
+        S.cnt[8 * w + 2] += mc.hop_a;
+        S.cnt[8 * w + 3] += mc.ex_a;
+        S.cnt[8 * w + 6] += mc.samples;
+        S.acc_since[w] = acc_since;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Expand the parameter vector into dense tables (f, f^T in FP64 and FP32, v, g).
+__global__ void k_expand(SysDev S) {
+  const int Ns = S.Ns;
+  const size_t n2 = (size_t)Ns * Ns;
+  const int base = S.n_g + S.n_v;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n2;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / Ns), j = (int)(q - (size_t)i * Ns);
+    const int c = S.f_idx[q];
+    const double f = (c >= 0) ? S.f_sign[q] * S.params[base + c] : 0.0;
+    S.f64[q] = f;
+    S.fT64[(size_t)j * Ns + i] = f;
+    S.f32[q] = (float)f;
+    S.fT32[(size_t)j * Ns + i] = (float)f;
+    const int vc = S.v_idx[q];
+    S.vmat[q] = (vc >= 0 && i != j) ? S.params[S.n_g + vc] : 0.0;
+    if (q < (size_t)Ns) {
+      const int gc = S.g_idx[q];
+      S.gsite[q] = (gc >= 0) ? S.params[gc] : 0.0;
+    }
+  }
+}
+
+// From-scratch inverse of M (FP64 Gauss-Jordan with partial pivoting, in
+// place in shared memory), log|det M| and its sign, Jastrow field and
+// occupation table.  With only_due, only walkers whose accepted-move count
+// since the last inverse reached due_threshold are rebuilt, and the drift
+// max|M^-1_updated - M^-1_fresh| / max|M^-1_fresh| is recorded.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *work, int n_work,
+                                             int only_due, int due_threshold) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SysDev S;
+  __shared__ GJShared g;
+  for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
+    __syncthreads();
+    const int2 wk = work[item];
+    load_sys(&S, systems + wk.x);
+    const int w = wk.y;
+    if (only_due && S.acc_since[w] < due_threshold) continue;
+    const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
+    double *A = (double *)smem_raw;                 // N x ldm
+    int *ele = (int *)(A + (size_t)N * ldm);        // Ne
+    int *perm = ele + Ne;                            // N
+    for (int k = tid; k < Ne; k += NT) ele[k] = S.ele[(size_t)w * Ne + k];
+    __syncthreads();
+    for (int q = tid; q < N * N; q += NT) {
+      const int n = q / N, m = q - n * N;
+      A[n * ldm + m] = S.f64[(size_t)ele[n] * Ns + ele[N + m]];
+    }
+    __syncthreads();
+    gj_invert(A, ldm, N, perm, g);
+    const size_t nb = minv_bytes(N, ldm, sizeof(T));
+    T *dst = (T *)((unsigned char *)S.minv + (size_t)w * nb);
+    if (!g.bad) {
+      if (only_due) {
+        double dmax = 0.0, amax = 0.0;
+        for (int q = tid; q < N * N; q += NT) {
+          const int r = q / N, c = q - r * N;
+          const double fresh = A[r * ldm + c];
+          dmax = fmax(dmax, fabs((double)dst[r * ldm + c] - fresh));
+          amax = fmax(amax, fabs(fresh));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+          amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        }
+        if ((tid & 31) == 0) {
+          g.val[tid >> 5] = dmax;
+          g.amax[tid >> 5] = amax;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double d = 0.0, a = 0.0;
+          for (int q = 0; q < NWARP; ++q) {
+            d = fmax(d, g.val[q]);
+            a = fmax(a, g.amax[q]);
+          }
+          S.drift[w] = fmax(S.drift[w], (a > 0.0) ? d / a : d);
+        }
+        __syncthreads();
+      }
+      for (int q = tid; q < N * ldm; q += NT) dst[q] = (T)A[q];
+    }
+    if (!only_due) {
+      for (int k = tid; k < 2 * Ns; k += NT) S.occ[(size_t)w * 2 * Ns + k] = -1;
+      __syncthreads();
+      for (int k = tid; k < Ne; k += NT) {
+        const int s = (k >= N) ? 1 : 0;
+        S.occ[(size_t)w * 2 * Ns + s * Ns + ele[k]] = k;
+      }
+      __syncthreads();
+      // Jastrow field h_i = sum_{j != i} v_ij (n_j - 1)
+      const int *occ = S.occ + (size_t)w * 2 * Ns;
+      for (int i = tid; i < Ns; i += NT) {
+        double h = 0.0;
+        for (int j = 0; j < Ns; ++j) {
+          const int mj = (occ[j] >= 0) + (occ[Ns + j] >= 0) - 1;
+          if (mj) h += S.vmat[(size_t)i * Ns + j] * mj;
+        }
+        S.jf[(size_t)w * Ns + i] = h;
+      }
+    }
+    if (tid == 0) {
+      S.acc_since[w] = 0;
+      if (only_due) S.n_rec[w] += 1;
+      if (g.bad) {
+        S.status[w] |= VMC_ST_SINGULAR;
+      } else {
+        S.status[w] &= ~(VMC_ST_SINGULAR | VMC_ST_ILLCOND);
+        if (g.pmin < 1e-12 * g.pmax) S.status[w] |= VMC_ST_ILLCOND;
+        S.logdet[w] = g.logdet;
+        S.detsign[w] = g.sign;
+        if (!isfinite(g.logdet)) S.status[w] |= VMC_ST_NUMERIC;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Ratio check hook: evaluate candidate moves on one walker's current state.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int sys, int w,
+                                                    int n_moves, const int *moves, double *out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
+  WSmem<T> sm;
+  walker_layout<T>(N, Ns, S.acc_len, smem_raw, &sm);
+  const size_t nb = minv_bytes(N, ldm, sizeof(T));
+  const T *src = (const T *)((const unsigned char *)S.minv + (size_t)w * nb);
+  for (int k = tid; k < N * ldm; k += NT) sm.minv[k] = src[k];
+  for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
+  for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
+  for (int k = tid; k < Ns; k += NT) sm.jf[k] = S.jf[(size_t)w * Ns + k];
+  __syncthreads();
+  int buf = 0;
+  for (int q = 0; q < n_moves; ++q) {
+    const int kind = moves[3 * q], a = moves[3 * q + 1], b = moves[3 * q + 2];
+    double res = 0.0;
+    if (kind == 0) {
+      if (a >= 0 && a < Ne && b >= 0 && b < Ns) {
+        const int s = (a >= N) ? 1 : 0;
+        if (sm.occ[s * Ns + b] < 0 && !(S.local_spin && sm.occ[(1 - s) * Ns + b] >= 0)) {
+          T fval;
+          const T rpf = hop_pf_ratio(S, sm, a, b, fval, buf);
+          res = (double)rpf * exp(corr_hop(S, sm.occ, sm.jf, s, sm.ele[a], b));
+        }
+      }
+    } else if (a >= 0 && a < N && b >= N && b < Ne) {
+      const int i = sm.ele[a], j = sm.ele[b];
+      if (i != j && sm.occ[Ns + i] < 0 && sm.occ[j] < 0) {
+        T K[4];
+        res = (double)exchange_pf_ratio(S, sm, a, b - N, i, j, buf, K);
+      }
+    }
+    if (tid == 0) out[q] = res;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host-side launch wrappers
+// ---------------------------------------------------------------------------
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int *acc_len) {
+  const int al = (Np <= VMC_ACC_MAX) ? Np : 0;
+  if (acc_len) *acc_len = al;
+  return precision == 0 ? walker_layout<double>(N, Ns, al, nullptr, nullptr)
+                        : walker_layout<float>(N, Ns, al, nullptr, nullptr);
+}
+
+size_t vmc_init_smem(int N, int Ns) {
+  (void)Ns;
+  const int ldm = (N % 2) ? N : N + 1;
+  return (size_t)N * ldm * sizeof(double) + sizeof(int) * 3 * N + 64;
+}
+
+int vmc_sample_occupancy(int precision, size_t smem) {
+  int nb = 0;
+  if (precision == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<double>, NT, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<float>, NT, smem);
+  return nb;
+}
+
+cudaError_t vmc_walker_set_smem_limits(size_t s64, size_t s32, size_t sinit) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
+  if ((e = cudaFuncSetAttribute(k_eval_ratios<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
+  if ((e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+  if ((e = cudaFuncSetAttribute(k_eval_ratios<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+  if ((e = cudaFuncSetAttribute(k_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sinit))) return e;
+  if ((e = cudaFuncSetAttribute(k_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sinit))) return e;
+  return cudaSuccess;
+}
+
+cudaError_t vmc_launch_expand(const SysDev *h_sys, cudaStream_t st, long long *nl) {
+  const size_t n2 = (size_t)h_sys->Ns * h_sys->Ns;
+  const int grid = (int)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096);
+  k_expand<<<grid, 256, 0, st>>>(*h_sys);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work, int precision,
+                            int only_due, int due_threshold, size_t smem, cudaStream_t st,
+                            long long *nl) {
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  int per = 1;
+  if (precision == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_init<double>, NT, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_init<float>, NT, smem);
+  if (per < 1) per = 1;
+  int grid = nsm * per;
+  if (grid > n_work) grid = n_work;
+  if (grid < 1) return cudaSuccess;
+  if (precision == 0)
+    k_init<double><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, only_due, due_threshold);
+  else
+    k_init<float><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, only_due, due_threshold);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_launch_sample(const SysDev *d_sys, const int2 *d_work, int n_work, int *d_work_ctr,
+                              int precision, uint64_t seed, int n_first, int n_samples,
+                              int sweeps_between, int sample_base, int grid, size_t smem,
+                              cudaStream_t st, long long *nl) {
+  cudaError_t e = cudaMemsetAsync(d_work_ctr, 0, sizeof(int), st);
+  if (e) return e;
+  const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+  if (grid > n_work) grid = n_work;
+  if (grid < 1) return cudaSuccess;
+  if (precision == 0)
+    k_sample<double><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
+                                             n_samples, sweeps_between, sample_base);
+  else
+    k_sample<float><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
+                                            n_samples, sweeps_between, sample_base);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker, int precision,
+                                   int n_moves, const int *d_moves, double *d_out, size_t smem,
+                                   cudaStream_t st, long long *nl) {
+  if (precision == 0)
+    k_eval_ratios<double><<<1, NT, smem, st>>>(d_sys, sys, walker, n_moves, d_moves, d_out);
+  else
+    k_eval_ratios<float><<<1, NT, smem, st>>>(d_sys, sys, walker, n_moves, d_moves, d_out);
+  ++*nl;
+  return cudaGetLastError();
+}
