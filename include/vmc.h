@@ -90,7 +90,7 @@ typedef struct {
   int32_t delay_k;               /* mixed: delayed-update depth (0 = default) */
   int32_t recompute_every;       /* FP64 from-scratch inverse inside the sweep once a
                                     walker has this many accepted moves since the
-                                    last one; 0 = default (mixed: 64, FP64: never),
+                                    last one; 0 = default (mixed: 256, FP64: never),
                                     -1 = never */
   int32_t max_samples;           /* sample rows kept per walker (>= 1) */
   void *stream;                  /* cudaStream_t; NULL = default stream */

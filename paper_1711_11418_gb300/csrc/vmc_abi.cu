@@ -365,6 +365,16 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dupload(c, (double **)&ht, m.hop_t, m.n_hop))) return fail(rc);
     d.hop_i = hi;
     d.hop_j = hj;
+    {
+      // hopping terms grouped by target site (CSR) for the measurement kernel
+      std::vector<int> ptr(Ns + 1, 0), term(m.n_hop);
+      for (int k = 0; k < m.n_hop; ++k) ptr[m.hop_i[k] + 1]++;
+      for (size_t i = 0; i < Ns; ++i) ptr[i + 1] += ptr[i];
+      std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+      for (int k = 0; k < m.n_hop; ++k) term[fill[m.hop_i[k]]++] = k;
+      if ((rc = dupload(c, (int **)&d.tgt_ptr, ptr.data(), Ns + 1))) return fail(rc);
+      if ((rc = dupload(c, (int **)&d.tgt_term, term.data(), m.n_hop))) return fail(rc);
+    }
     d.hop_t = ht;
     if ((rc = dupload(c, (double **)&d.U, m.U ? m.U : Uz.data(), Ns))) return fail(rc);
     if ((rc = dupload(c, (int **)&d.V_i, m.V_i, m.n_V))) return fail(rc);
@@ -443,7 +453,7 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
   const int occ = std::max(1, vmc_sample_occupancy(c->precision, c->smem_sample));
   c->grid_sample = std::min(c->n_work, nsm * occ);
   c->recompute_every = o->recompute_every > 0 ? o->recompute_every
-                       : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 64 : 0;
+                       : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 256 : 0;
   // Initial inverses; re-draw placements whose M is singular (bounded).
   uint64_t state = o->seed ^ 0x5851F42D4C957F2Dull;
   for (int attempt = 0;; ++attempt) {
@@ -586,6 +596,7 @@ int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_b
     CKC(cudaStreamSynchronize(c->st));
     for (int w = 0; w < s.W; ++w) bad |= st[w];
   }
+  if (bad & VMC_ST_TIMEOUT) return VMC_ETIMEOUT;
   if (bad & VMC_ST_SINGULAR) return VMC_ESINGULAR;
   if (bad & VMC_ST_NUMERIC) return VMC_ENUMERIC;
   return VMC_OK;

@@ -13,6 +13,7 @@
 #define VMC_ST_SINGULAR 1
 #define VMC_ST_NUMERIC 2
 #define VMC_ST_ILLCOND 4     // min/max |pivot| of the last from-scratch inverse below 1e-12
+#define VMC_ST_TIMEOUT 8     // a bounded wait on a bulk copy expired
 
 // One system of a (possibly batched) context, as the kernels see it.  All
 // pointers are device pointers.
@@ -27,6 +28,8 @@ struct SysDev {
   int acc_len;                 // O-row accumulator length in shared memory (0 = global)
   const int *hop_i, *hop_j;
   const double *hop_t;
+  const int *tgt_ptr;          // [Ns+1] hopping terms grouped by target site i (CSR)
+  const int *tgt_term;         // [n_hop] term indices
   const double *U;
   const int *V_i, *V_j;
   const double *V_val;

@@ -28,10 +28,11 @@ __device__ __forceinline__ double ld(const TO *p) { return (double)*p; }
 //   mode 3: O_rk t_r                   (CG: O^T t)
 template <typename TO>
 __global__ void k_colreduce(const TO *O, int ldO, int rows, int Np, const double *obar,
-                            const double *wvec, double wshift, int mode, double *part) {
+                            const double *wvec, double wshift, int mode, double *part,
+                            const int *done) {
   const int k = blockIdx.x * RB + threadIdx.x;
   const int c = blockIdx.y;
-  if (k >= Np) return;
+  if (k >= Np || (done && *done)) return;
   const int r0 = c * ROWCHUNK;
   const int r1 = min(rows, r0 + ROWCHUNK);
   const double ok = (mode == 1 || mode == 2) ? obar[k] : 0.0;
@@ -48,9 +49,10 @@ __global__ void k_colreduce(const TO *O, int ldO, int rows, int Np, const double
   part[(size_t)c * Np + k] = s;
 }
 
-__global__ void k_sum_parts(const double *part, int nparts, int Np, double scale, double *out) {
+__global__ void k_sum_parts(const double *part, int nparts, int Np, double scale, double *out,
+                            const int *done) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Np) return;
+  if (k >= Np || (done && *done)) return;
   double s = 0.0;
   for (int c = 0; c < nparts; ++c) s += part[(size_t)c * Np + k];
   out[k] = s * scale;
@@ -125,6 +127,57 @@ __global__ void __launch_bounds__(256) k_syrk(const TO *O, int ldO, int rows, in
     }
 }
 
+// FP32 variant for the mixed form: FP32 products and FP32 accumulation over
+// at most 1024 rows per split, FP64 accumulation across splits.
+__global__ void __launch_bounds__(256) k_syrk32(const float *O, int ldO, int rows, int Np,
+                                                const double *obar, double scale,
+                                                int rows_per_split, double *S) {
+  int t = blockIdx.x, bi = 0;
+  const int nt = (Np + ST - 1) / ST;
+  while (t >= nt - bi) {
+    t -= nt - bi;
+    ++bi;
+  }
+  const int bj = bi + t;
+  const int r0 = blockIdx.y * rows_per_split;
+  const int r1 = min(rows, r0 + rows_per_split);
+  __shared__ float As[SKK][ST + 1];
+  __shared__ float Bs[SKK][ST + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float acc[4][4] = {};
+  for (int rb = r0; rb < r1; rb += SKK) {
+    for (int q = threadIdx.x; q < SKK * ST; q += 256) {
+      const int rr = q / ST, cc = q % ST;
+      const int r = rb + rr;
+      const int ka = bi * ST + cc, kb = bj * ST + cc;
+      As[rr][cc] = (r < r1 && ka < Np) ? (float)((double)O[(size_t)r * ldO + ka] - obar[ka]) : 0.f;
+      Bs[rr][cc] = (r < r1 && kb < Np) ? (float)((double)O[(size_t)r * ldO + kb] - obar[kb]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SKK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty + 16 * u];
+        b[u] = Bs[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = bi * ST + ty + 16 * u, j = bj * ST + tx + 16 * v;
+      if (i < Np && j < Np && i <= j) atomicAdd(S + (size_t)i * Np + j, (double)acc[u][v] * scale);
+    }
+}
+
 // Mirror the upper triangle and apply the diagonal shift.
 __global__ void k_mirror_shift(double *S, int Np, double shift_rel, double shift_abs) {
   const size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -134,64 +187,174 @@ __global__ void k_mirror_shift(double *S, int Np, double shift_rel, double shift
   else if (i == j) S[q] = S[q] * (1.0 + shift_rel) + shift_abs;
 }
 
-// Right-looking Cholesky, one column per pair of launches (lower triangle in place).
-__global__ void k_chol_col(double *A, int n, int j, int *info) {
-  __shared__ double d;
-  if (threadIdx.x == 0) {
-    const double a = A[(size_t)j * n + j];
-    if (!(a > 0.0) || !isfinite(a)) {
-      if (*info == 0) *info = j + 1;
-      d = 1.0;
-    } else {
-      d = sqrt(a);
+// Blocked right-looking Cholesky (lower triangle in place), panels of CB
+// columns: factor the diagonal block (one CTA), solve the panel below it
+// (L_ij = A_ij L_jj^-T), update the trailing lower triangle (A -= L L^T).
+constexpr int CB = 32;
+
+__global__ void k_potrf_diag(double *A, int n, int j0, int nb, int *info) {
+  __shared__ double D[CB][CB + 1];
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    D[r][c] = A[(size_t)(j0 + r) * n + j0 + c];
+  }
+  __syncthreads();
+  for (int k = 0; k < nb; ++k) {
+    if (threadIdx.x == 0) {
+      const double a = D[k][k];
+      if (!(a > 0.0) || !isfinite(a)) {
+        if (*info == 0) *info = j0 + k + 1;
+        D[k][k] = 1.0;
+      } else {
+        D[k][k] = sqrt(a);
+      }
     }
-    A[(size_t)j * n + j] = d;
+    __syncthreads();
+    const double inv = 1.0 / D[k][k];
+    for (int r = k + 1 + threadIdx.x; r < nb; r += blockDim.x) D[r][k] *= inv;
+    __syncthreads();
+    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+      const int r = q / nb, c = q % nb;
+      if (c > k && r >= c) D[r][c] -= D[r][k] * D[c][k];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const double inv = 1.0 / d;
-  for (int i = j + 1 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    A[(size_t)i * n + j] *= inv;
-}
-
-__global__ void k_chol_update(double *A, int n, int j) {
-  // trailing A[i][k] -= L[i][j] L[k][j] for j < k <= i
-  const int m = n - j - 1;
-  const size_t tot = (size_t)m * m;
-  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < tot;
-       q += (size_t)gridDim.x * blockDim.x) {
-    const int i = j + 1 + (int)(q / m), k = j + 1 + (int)(q % m);
-    if (k <= i) A[(size_t)i * n + k] -= A[(size_t)i * n + j] * A[(size_t)k * n + j];
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    if (r >= c) A[(size_t)(j0 + r) * n + j0 + c] = D[r][c];
   }
 }
 
-// Forward (L y = b) then backward (L^T x = y) substitution, one block.
-__global__ void k_chol_solve(const double *L, int n, const double *b, double *x) {
-  extern __shared__ double y[];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = b[i];
+__global__ void k_trsm_panel(double *A, int n, int j0, int nb) {
+  __shared__ double L[CB][CB + 1];
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    L[r][c] = (r >= c) ? A[(size_t)(j0 + r) * n + j0 + c] : 0.0;
+  }
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    const double yj = y[j] / L[(size_t)j * n + j];
-    __syncthreads();
-    if (threadIdx.x == 0) y[j] = yj;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) y[i] -= L[(size_t)i * n + j] * yj;
-    __syncthreads();
+  const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[CB];
+  double *row = A + (size_t)i * n + j0;
+#pragma unroll
+  for (int k = 0; k < CB; ++k) x[k] = (k < nb) ? row[k] : 0.0;
+#pragma unroll
+  for (int k = 0; k < CB; ++k) {
+    if (k < nb) {
+      double v = x[k];
+#pragma unroll
+      for (int l = 0; l < CB; ++l)
+        if (l < k) v -= x[l] * L[k][l];
+      x[k] = v / L[k][k];
+    }
   }
-  for (int j = n - 1; j >= 0; --j) {
-    const double xj = y[j] / L[(size_t)j * n + j];
-    __syncthreads();
-    if (threadIdx.x == 0) y[j] = xj;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) y[i] -= L[(size_t)j * n + i] * xj;
-    __syncthreads();
+#pragma unroll
+  for (int k = 0; k < CB; ++k)
+    if (k < nb) row[k] = x[k];
+}
+
+// trailing A[i][k] -= sum_l L[i][j0+l] L[k][j0+l], j1 <= k <= i < n (j1 = j0 + nb)
+__global__ void __launch_bounds__(256) k_syrk_trailing(double *A, int n, int j0, int nb) {
+  const int j1 = j0 + nb;
+  const int m = n - j1;
+  const int nt = (m + 63) / 64;
+  int t = blockIdx.x, bi = 0;
+  while (t >= bi + 1) {
+    t -= bi + 1;
+    ++bi;
   }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = y[i];
+  const int bj = t;   // bj <= bi: lower tiles
+  __shared__ double Pi[CB][65];
+  __shared__ double Pk[CB][65];
+  for (int q = threadIdx.x; q < CB * 64; q += 256) {
+    const int l = q / 64, r = q % 64;
+    const int ii = j1 + bi * 64 + r, kk = j1 + bj * 64 + r;
+    Pi[l][r] = (l < nb && ii < n) ? A[(size_t)ii * n + j0 + l] : 0.0;
+    Pk[l][r] = (l < nb && kk < n) ? A[(size_t)kk * n + j0 + l] : 0.0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int l = 0; l < nb; ++l) {
+    double a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      a[u] = Pi[l][ty + 16 * u];
+      b[u] = Pk[l][tx + 16 * u];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  }
+  (void)nt;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = j1 + bi * 64 + ty + 16 * u, k = j1 + bj * 64 + tx + 16 * v;
+      if (i < n && k < n && k <= i) A[(size_t)i * n + k] -= acc[u][v];
+    }
+}
+
+// Blocked triangular solves with the Cholesky factor (lower, row-major):
+// forward L y = b and backward L^T x = y, panels of CB rows.  The diagonal
+// block is solved by one CTA in shared memory; the rest of the vector is
+// updated by a matrix-vector product over the panel (coalesced row reads).
+__global__ void k_trsv_diag(const double *L, int n, int p0, int nb, double *y, int backward) {
+  __shared__ double D[CB][CB + 1];
+  __shared__ double v[CB];
+  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
+    const int r = q / nb, c = q % nb;
+    D[r][c] = L[(size_t)(p0 + r) * n + p0 + c];
+  }
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) v[q] = y[p0 + q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!backward) {
+      for (int k = 0; k < nb; ++k) {
+        double s = v[k];
+        for (int l = 0; l < k; ++l) s -= D[k][l] * v[l];
+        v[k] = s / D[k][k];
+      }
+    } else {
+      for (int k = nb - 1; k >= 0; --k) {
+        double s = v[k];
+        for (int l = k + 1; l < nb; ++l) s -= D[l][k] * v[l];
+        v[k] = s / D[k][k];
+      }
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < nb; q += blockDim.x) y[p0 + q] = v[q];
+}
+
+// forward: y[i] -= sum_l L[i][p0+l] y[p0+l] for i >= p0 + nb (one warp per row)
+__global__ void k_trsv_fwd_update(const double *L, int n, int p0, int nb, double *y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int i = p0 + nb + warp;
+  if (i >= n) return;
+  double s = (lane < nb) ? L[(size_t)i * n + p0 + lane] * y[p0 + lane] : 0.0;
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) y[i] -= s;
+}
+
+// backward: y[i] -= sum_l L[p0+l][i] x[p0+l] for i < p0 (rows p0+l read contiguously)
+__global__ void k_trsv_bwd_update(const double *L, int n, int p0, int nb, double *y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p0) return;
+  double s = 0.0;
+  for (int l = 0; l < nb; ++l) s += L[(size_t)(p0 + l) * n + i] * y[p0 + l];
+  y[i] -= s;
 }
 
 // t = O v (one warp per row)
 template <typename TO>
-__global__ void k_gemv_rows(const TO *O, int ldO, int rows, int Np, const double *v, double *t) {
+__global__ void k_gemv_rows(const TO *O, int ldO, int rows, int Np, const double *v, double *t,
+                            const int *done) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (warp >= rows) return;
+  if (warp >= rows || *done) return;
   const TO *o = O + (size_t)warp * ldO;
   double s = 0.0;
   for (int k = lane; k < Np; k += 32) s += ld(o + k) * v[k];
@@ -212,29 +375,84 @@ __global__ void k_dot(const double *a, const double *b, int n, double *out) {
   if (threadIdx.x == 0) out[0] = red[0];
 }
 
-// w = u - o (o . v) + (shift_rel diagS + shift_abs) v, where u = O^T t / rows
-// and odv = o . v is a device scalar.
+// CG (Algorithm 1) on the device.  cg[0..1]: rho ping-pong, cg[2]: p.w,
+// cg[3]: o.v, cg[4]: threshold eps^2 |b|^2; flags[0]: done, flags[1]:
+// iterations, flags[2]: breakdown.
 __global__ void k_cg_finish(const double *u, const double *obar, const double *odv,
                             const double *diagS, const double *v, double shift_rel,
-                            double shift_abs, int n, double *w) {
+                            double shift_abs, int n, double *w, const int *done) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  if (k >= n || *done) return;
   w[k] = u[k] - obar[k] * odv[0] + (shift_rel * diagS[k] + shift_abs) * v[k];
 }
 
-__global__ void k_axpy(double *y, const double *x, const double *num, const double *den,
-                       double sign, int n) {
-  // y += sign * (num/den) * x
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  y[k] += sign * (num[0] / den[0]) * x[k];
+__global__ void k_dot_dev(const double *a, const double *b, int n, double *out, const int *done) {
+  __shared__ double red[256];
+  if (done && *done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
 }
 
-__global__ void k_xpay(double *p, const double *r, const double *num, const double *den, int n) {
-  // p = r + (num/den) p
+// x += alpha p, r -= alpha w with alpha = rho / (p.w)
+__global__ void k_cg_update_xr(double *x, double *r, const double *p, const double *w,
+                               const double *rho, const double *pw, int n, int *flags) {
+  if (flags[0]) return;
+  const double alpha = rho[0] / pw[0];
+  if (!isfinite(alpha) || pw[0] == 0.0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      flags[2] = 1;
+      flags[0] = 1;
+    }
+    return;
+  }
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  p[k] = r[k] + (num[0] / den[0]) * p[k];
+  x[k] += alpha * p[k];
+  r[k] -= alpha * w[k];
+}
+
+// rho' = r.r; done if rho' < threshold (one block)
+__global__ void k_cg_check(const double *r, int n, double *rho_new, const double *thr, int *flags) {
+  __shared__ double red[256];
+  if (flags[0]) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += r[i] * r[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    rho_new[0] = red[0];
+    flags[1] += 1;
+    if (!(red[0] >= thr[0])) flags[0] = 1;   // converged (or NaN: flagged below)
+    if (!isfinite(red[0])) flags[2] = 1;
+  }
+}
+
+// p = r + (rho'/rho) p
+__global__ void k_cg_update_p(double *p, const double *r, const double *rho_new,
+                              const double *rho, int n, const int *flags) {
+  if (flags[0]) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  p[k] = r[k] + (rho_new[0] / rho[0]) * p[k];
+}
+
+__global__ void k_cg_init(double *cg, int *flags, double eps) {
+  // cg[0] holds |b|^2 = rho_0 on entry
+  cg[4] = eps * eps * cg[0];
+  flags[0] = (cg[0] == 0.0) ? 1 : 0;
+  flags[1] = 0;
+  flags[2] = 0;
 }
 
 __global__ void k_update_params(double *p, const double *x, double dtau, int n) {
@@ -244,20 +462,23 @@ __global__ void k_update_params(double *p, const double *x, double dtau, int n) 
 
 template <typename TO>
 cudaError_t colreduce(const SrWork &w, const TO *O, int mode, const double *wvec, double wshift,
-                      double scale, double *out, cudaStream_t st, long long *nl) {
+                      double scale, double *out, cudaStream_t st, long long *nl,
+                      const int *done = nullptr) {
   const int nparts = (w.rows + ROWCHUNK - 1) / ROWCHUNK;
   dim3 grid((w.Np + RB - 1) / RB, nparts);
-  k_colreduce<TO><<<grid, RB, 0, st>>>(O, w.ldO, w.rows, w.Np, w.obar, wvec, wshift, mode, w.part);
-  k_sum_parts<<<(w.Np + 255) / 256, 256, 0, st>>>(w.part, nparts, w.Np, scale, out);
+  k_colreduce<TO><<<grid, RB, 0, st>>>(O, w.ldO, w.rows, w.Np, w.obar, wvec, wshift, mode, w.part,
+                                       done);
+  k_sum_parts<<<(w.Np + 255) / 256, 256, 0, st>>>(w.part, nparts, w.Np, scale, out, done);
   *nl += 2;
   return cudaGetLastError();
 }
 
 cudaError_t colreduce_any(const SrWork &w, int mode, const double *wvec, double wshift,
-                          double scale, double *out, cudaStream_t st, long long *nl) {
+                          double scale, double *out, cudaStream_t st, long long *nl,
+                          const int *done = nullptr) {
   if (w.precision == 0)
-    return colreduce<double>(w, (const double *)w.O, mode, wvec, wshift, scale, out, st, nl);
-  return colreduce<float>(w, (const float *)w.O, mode, wvec, wshift, scale, out, st, nl);
+    return colreduce<double>(w, (const double *)w.O, mode, wvec, wshift, scale, out, st, nl, done);
+  return colreduce<float>(w, (const float *)w.O, mode, wvec, wshift, scale, out, st, nl, done);
 }
 
 }  // namespace
@@ -293,6 +514,7 @@ cudaError_t vmc_sr_build_S(const SrWork &w, double shift_rel, double shift_abs, 
   int splits = (4 * nsm + ntiles - 1) / ntiles;
   const int max_splits = (w.rows + 255) / 256;
   if (splits > max_splits) splits = max_splits;
+  if (w.precision != 0 && splits < (w.rows + 1023) / 1024) splits = (w.rows + 1023) / 1024;
   if (splits < 1) splits = 1;
   int rps = (w.rows + splits - 1) / splits;
   rps = (rps + SKK - 1) / SKK * SKK;
@@ -302,8 +524,8 @@ cudaError_t vmc_sr_build_S(const SrWork &w, double shift_rel, double shift_abs, 
     k_syrk<double><<<grid, 256, 0, st>>>((const double *)w.O, w.ldO, w.rows, w.Np, w.obar,
                                          1.0 / w.rows, rps, w.S);
   else
-    k_syrk<float><<<grid, 256, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, w.obar,
-                                        1.0 / w.rows, rps, w.S);
+    k_syrk32<<<grid, 256, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, w.obar,
+                                   1.0 / w.rows, rps, w.S);
   const size_t n2 = (size_t)w.Np * w.Np;
   k_mirror_shift<<<(unsigned)((n2 + 255) / 256), 256, 0, st>>>(w.S, w.Np, shift_rel, shift_abs);
   *nl += 2;
@@ -313,19 +535,32 @@ cudaError_t vmc_sr_build_S(const SrWork &w, double shift_rel, double shift_abs, 
 int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl) {
   const int n = w.Np;
   cudaMemsetAsync(w.info, 0, sizeof(int), st);
-  for (int j = 0; j < n; ++j) {
-    const int rem = n - j - 1;
-    k_chol_col<<<rem > 256 ? (rem + 255) / 256 : 1, 256, 0, st>>>(w.S, n, j, w.info);
+  for (int j0 = 0; j0 < n; j0 += CB) {
+    const int nb = n - j0 < CB ? n - j0 : CB;
+    k_potrf_diag<<<1, 256, 0, st>>>(w.S, n, j0, nb, w.info);
+    ++*nl;
+    const int rem = n - j0 - nb;
     if (rem > 0) {
-      const size_t tot = (size_t)rem * rem;
-      const int g = (int)((tot + 255) / 256 < 8192 ? (tot + 255) / 256 : 8192);
-      k_chol_update<<<g, 256, 0, st>>>(w.S, n, j);
-      *nl += 1;
+      k_trsm_panel<<<(rem + 127) / 128, 128, 0, st>>>(w.S, n, j0, nb);
+      const int nt = (rem + 63) / 64;
+      k_syrk_trailing<<<nt * (nt + 1) / 2, 256, 0, st>>>(w.S, n, j0, nb);
+      *nl += 2;
     }
-    *nl += 1;
   }
-  k_chol_solve<<<1, 256, sizeof(double) * n, st>>>(w.S, n, w.g, w.x);
-  *nl += 1;
+  cudaMemcpyAsync(w.x, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  for (int p0 = 0; p0 < n; p0 += CB) {
+    const int nb = n - p0 < CB ? n - p0 : CB;
+    k_trsv_diag<<<1, 32, 0, st>>>(w.S, n, p0, nb, w.x, 0);
+    const int rem = n - p0 - nb;
+    if (rem > 0) k_trsv_fwd_update<<<(rem * 32 + 255) / 256, 256, 0, st>>>(w.S, n, p0, nb, w.x);
+    *nl += 1 + (rem > 0);
+  }
+  for (int p0 = ((n - 1) / CB) * CB; p0 >= 0; p0 -= CB) {
+    const int nb = n - p0 < CB ? n - p0 : CB;
+    k_trsv_diag<<<1, 32, 0, st>>>(w.S, n, p0, nb, w.x, 1);
+    if (p0 > 0) k_trsv_bwd_update<<<(p0 + 255) / 256, 256, 0, st>>>(w.S, n, p0, nb, w.x);
+    *nl += 1 + (p0 > 0);
+  }
   if (cudaGetLastError() != cudaSuccess) return -3;
   int info = 0;
   if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
@@ -334,59 +569,59 @@ int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl) {
   return info ? -4 : 0;
 }
 
-// One SR-CG product w = S~ v (Sec. 2.3.2): t = O v, u = O^T t / rows,
-// w = u - o (o . v) + shift terms.
+// One SR-CG product out = S~ v (Sec. 2.3.2): t = O v, u = O^T t / rows,
+// out = u - o (o . v) + shift terms.  2 (rows + 1) Np products for the S part.
 static cudaError_t srcg_matvec(const SrWork &w, const double *v, double *out, double shift_rel,
-                               double shift_abs, cudaStream_t st, long long *nl) {
+                               double shift_abs, const int *done, cudaStream_t st, long long *nl) {
   const int threads = 256;
   const int blocks = (int)(((size_t)w.rows * 32 + threads - 1) / threads);
   if (w.precision == 0)
-    k_gemv_rows<double><<<blocks, threads, 0, st>>>((const double *)w.O, w.ldO, w.rows, w.Np, v, w.t);
+    k_gemv_rows<double><<<blocks, threads, 0, st>>>((const double *)w.O, w.ldO, w.rows, w.Np, v, w.t, done);
   else
-    k_gemv_rows<float><<<blocks, threads, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, v, w.t);
+    k_gemv_rows<float><<<blocks, threads, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, v, w.t, done);
   ++*nl;
-  cudaError_t e = colreduce_any(w, 3, w.t, 0.0, 1.0 / w.rows, w.r + w.Np, st, nl);
+  cudaError_t e = colreduce_any(w, 3, w.t, 0.0, 1.0 / w.rows, w.r + w.Np, st, nl, done);
   if (e) return e;
-  k_dot<<<1, 256, 0, st>>>(w.obar, v, w.Np, w.scal + 4);
-  k_cg_finish<<<(w.Np + 255) / 256, 256, 0, st>>>(w.r + w.Np, w.obar, w.scal + 4, w.diagS, v,
-                                                   shift_rel, shift_abs, w.Np, out);
+  k_dot_dev<<<1, 256, 0, st>>>(w.obar, v, w.Np, w.scal + 3, done);
+  k_cg_finish<<<(w.Np + 255) / 256, 256, 0, st>>>(w.r + w.Np, w.obar, w.scal + 3, w.diagS, v,
+                                                   shift_rel, shift_abs, w.Np, out, done);
   *nl += 2;
   return cudaGetLastError();
 }
 
-// Algorithm 1 with x0 = 0.  Device scalars: scal[0] = rho, scal[1] = p.w,
-// scal[2] = rho', scal[3] = |b|^2.  w.r holds 2*Np doubles (r and scratch).
+// Algorithm 1 with x0 = 0, run on the device in batches of iterations; the
+// host reads the convergence flag once per batch.  w.r holds 2 Np doubles.
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps, int kmax,
                     int *iters, cudaStream_t st, long long *nl) {
   const int n = w.Np, g = (n + 255) / 256;
+  int *flags = w.info;
+  double *cg = w.scal;
   cudaMemsetAsync(w.x, 0, sizeof(double) * n, st);
   cudaMemcpyAsync(w.r, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(w.p, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  k_dot<<<1, 256, 0, st>>>(w.r, w.r, n, w.scal + 0);
-  *nl += 1;
-  double h[2];
-  if (cudaMemcpyAsync(h, w.scal, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
-  const double thr = eps * eps * h[0];
-  *iters = 0;
-  if (h[0] == 0.0) return 0;
+  k_dot_dev<<<1, 256, 0, st>>>(w.r, w.r, n, cg + 0, nullptr);
+  k_cg_init<<<1, 1, 0, st>>>(cg, flags, eps);
+  *nl += 2;
+  const int batch = 16;
+  int h[3] = {0, 0, 0};
   for (int k = 1; k <= kmax; ++k) {
-    if (srcg_matvec(w, w.p, w.w, shift_rel, shift_abs, st, nl) != cudaSuccess) return -3;
-    k_dot<<<1, 256, 0, st>>>(w.p, w.w, n, w.scal + 1);
-    k_axpy<<<g, 256, 0, st>>>(w.x, w.p, w.scal + 0, w.scal + 1, 1.0, n);
-    k_axpy<<<g, 256, 0, st>>>(w.r, w.w, w.scal + 0, w.scal + 1, -1.0, n);
-    k_dot<<<1, 256, 0, st>>>(w.r, w.r, n, w.scal + 2);
+    double *rho = cg + ((k - 1) & 1), *rho_new = cg + (k & 1);
+    if (srcg_matvec(w, w.p, w.w, shift_rel, shift_abs, flags, st, nl) != cudaSuccess) return -3;
+    k_dot_dev<<<1, 256, 0, st>>>(w.p, w.w, n, cg + 2, flags);
+    k_cg_update_xr<<<g, 256, 0, st>>>(w.x, w.r, w.p, w.w, rho, cg + 2, n, flags);
+    k_cg_check<<<1, 256, 0, st>>>(w.r, n, rho_new, cg + 4, flags);
+    k_cg_update_p<<<g, 256, 0, st>>>(w.p, w.r, rho_new, rho, n, flags);
     *nl += 4;
-    double rho[3];
-    if (cudaMemcpyAsync(rho, w.scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
-    *iters = k;
-    if (!(rho[1] != 0.0) || !isfinite(rho[2])) return -5;
-    if (rho[2] < thr) break;
-    k_xpay<<<g, 256, 0, st>>>(w.p, w.r, w.scal + 2, w.scal + 0, n);
-    cudaMemcpyAsync(w.scal, w.scal + 2, sizeof(double), cudaMemcpyDeviceToDevice, st);
-    *nl += 1;
+    if (k % batch == 0 || k == kmax) {
+      if (cudaMemcpyAsync(h, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
+      if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+      if (h[0]) break;
+    }
   }
+  if (cudaMemcpyAsync(h, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+  *iters = h[1];
+  if (h[2]) return -5;
   return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -36,6 +36,54 @@ __host__ __device__ __forceinline__ size_t minv_bytes(int N, int ldm, int esize)
   return align_up((size_t)N * ldm * esize, 128);
 }
 
+// ---- TMA bulk copies (cp.async.bulk) with an mbarrier, bounded waits ----
+constexpr uint32_t WAIT_LIMIT = 1u << 22;   // try_wait attempts before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase with the given parity; false after WAIT_LIMIT attempts.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 // Shared-memory carve-up of one walker.
 template <typename T>
 struct WSmem {
@@ -50,6 +98,7 @@ struct WSmem {
   int *occ;     // 2 Ns
   int *ilist;   // Ns
   int *misc;    // 8
+  uint4 *rnd;   // NT Philox draws (one batch)
 };
 
 template <typename T>
@@ -68,6 +117,7 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, unsigned ch
   const size_t o_occ = take(sizeof(int) * 2 * Ns);
   const size_t o_il = take(sizeof(int) * Ns);
   const size_t o_misc = take(sizeof(int) * 8);
+  const size_t o_rnd = take(sizeof(uint4) * NT);
   if (sm) {
     sm->minv = (T *)(base + o_minv);
     sm->vec = (T *)(base + o_vec);
@@ -80,6 +130,7 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, unsigned ch
     sm->occ = (int *)(base + o_occ);
     sm->ilist = (int *)(base + o_il);
     sm->misc = (int *)(base + o_misc);
+    sm->rnd = (uint4 *)(base + o_rnd);
   }
   return off;
 }
@@ -188,8 +239,15 @@ __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m
   __syncthreads();
   T a22 = (T)0, a12 = (T)0;
   if (tid < N) {
-    T w = (T)0;
-    for (int l = 0; l < N; ++l) w += vA[l] * sm.minv[l * ldm + tid];
+    T w0 = (T)0, w1 = (T)0;
+    int l = 0;
+#pragma unroll 4
+    for (; l + 1 < N; l += 2) {
+      w0 += vA[l] * sm.minv[l * ldm + tid];
+      w1 += vA[l + 1] * sm.minv[(l + 1) * ldm + tid];
+    }
+    if (l < N) w0 += vA[l] * sm.minv[l * ldm + tid];
+    const T w = w0 + w1;
     vB[tid] = w;
     const int site = (tid == n) ? j : sm.ele[tid];
     const T c = FT[(size_t)i * Ns + site];
@@ -306,10 +364,19 @@ struct MoveCounts {
 
 template <typename T>
 __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t walker,
-                        unsigned long long &ctr, MoveCounts &mc, int &acc_since, int &buf) {
+                        unsigned long long &ctr, int &rpos, MoveCounts &mc, int &acc_since,
+                        int &buf) {
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, tid = threadIdx.x;
-  const uint4 r = vmc_philox(make_uint4((uint32_t)ctr, (uint32_t)(ctr >> 32), walker,
+  if (rpos == NT) {
+    // Next NT draws of this walker's stream, one per thread.
+    __syncthreads();
+    const unsigned long long c = ctr + tid;
+    sm.rnd[tid] = vmc_philox(make_uint4((uint32_t)c, (uint32_t)(c >> 32), walker,
                                         (uint32_t)S.sys_index), key);
+    __syncthreads();
+    rpos = 0;
+  }
+  const uint4 r = sm.rnd[rpos++];
   ctr++;
   const T u = (T)(r.w >> 8) * (T)(1.0 / 16777216.0);
   if ((unsigned long long)r.x < S.pex) {
@@ -433,36 +500,54 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     const double sb = 0.5 * ((sm.occ[b] >= 0) - (sm.occ[Ns + b] >= 0));
     ed += S.J_val[k] * sa * sb;
   }
-  // --- hopping: one thread per (term, spin); each valid one is a dot product
-  // of the new row (column) of M with a column (row) of M^-1 (Green-function
-  // ratio), times the correlation-factor ratio.
+  // --- hopping, one warp per target site i: the warp gathers the rows
+  // f(i, r_m,dn) and f(r_n,up, i) once (lane-strided), then every electron on a
+  // neighbouring site j that can hop to i gives a Green-function ratio as a dot
+  // product with a column (row) of M^-1, times the correlation-factor ratio.
   double eo = 0.0;
-  for (int q = tid; q < 2 * S.n_hop; q += NT) {
-    const int k = q >> 1, s = q & 1;
-    const int i = S.hop_i[k], j = S.hop_j[k];
-    const int e = sm.occ[s * Ns + j];
-    if (e < 0 || sm.occ[s * Ns + i] >= 0) continue;
-    T a0 = (T)0, a1 = (T)0;
-    if (s == 0) {
-      const T *Fi = F + (size_t)i * Ns;
-      int m = 0;
-      for (; m + 1 < N; m += 2) {
-        a0 += sm.minv[m * ldm + e] * Fi[sm.ele[N + m]];
-        a1 += sm.minv[(m + 1) * ldm + e] * Fi[sm.ele[N + m + 1]];
-      }
-      if (m < N) a0 += sm.minv[m * ldm + e] * Fi[sm.ele[N + m]];
-    } else {
-      const T *Fi = FT + (size_t)i * Ns;
-      const T *row = sm.minv + (e - N) * ldm;
-      int n = 0;
-      for (; n + 1 < N; n += 2) {
-        a0 += row[n] * Fi[sm.ele[n]];
-        a1 += row[n + 1] * Fi[sm.ele[n + 1]];
-      }
-      if (n < N) a0 += row[n] * Fi[sm.ele[n]];
+  for (int i = warp; i < Ns; i += NWARP) {
+    const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
+    if (kb == ke) continue;
+    const bool up_free = sm.occ[i] < 0, dn_free = sm.occ[Ns + i] < 0;
+    T gu[4], gd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = lane + 32 * u;
+      gu[u] = (up_free && q < N) ? F[(size_t)i * Ns + sm.ele[N + q]] : (T)0;
+      gd[u] = (dn_free && q < N) ? FT[(size_t)i * Ns + sm.ele[q]] : (T)0;
     }
-    eo += -S.hop_t[k] * (double)(a0 + a1) * (double)corr_factor<T>(corr_hop(S, sm.occ, sm.jf, s, j, i));
-    mc.meas_hop++;
+    for (int kk = kb; kk < ke; ++kk) {
+      const int k = S.tgt_term[kk];
+      const int j = S.hop_j[k];
+      const int eu = sm.occ[j], ed = sm.occ[Ns + j];
+      if (up_free && eu >= 0) {
+        T part = (T)0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = lane + 32 * u;
+          if (q < N) part += gu[u] * sm.minv[q * ldm + eu];
+        }
+        part = warp_sum(part);
+        if (lane == 0) {
+          eo += -S.hop_t[k] * (double)part * (double)corr_factor<T>(corr_hop(S, sm.occ, sm.jf, 0, j, i));
+          mc.meas_hop++;
+        }
+      }
+      if (dn_free && ed >= 0) {
+        const T *row = sm.minv + (ed - N) * ldm;
+        T part = (T)0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int q = lane + 32 * u;
+          if (q < N) part += gd[u] * row[q];
+        }
+        part = warp_sum(part);
+        if (lane == 0) {
+          eo += -S.hop_t[k] * (double)part * (double)corr_factor<T>(corr_hop(S, sm.occ, sm.jf, 1, j, i));
+          mc.meas_hop++;
+        }
+      }
+    }
   }
   // --- Heisenberg exchange: J/2 (S+_a S-_b + S-_a S+_b) = -J/2 x (labelled swap ratio)
   T *R = sm.vec + (2 * warp) * VMC_MAX_N;
@@ -524,7 +609,7 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
   // (= -(X^-1)_{n, N+m}, Eq. DiffPf / Appendix C), times the class sign.
   const int base = S.n_g + S.n_v;
   for (int p = tid; p < N * N; p += NT) {
-    const int m = p / N, n = p - m * N;
+    const int n = p / N, m = p - n * N;
     const size_t ab = (size_t)sm.ele[n] * Ns + sm.ele[N + m];
     const int cls = S.f_idx[ab];
     if (cls < 0) continue;
@@ -662,9 +747,13 @@ template <typename T>
 __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2 *work, int n_work,
                                                int *work_ctr, uint2 key, int n_first, int n_samples,
                                                int sweeps_between, int sample_base) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SysDev S;
   __shared__ int s_item;
+  __shared__ __align__(8) uint64_t bar;
+  uint32_t phase = 0;
+  if (threadIdx.x == 0) mbar_init(&bar);
+  __syncthreads();
   for (;;) {
     if (threadIdx.x == 0) s_item = atomicAdd(work_ctr, 1);
     __syncthreads();
@@ -676,27 +765,38 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
     WSmem<T> sm;
     walker_layout<T>(N, Ns, S.acc_len, smem_raw, &sm);
-    // --- load the walker (M^-1 block, configuration, Jastrow field)
+    // --- load the walker: M^-1 block by a TMA bulk copy, configuration and
+    // Jastrow field by plain loads while the copy is in flight
+    const uint32_t nbytes = (uint32_t)minv_bytes(N, ldm, sizeof(T));
     {
-      const size_t nb = minv_bytes(N, ldm, sizeof(T));
-      const int4 *src = (const int4 *)((const unsigned char *)S.minv + (size_t)w * nb);
-      int4 *dst = (int4 *)sm.minv;
-      for (size_t k = tid; k < nb / 16; k += NT) dst[k] = src[k];
+      if (tid == 0) bulk_load(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, nbytes, &bar);
       for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
       for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
       for (int k = tid; k < Ns; k += NT) sm.jf[k] = S.jf[(size_t)w * Ns + k];
     }
+    const bool loaded = mbar_wait(&bar, phase);
+    phase ^= 1;
+    if (__syncthreads_or(!loaded)) {
+      // the copy did not complete within the limit: flag, wait once more for it
+      // (bounded), skip the walker and stop this CTA
+      if (tid == 0) {
+        S.status[w] |= VMC_ST_TIMEOUT;
+        mbar_wait(&bar, phase ^ 1);
+      }
+      break;
+    }
     unsigned long long ctr = S.ctr[w];
+    int rpos = NT;
     MoveCounts mc;
     int acc_since = S.acc_since[w];
     int buf = 0;
     const uint32_t key_w = (uint32_t)w;
     __syncthreads();
     const long long props_first = (long long)n_first * Ne;
-    for (long long p = 0; p < props_first; ++p) propose(S, sm, key, key_w, ctr, mc, acc_since, buf);
+    for (long long p = 0; p < props_first; ++p) propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf);
     for (int s = 0; s < n_samples; ++s) {
       const long long props = (long long)sweeps_between * Ne;
-      for (long long p = 0; p < props; ++p) propose(S, sm, key, key_w, ctr, mc, acc_since, buf);
+      for (long long p = 0; p < props; ++p) propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf);
       __syncthreads();
       measure(S, sm, w, sample_base + s, buf, mc);
       mc.samples++;
@@ -704,12 +804,11 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     if (mc.meas_hop) atomicAdd((unsigned long long *)&S.cnt[8 * w + 4], (unsigned long long)mc.meas_hop);
     if (mc.meas_ex) atomicAdd((unsigned long long *)&S.cnt[8 * w + 5], (unsigned long long)mc.meas_ex);
     __syncthreads();
-    // --- store the walker back
+    // --- store the walker back (M^-1 by a TMA bulk copy)
+    fence_proxy_async();
+    __syncthreads();
     {
-      const size_t nb = minv_bytes(N, ldm, sizeof(T));
-      int4 *dst = (int4 *)((unsigned char *)S.minv + (size_t)w * nb);
-      const int4 *src = (const int4 *)sm.minv;
-      for (size_t k = tid; k < nb / 16; k += NT) dst[k] = src[k];
+      if (tid == 0) bulk_store((unsigned char *)S.minv + (size_t)w * nbytes, sm.minv, nbytes);
       for (int k = tid; k < Ne; k += NT) S.ele[(size_t)w * Ne + k] = sm.ele[k];
       for (int k = tid; k < 2 * Ns; k += NT) S.occ[(size_t)w * 2 * Ns + k] = sm.occ[k];
       for (int k = tid; k < Ns; k += NT) S.jf[(size_t)w * Ns + k] = sm.jf[k];
@@ -718,6 +817,7 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
         S.ctr[w] = ctr;
         S.n_prop[w] += total;
         S.n_acc[w] += mc.hop_a + mc.ex_a;
+        bulk_wait_read();   // shared memory is reused by the next walker
         S.cnt[8 * w + 0] += mc.hop_t;
         S.cnt[8 * w + 1] += mc.ex_t;
         S.cnt[8 * w + 2] += mc.hop_a;
@@ -761,7 +861,7 @@ __global__ void k_expand(SysDev S) {
 template <typename T>
 __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *work, int n_work,
                                              int only_due, int due_threshold) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SysDev S;
   __shared__ GJShared g;
   for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
@@ -822,13 +922,25 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
         S.occ[(size_t)w * 2 * Ns + s * Ns + ele[k]] = k;
       }
       __syncthreads();
-      // Jastrow field h_i = sum_{j != i} v_ij (n_j - 1)
-      const int *occ = S.occ + (size_t)w * 2 * Ns;
+      // Jastrow field h_i = sum_{j != i} v_ij (n_j - 1): only sites with
+      // n_j != 1 contribute; v is symmetric, so row j is read (coalesced).
+      int *nsite = perm + N;        // [Ns] n_j
+      int *jlist = nsite + Ns;      // [Ns] sites with n_j != 1
+      int *jcount = jlist + Ns;     // [1]
+      if (tid == 0) *jcount = 0;
+      for (int k = tid; k < Ns; k += NT) nsite[k] = 0;
+      __syncthreads();
+      for (int k = tid; k < Ne; k += NT) atomicAdd(&nsite[ele[k]], 1);
+      __syncthreads();
+      for (int j = tid; j < Ns; j += NT)
+        if (nsite[j] != 1) jlist[atomicAdd(jcount, 1)] = j;
+      __syncthreads();
+      const int nl = *jcount;
       for (int i = tid; i < Ns; i += NT) {
         double h = 0.0;
-        for (int j = 0; j < Ns; ++j) {
-          const int mj = (occ[j] >= 0) + (occ[Ns + j] >= 0) - 1;
-          if (mj) h += S.vmat[(size_t)i * Ns + j] * mj;
+        for (int q = 0; q < nl; ++q) {
+          const int j = jlist[q];
+          h += S.vmat[(size_t)j * Ns + i] * (double)(nsite[j] - 1);
         }
         S.jf[(size_t)w * Ns + i] = h;
       }
@@ -854,7 +966,7 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
 template <typename T>
 __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int sys, int w,
                                                     int n_moves, const int *moves, double *out) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SysDev S;
   load_sys(&S, systems + sys);
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
@@ -905,9 +1017,8 @@ size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int *acc_len) {
 }
 
 size_t vmc_init_smem(int N, int Ns) {
-  (void)Ns;
   const int ldm = (N % 2) ? N : N + 1;
-  return (size_t)N * ldm * sizeof(double) + sizeof(int) * 3 * N + 64;
+  return (size_t)N * ldm * sizeof(double) + sizeof(int) * (3 * N + 2 * Ns + 1) + 64;
 }
 
 int vmc_sample_occupancy(int precision, size_t smem) {
