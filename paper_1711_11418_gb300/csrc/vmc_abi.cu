@@ -25,6 +25,8 @@ struct SysHost {
   SrWork sr{};
   bool sr_alloc = false;
   bool S_alloc = false;
+  void *tc_hi = nullptr, *tc_lo = nullptr;   // split-BF16 operands (mixed form)
+  int *tc_status = nullptr;
 };
 
 }  // namespace
@@ -275,6 +277,13 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
   }
   if (need_S && !s.S_alloc) {
     CK(dalloc(c, &s.sr.S, sizeof(double) * (size_t)s.Np * s.Np));
+    if (c->precision == VMC_MIXED) {
+      int ldK, Np_pad;
+      vmc_tc_dims(rows_cap, s.Np, &ldK, &Np_pad);
+      CK(dalloc(c, &s.tc_hi, 2 * (size_t)Np_pad * ldK));
+      CK(dalloc(c, &s.tc_lo, 2 * (size_t)Np_pad * ldK));
+      CK(dalloc(c, &s.tc_status, sizeof(int) * 4));
+    }
     s.S_alloc = true;
   }
   s.sr.Np = s.Np;
@@ -283,6 +292,21 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
   s.sr.precision = c->precision;
   s.sr.O = s.dev.O;
   s.sr.E = s.dev.E;
+  return VMC_OK;
+}
+
+// Dense S~: FP64 SIMT GEMM (plain form) or split-BF16 tensor-core GEMM (mixed).
+int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
+  if (c->precision == VMC_MIXED) {
+    CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, c->st,
+                          &c->n_launch));
+    int bad = 0;
+    CKC(cudaMemcpyAsync(&bad, s.tc_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    if (bad) return VMC_ETIMEOUT;
+    return VMC_OK;
+  }
+  CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, c->st, &c->n_launch));
   return VMC_OK;
 }
 
@@ -714,7 +738,7 @@ int vmc_get_sr_matrices(vmc_ctx *c, int32_t system, double shift_rel, double shi
   CKC(vmc_sr_means(s.sr, c->st, &c->n_launch));
   CKC(vmc_sr_build_g(s.sr, c->st, &c->n_launch));
   if (S) {
-    CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, c->st, &c->n_launch));
+    CK(build_S(c, s, shift_rel, shift_abs));
     CKC(cudaMemcpyAsync(S, s.sr.S, sizeof(double) * (size_t)s.Np * s.Np, cudaMemcpyDeviceToHost, c->st));
   }
   if (g) CKC(cudaMemcpyAsync(g, s.sr.g, sizeof(double) * s.Np, cudaMemcpyDeviceToHost, c->st));
@@ -736,7 +760,7 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
   CKC(vmc_sr_build_g(w, c->st, &c->n_launch));
   int iters = 0;
   if (chol) {
-    CKC(vmc_sr_build_S(w, o->shift_rel, o->shift_abs, c->st, &c->n_launch));
+    CK(build_S(c, s, o->shift_rel, o->shift_abs));
     const int rc = vmc_sr_cholesky_solve(w, c->st, &c->n_launch);
     if (rc) return rc;
   } else {

@@ -126,6 +126,9 @@ cudaError_t vmc_sr_diag(const SrWork &w, cudaStream_t st, long long *nl);
 int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl);
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
                     int kmax, int *iters, cudaStream_t st, long long *nl);
+void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad);
+cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
+                              double shift_abs, cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_update_params(double *params, const double *x, double dtau, int Np,
                                  cudaStream_t st, long long *nl);
 cudaError_t vmc_dot_host(const double *a, const double *b, int n, double *out_host,

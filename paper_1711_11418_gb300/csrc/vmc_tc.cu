@@ -1,0 +1,283 @@
+// SR overlap matrix on the tensor cores (tcgen05, sm_103a):
+//   S = (1/N_MC) (O - o)^T (O - o)          (Sec. 2.3.1, S_km = <O_k O_m> - <O_k><O_m>)
+// in split-BF16: every centred entry x = x_hi + x_lo with x_hi = bf16(x),
+// x_lo = bf16(x - x_hi); each product takes the three terms
+// hi*hi + hi*lo + lo*hi (the lo*lo term is below 2^-16 relative), accumulated
+// in FP32 in tensor memory.
+//
+// Pass 1 (k_split_T): O (rows x Np, FP32 or FP64, row-major) -> Hi, Lo
+//   (Np_pad x K_pad BF16, parameter-major = K-major for the GEMM, zero padded).
+// Pass 2 (k_syrk_tc): one CTA per 128x128 tile of the upper triangle.  The
+//   four operand tiles of a 64-sample chunk (A_hi, A_lo, B_hi, B_lo) are
+//   staged in shared memory in the canonical no-swizzle K-major layout (8x8
+//   core matrices of 128 contiguous bytes); one thread issues
+//   tcgen05.mma.kind::f16 (BF16 in, FP32 accumulate into TMEM, M = N = 128,
+//   K = 16), tcgen05.commit signals an mbarrier when the chunk's MMAs have
+//   read shared memory, and the epilogue reads TMEM with tcgen05.ld and writes
+//   the tile and its mirror image.  Two shared-memory stages: the producers
+//   fill one while the tensor cores consume the other.  Every wait is bounded.
+#include "vmc_common.cuh"
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace {
+
+constexpr int TM = 128;              // tile edge (M = N)
+constexpr int TKC = 64;              // samples per chunk (64 BF16 = 128 B per row)
+constexpr int STAGES = 2;
+constexpr int TILE_BYTES = TM * TKC * 2;          // 16 KB per operand tile
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_SMEM = STAGES * STAGE_BYTES + 1024;
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading (K)
+// byte offset, stride (M/N) byte offset, all >> 4; descriptor version 1;
+// no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) |
+         ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N = 128 (>> 3 at bit 17), M = 128 (>> 4 at bit 24).
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((TM >> 3) << 17) | ((TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   su32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity) {
+  for (uint32_t it = 0; it < TC_WAIT_LIMIT; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Pass 1: centre, split, transpose.  Block (32, 8) handles a 32x32 tile.
+template <typename TO>
+__global__ void k_split_T(const TO *O, int ldO, int rows, int Np, const double *obar,
+                          __nv_bfloat16 *Hi, __nv_bfloat16 *Lo, int ldK) {
+  __shared__ float t[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int r = r0 + y, c = c0 + threadIdx.x;
+    float v = 0.f;
+    if (r < rows && c < Np) v = (float)((double)O[(size_t)r * ldO + c] - obar[c]);
+    t[y][threadIdx.x] = v;
+  }
+  __syncthreads();
+  for (int y = threadIdx.y; y < 32; y += 8) {
+    const int c = c0 + y, r = r0 + threadIdx.x;   // output row = parameter, column = sample
+    const float v = t[threadIdx.x][y];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    Hi[(size_t)c * ldK + r] = h;
+    Lo[(size_t)c * ldK + r] = l;
+  }
+}
+
+// Offset of the 16-byte chunk (row r, k-group kg) of a 128 x 64 BF16 tile in
+// the no-swizzle K-major layout: core matrix (r/8, kg) at (r/8)*1024 + kg*128.
+__device__ __forceinline__ uint32_t tile_off(int r, int kg) {
+  return (uint32_t)((r >> 3) * 1024 + kg * 128 + (r & 7) * 16);
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(128, 1) k_syrk_tc(const __nv_bfloat16 *Hi, const __nv_bfloat16 *Lo,
+                                                    int ldK, int K, int Np, double scale, TS *S,
+                                                    int ldS, int *status) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mma_bar[STAGES];
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int fail;
+  // upper-triangular tile (bi <= bj)
+  const int nt = (Np + TM - 1) / TM;
+  int t = blockIdx.x, bi = 0;
+  while (t >= nt - bi) {
+    t -= nt - bi;
+    ++bi;
+  }
+  const int bj = bi + t;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  unsigned char *base = (unsigned char *)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
+  if (tid == 0) {
+    fail = 0;
+    for (int s = 0; s < STAGES; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&mma_bar[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     su32(&tmem_base_sh))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base_sh;
+  const int nchunks = (K + TKC - 1) / TKC;
+  const __nv_bfloat16 *src[4] = {Hi + (size_t)bi * TM * ldK, Lo + (size_t)bi * TM * ldK,
+                                 Hi + (size_t)bj * TM * ldK, Lo + (size_t)bj * TM * ldK};
+  uint32_t phase[STAGES] = {0, 0};
+  for (int kc = 0; kc < nchunks; ++kc) {
+    const int st = kc % STAGES;
+    unsigned char *stage = base + st * STAGE_BYTES;
+    if (kc >= STAGES) {
+      // the MMAs that last read this stage must have completed
+      const bool ok = bar_wait(&mma_bar[st], phase[st]);
+      phase[st] ^= 1;
+      if (!ok) atomicExch(&fail, 1);
+    }
+    if (__syncthreads_or(fail)) break;
+    // producers: 4 tiles x 128 rows x 8 chunks of 16 B (cp.async, 16 B each)
+#pragma unroll 4
+    for (int q = tid; q < 4 * TM * 8; q += 128) {
+      const int op = q >> 10, rem = q & 1023;
+      const int r = (rem & 7) + ((rem >> 6) << 3);   // 8 lanes cover one core matrix
+      const int kg = (rem >> 3) & 7;
+      const __nv_bfloat16 *g = src[op] + (size_t)r * ldK + (size_t)kc * TKC + kg * 8;
+      const uint32_t d = su32(stage + op * TILE_BYTES + tile_off(r, kg));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_hi = su32(stage), a_lo = su32(stage + TILE_BYTES);
+      const uint32_t b_hi = su32(stage + 2 * TILE_BYTES), b_lo = su32(stage + 3 * TILE_BYTES);
+#pragma unroll
+      for (int ks = 0; ks < TKC / 16; ++ks) {
+        const uint32_t off = ks * 256;   // two core matrices along K per MMA
+        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
+        mma_bf16(tmem, smem_desc(a_hi + off, 128, 1024), smem_desc(b_hi + off, 128, 1024), acc0);
+        mma_bf16(tmem, smem_desc(a_hi + off, 128, 1024), smem_desc(b_lo + off, 128, 1024), 1u);
+        mma_bf16(tmem, smem_desc(a_lo + off, 128, 1024), smem_desc(b_hi + off, 128, 1024), 1u);
+      }
+      mma_commit(&mma_bar[st]);
+    }
+  }
+  // wait for the last chunk of each stage still in flight
+  if (!fail) {
+    for (int kc = (nchunks > STAGES ? nchunks - STAGES : 0); kc < nchunks; ++kc) {
+      const int st = kc % STAGES;
+      if (!bar_wait(&mma_bar[st], phase[st])) atomicExch(&fail, 1);
+      phase[st] ^= 1;
+    }
+  }
+  if (fail && tid == 0) {
+    // a wait expired: give the tensor cores a bounded chance to finish what
+    // was issued before the memory they read or write is released
+    for (int s = 0; s < STAGES; ++s) bar_wait(&mma_bar[s], phase[s]);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const bool bad = __syncthreads_or(fail);
+  if (!bad) {
+    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
+    const int row = bi * TM + warp * 32 + lane;
+#pragma unroll 1
+    for (int cc = 0; cc < TM; cc += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + cc;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < Np) {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int col = bj * TM + cc + u;
+          if (col < Np) {
+            const TS val = (TS)((double)__uint_as_float(v[u]) * scale);
+            S[(size_t)row * ldS + col] = val;
+            if (bi != bj) S[(size_t)col * ldS + row] = val;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(status, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+__global__ void k_shift_diag(double *S, int Np, double shift_rel, double shift_abs) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < Np) S[(size_t)k * Np + k] = S[(size_t)k * Np + k] * (1.0 + shift_rel) + shift_abs;
+}
+
+}  // namespace
+
+// Padded sizes of the split operands.
+void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad) {
+  *ldK = (rows + TKC - 1) / TKC * TKC;
+  *Np_pad = (Np + TM - 1) / TM * TM;
+}
+
+// S (FP64, Np x Np, shifted) from O via split-BF16 tensor-core products.
+// hi/lo: device buffers of Np_pad * ldK BF16 each; status: device int.
+cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
+                              double shift_abs, cudaStream_t st, long long *nl) {
+  int ldK, Np_pad;
+  vmc_tc_dims(w.rows, w.Np, &ldK, &Np_pad);
+  cudaError_t e = cudaMemsetAsync(hi, 0, sizeof(__nv_bfloat16) * (size_t)Np_pad * ldK, st);
+  if (e) return e;
+  if ((e = cudaMemsetAsync(lo, 0, sizeof(__nv_bfloat16) * (size_t)Np_pad * ldK, st))) return e;
+  if ((e = cudaMemsetAsync(status, 0, sizeof(int), st))) return e;
+  dim3 g1((w.rows + 31) / 32, (w.Np + 31) / 32), b1(32, 8);
+  if (w.precision == 0)
+    k_split_T<double><<<g1, b1, 0, st>>>((const double *)w.O, w.ldO, w.rows, w.Np, w.obar,
+                                         (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, ldK);
+  else
+    k_split_T<float><<<g1, b1, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, w.obar,
+                                        (__nv_bfloat16 *)hi, (__nv_bfloat16 *)lo, ldK);
+  ++*nl;
+  static bool attr = false;
+  if (!attr) {
+    if ((e = cudaFuncSetAttribute(k_syrk_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  TC_SMEM)))
+      return e;
+    attr = true;
+  }
+  const int nt = Np_pad / TM;
+  k_syrk_tc<double><<<nt * (nt + 1) / 2, 128, TC_SMEM, st>>>(
+      (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, ldK, ldK, w.Np, 1.0 / w.rows, w.S,
+      w.Np, status);
+  k_shift_diag<<<(w.Np + 255) / 256, 256, 0, st>>>(w.S, w.Np, shift_rel, shift_abs);
+  *nl += 2;
+  return cudaGetLastError();
+}

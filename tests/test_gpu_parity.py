@@ -301,3 +301,30 @@ def test_mixed_precision_close_to_fp64(vmc):
     dE = np.abs(res[vmc.FP64][0] - res[vmc.MIXED][0]) / p.Ns
     assert dE.max() < 1e-4
     assert np.allclose(res[vmc.FP64][1], res[vmc.MIXED][1], rtol=1e-3, atol=1e-3)
+
+
+@pytest.mark.parametrize("rows,Np", [(1000, 19), (2049, 300), (4096, 1069)])
+def test_sr_overlap_tensor_cores_split_bf16(vmc, rows, Np):
+    """Mixed form: S built by the tcgen05 split-BF16 GEMM (FP32 accumulation)
+    against the oracle's FP64 S; tiles, chunks and ragged edges covered.
+    Tolerance: 2e-4 of max|S| (three BF16 products ~2^-16 relative each, FP32
+    sums over the samples)."""
+    base = I.ring8_hubbard()
+    n_f = Np - base.n_g - base.n_v
+    if n_f == base.n_f:
+        p = base
+    else:   # one class per (i, j) pair, extra classes unused by the wave function
+        p = base.copy_with(n_f=n_f, f_idx=np.arange(64, dtype=np.int32), f_sign=np.ones(64, np.int8),
+                           params=np.concatenate([base.params[:3],
+                                                  np.random.default_rng(0).uniform(-1, 1, n_f)]))
+    E, O = I.random_samples(rows, Np, seed=rows + Np)
+    O[:, : Np // 3] += 0.5           # non-zero means: centring matters
+    W = 16
+    with vmc.Context(p, W, seed=1, precision=vmc.MIXED, max_samples=(rows + W - 1) // W) as ctx:
+        ctx.set_samples(E, O)
+        S_gpu, g_gpu = ctx.get_sr_matrices(0.0, 0.0)
+    S, g, _, _ = sr_matrices(E, O.astype(np.float32).astype(np.float64))
+    err = np.max(np.abs(S_gpu - S)) / np.max(np.abs(S))
+    assert err < 2e-4, err
+    assert np.allclose(S_gpu, S_gpu.T)
+    assert rel_close(g_gpu, g, rtol=1e-6)
