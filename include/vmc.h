@@ -2,26 +2,32 @@
  * vmc.h - C ABI of the GB300 many-variable VMC hot path.
  *
  * The library samples a Gutzwiller-Jastrow projected anti-parallel Pfaffian
- * wave function  psi(x) = P_G P_J <x|phi_AP-Pf>  (mVMC paper, Sec. 2.2:
- * Eqs. Pf, AP-Pf and the correlation factors of Sec. 2.2.3) with many
- * Metropolis walkers (Sec. 2.1.1-2.1.2), measures the local energy and the
- * log-derivatives O_k (Eq. MC, Sec. 2.3.1), and performs stochastic
- * reconfiguration steps (Eq. SR_equation_system, Sec. 2.3.2, Algorithm 1).
+ * wave function  psi(x) = P_G P_J <x|phi_AP-Pf>  (mVMC paper, Sec. 3.2:
+ * Eqs. Pf, AP-Pf and the correlation factors of Sec. 3.2.3) with many
+ * Metropolis walkers (Sec. 3.1.1-3.1.2), measures the local energy and the
+ * log-derivatives O_k (Eq. MC, Sec. 3.3.1), and performs stochastic
+ * reconfiguration steps (Eq. SR_equation_system, Sec. 3.3.2, Algorithm 1).
  * One GPU; every numerical step runs in the library's own CUDA kernels.
  *
  * Conventions
  *  - Sites i = 0..Ns-1; electrons: Ne = 2N with S^z = 0; ele[n] (n < N) is
  *    the site of up electron n, ele[N+m] the site of down electron m.
  *    Labels are kept through every move.
- *  - Hamiltonian (Sec. 2.1, Eq. GHam and the Hubbard / Spin models):
+ *  - Hamiltonian (Sec. 2.3, Eq. GHam and the Hubbard / Spin models):
  *      H = sum_k -t_k c^dag_{i_k s} c_{j_k s}  (each directed term, both spins)
  *        + sum_i U_i n_i,up n_i,dn + sum_k V_k n_{i_k} n_{j_k}
  *        + sum_k J_k S_{i_k} . S_{j_k}.
- *  - Parameters: one real vector [g (n_g) | v (n_v) | f (n_f)]:
+ *  - Parameters: one real vector [g (n_g) | v (n_v) | f (n_f) | mlp]:
  *      g_i  = p[g_idx[i]]                (0 where g_idx = -1)
  *      v_ij = p[n_g + v_idx[i*Ns+j]]     (v_idx symmetric, -1 = absent)
  *      f_ij = f_sign[i*Ns+j] * p[n_g + n_v + f_idx[i*Ns+j]]
- *    (sublattice classes and anti-periodic signs, Sec. 2.2.1 and App. A).
+ *    (sublattice classes and anti-periodic signs, Sec. 3.2.1 and App. A).
+ *    With n_hidden = H > 0 the wave function carries a learned correlation
+ *    factor exp(w2 . tanh(W1 n + b1) + b2) (not in the paper) on the
+ *    spin-resolved occupations n_c, c = i + Ns*spin; its H*2Ns + 2H + 1
+ *    parameters follow f as [W1 (H x 2Ns, row-major) | b1 (H) | w2 (H) | b2].
+ *    The plain form evaluates it in FP64, the mixed form with BF16 W1 and
+ *    FP32 arithmetic.
  *  - Ownership: every pointer argument is a HOST pointer owned by the caller
  *    and only read (or written, for outputs) during the call; the library
  *    copies what it keeps.  Device memory is allocated by the library in
@@ -54,7 +60,10 @@ enum {
 };
 
 enum { VMC_FP64 = 0, VMC_MIXED = 1 };
-enum { VMC_SOLVE_CHOLESKY = 0, VMC_SOLVE_CG = 1 };
+/* SR solvers: dense S~ + Cholesky; CG (Algorithm 1) with the SR-CG product
+ * from the sample matrix (S never formed); CG with the dense S~ built by the
+ * GEMM (tensor cores in the mixed form). */
+enum { VMC_SOLVE_CHOLESKY = 0, VMC_SOLVE_CG = 1, VMC_SOLVE_CG_DENSE = 2 };
 
 typedef struct vmc_ctx vmc_ctx;
 
@@ -81,6 +90,7 @@ typedef struct {
   const int32_t *v_idx;          /* [Ns*Ns], symmetric, diagonal -1 */
   const int32_t *f_idx;          /* [Ns*Ns] */
   const int8_t *f_sign;          /* [Ns*Ns], +1 / -1 */
+  int32_t n_hidden;              /* MLP hidden units H (0 = no MLP factor, <= 4096) */
 } vmc_layout;
 
 typedef struct {
@@ -120,7 +130,7 @@ typedef struct {
   double dtau;                   /* Delta tau of Eq. SR_equation_system */
   double shift_rel;              /* S~_kk = S_kk (1 + shift_rel) + shift_abs */
   double shift_abs;
-  int32_t solver;                /* VMC_SOLVE_CHOLESKY or VMC_SOLVE_CG */
+  int32_t solver;                /* VMC_SOLVE_CHOLESKY, VMC_SOLVE_CG or VMC_SOLVE_CG_DENSE */
   double cg_eps;                 /* Algorithm 1: stop when |r|^2 < eps^2 |b|^2 */
   int32_t cg_kmax;               /* Algorithm 1: iteration limit */
 } vmc_sr_opts;
@@ -133,9 +143,9 @@ typedef struct {
   int32_t n_params;
 } vmc_sr_report;
 
-/* Create a context for one system (Sec. 2.1-2.2 problem statement).
- * params: initial parameter vector [n_g + n_v + n_f].  p_exchange: the
- * probability that a proposal is an exchange (Sec. 2.1.2); forced to 1 when
+/* Create a context for one system (Sec. 2.3-2.2 problem statement).
+ * params: initial parameter vector [n_g + n_v + n_f (+ MLP block)].  p_exchange: the
+ * probability that a proposal is an exchange (Sec. 3.1.2); forced to 1 when
  * local_spin.  Walker configurations start from a seeded random placement;
  * vmc_set_configs replaces them.
  * Errors: VMC_EINVAL (sizes, Ne odd, Ne/2 > 128, Ns > 4096, index out of
@@ -164,7 +174,7 @@ int vmc_set_configs(vmc_ctx *ctx, int32_t system, const int32_t *ele,
 int vmc_get_configs(vmc_ctx *ctx, int32_t system, int32_t *ele,
                     uint64_t *counters);
 
-/* Markov chains (Sec. 2.1.1-2.1.2): every walker makes n_warmup sweeps,
+/* Markov chains (Sec. 3.1.1-3.1.2): every walker makes n_warmup sweeps,
  * then n_samples times (sweeps_between sweeps, then a measurement of E_loc
  * and the O_k row).  One sweep = Ne proposals.  Replaces the stored
  * samples (n_samples <= max_samples).  Errors: VMC_EINVAL, VMC_ESINGULAR
@@ -185,10 +195,10 @@ int vmc_get_samples(vmc_ctx *ctx, int32_t system, double *E, double *O);
 int vmc_set_samples(vmc_ctx *ctx, int32_t system, int32_t rows,
                     const double *E, const double *O);
 
-/* One SR step on the stored samples of one system (Sec. 2.3.1-2.3.2):
+/* One SR step on the stored samples of one system (Sec. 3.3.1-3.3.2):
  * S_km = <O_k O_m> - <O_k><O_m>, g_m = <E O_m> - <E><O_m>,
  * S~ = S with diagonal shift, solve S~ x = g by Cholesky (S~ = L L^T) or by
- * CG with the SR-CG product (Algorithm 1), alpha += -dtau x.  Walker
+ * CG (Algorithm 1) with the SR-CG product or the dense S~, alpha += -dtau x.  Walker
  * inverses are rebuilt on the next vmc_sample.  Errors: VMC_EINVAL,
  * VMC_ESTATE (no samples), VMC_ESINGULAR (S~ not positive definite),
  * VMC_ENUMERIC (CG breakdown), VMC_ECUDA. */
@@ -204,7 +214,7 @@ int vmc_get_params(vmc_ctx *ctx, int32_t system, double *params);
 int vmc_set_params(vmc_ctx *ctx, int32_t system, const double *params);
 int vmc_num_params(vmc_ctx *ctx, int32_t system);
 
-/* Pfaffian-ratio check hook (Sec. 2.1.2 fast update): for walker w of a
+/* Pfaffian-ratio check hook (Sec. 3.1.2 fast update): for walker w of a
  * system, psi(x')/psi(x) of n_moves candidate moves of its current
  * configuration, each moves[3k..3k+2] = {kind, a, b}: kind 0 = hop of
  * electron a to site b; kind 1 = exchange of up electron a with down

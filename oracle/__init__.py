@@ -12,10 +12,10 @@ Modules
 philox        Philox4x32-10 counter-based generator (Salmon et al., SC'11).
 pfaffian      Pfaffian by Parlett-Reid elimination; brute-force expansion.
 fock          Canonical Fock basis with Jordan-Wigner signs; operator algebra.
-wavefunction  psi(x) = P_G P_J <x|phi_AP-Pf> (Sec. 2.2) and O_k (Sec. 2.3.1).
-hamiltonian   Local energy E_loc(x) (Eq. MC, Sec. 2.1.1) and ED matrices.
-sampler       Metropolis chains with hop / exchange updates (Sec. 2.1.2).
-sr            SR matrices S, g and the solve: Cholesky or CG (Sec. 2.3.1-2,
+wavefunction  psi(x) = P_G P_J <x|phi_AP-Pf> (Sec. 3.2) and O_k (Sec. 3.3.1).
+hamiltonian   Local energy E_loc(x) (Eq. MC, Sec. 3.1.1) and ED matrices.
+sampler       Metropolis chains with hop / exchange updates (Sec. 3.1.2).
+sr            SR matrices S, g and the solve: Cholesky or CG (Sec. 3.3.1-2,
               Algorithm 1).
 exact         Exact enumeration over all configurations (tiny systems).
 

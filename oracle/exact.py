@@ -1,6 +1,6 @@
 """Exact enumeration over all configurations of a tiny system: the
 expectation values that the Monte Carlo estimator of Eq. MC approximates,
-with rho(x) = |<x|psi>|^2 / <psi|psi> (Sec. 2.1.1), and the exact SR
+with rho(x) = |<x|psi>|^2 / <psi|psi> (Sec. 3.1.1), and the exact SR
 matrices for the current parameters."""
 import numpy as np
 

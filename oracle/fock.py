@@ -1,8 +1,8 @@
-"""Canonical Fock basis over spin-orbitals I = i + Ns*sigma (Sec. 2.2.1).
+"""Canonical Fock basis over spin-orbitals I = i + Ns*sigma (Sec. 3.2.1).
 
 A basis state is a Python int bitmask n; bit I set means orbital I is
 occupied.  The state is c^dag_{I_1} c^dag_{I_2} ... c^dag_{I_K} |0> with
-I_1 < I_2 < ... < I_K (the real-space configuration |x> of Sec. 2.1.1 with
+I_1 < I_2 < ... < I_K (the real-space configuration |x> of Sec. 3.1.1 with
 the electrons in ascending orbital order).  Creation and annihilation carry
 the Jordan-Wigner sign (-1)^(number of occupied orbitals below I).
 """

@@ -1,6 +1,6 @@
 """Hamiltonian action in the canonical Fock basis and the local energy.
 
-H = H_T + H_U + H_V + J sum S_i.S_j (Sec. 2.1: Eq. GHam, the Hubbard and
+H = H_T + H_U + H_V + J sum S_i.S_j (Sec. 2.3: Eq. GHam, the Hubbard and
 Spin models):
 
 * hopping term (i, j, t): -t c^dag_{i s} c_{j s} for both spins s;

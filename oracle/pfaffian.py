@@ -1,4 +1,4 @@
-"""Pfaffians of real skew-symmetric matrices (Sec. 2.2.1: <x|phi_Pf> is
+"""Pfaffians of real skew-symmetric matrices (Sec. 3.2.1: <x|phi_Pf> is
 (Ne/2)! Pf(X); Pf(X)^2 = det X).
 
 ``pfaffian`` is Parlett-Reid elimination: congruence transforms by unit

@@ -1,7 +1,7 @@
 """Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
 easy as 1, 2, 3", SC'11), written from its published definition.
 
-The paper's own generator (SFMT, Sec. 2.1.1) is replaced by this
+The paper's own generator (SFMT, Sec. 3.1.1) is replaced by this
 counter-based one so that every (walker, proposal) draw is reproducible on
 any device.  Pure Python integers; slow by design.
 """

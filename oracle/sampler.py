@@ -1,6 +1,6 @@
-"""Markov-chain Monte Carlo over real-space configurations (Sec. 2.1.1-2).
+"""Markov-chain Monte Carlo over real-space configurations (Sec. 3.1.1-2).
 
-Moves (Sec. 2.1.2, Fig. update (a), (b)):
+Moves (Sec. 3.1.2, Fig. update (a), (b)):
 * hop: one electron moves to another site (not allowed under the
   local-spin constraint);
 * exchange: an up and a down electron on different, singly occupied sites

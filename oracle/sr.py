@@ -1,12 +1,12 @@
-"""Stochastic reconfiguration (Sec. 2.3.1-2.3.2, Algorithm 1).
+"""Stochastic reconfiguration (Sec. 3.3.1-3.3.2, Algorithm 1).
 
 * S_km = <O_k O_m> - <O_k><O_m>, g_m = <H O_m> - <H><O_m> (real parameters,
   so Re is the identity), averages over the N_MC samples (Eq. MC).
 * Diagonal shift (the paper gives no form): S~_kk = S_kk (1 + shift_rel)
   + shift_abs.
 * Delta alpha = -dtau S~^-1 g (Eq. SR_equation_system).
-* Solve by Cholesky S~ = L L^T (Sec. 2.3.2, first paragraph) or by CG
-  (Algorithm 1) whose matrix-vector product is the SR-CG form of Sec. 2.3.2:
+* Solve by Cholesky S~ = L L^T (Sec. 3.3.2, first paragraph) or by CG
+  (Algorithm 1) whose matrix-vector product is the SR-CG form of Sec. 3.3.2:
   y = z1 - z2 with z1 = (1/N_MC) O^T (O v) and z2 = <O> (<O> . v), O the
   uncentred sample matrix.
 """

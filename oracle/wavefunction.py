@@ -1,16 +1,21 @@
 """psi(x) = <x| P_G P_J |phi_AP-Pf> for real parameters, and the
 log-derivatives O_k(x) = d ln<x|psi> / d alpha_k.
 
-* Pair-product part (Sec. 2.2.1, Eqs. Pf and AP-Pf): F_{(a up),(b down)} =
+* Pair-product part (Sec. 3.2.1, Eqs. Pf and AP-Pf): F_{(a up),(b down)} =
   f_ab, all other F_IJ = 0; <x|phi> = (Ne/2)! Pf(X) with
   X_IJ = F_IJ - F_JI over the occupied orbitals in ascending order.
-* Correlation factors (Sec. 2.2.3): P_G = exp(sum_i g_i n_i,up n_i,dn),
+* Correlation factors (Sec. 3.2.3): P_G = exp(sum_i g_i n_i,up n_i,dn),
   P_J = exp(1/2 sum_{i != j} v_ij (n_i - 1)(n_j - 1)).  Under the
-  local-spin constraint (g -> -infinity, Sec. 2.2.3) a doubly occupied site
+  local-spin constraint (g -> -infinity, Sec. 3.2.3) a doubly occupied site
   gives psi = 0.
-* O_k (Sec. 2.3.1): Gutzwiller O = D_k(x); Jastrow O = sum over the class
+* O_k (Sec. 3.3.1): Gutzwiller O = D_k(x); Jastrow O = sum over the class
   of (n_i - 1)(n_j - 1) for i < j; pair orbital dPf/dF_AB = -Pf(X) (X^-1)_AB
   (Eq. DiffPf and Appendix C), summed over the class with the class sign.
+* Optional learned correlation factor (not in the paper): an MLP on the
+  spin-resolved occupations n (n_c, c = i + Ns*sigma), multiplying psi by
+  exp(w2 . tanh(W1 n + b1) + b2); its O_k are the derivatives of that
+  exponent: dW1_kc = w2_k (1 - tanh^2 h_k) n_c, db1_k = w2_k (1 - tanh^2 h_k),
+  dw2_k = tanh h_k, db2 = 1.
 """
 import math
 
@@ -41,6 +46,25 @@ class Wavefunction:
         F = np.zeros((2 * Ns, 2 * Ns))
         F[:Ns, Ns:] = self.f
         self.F = F
+        self.n_h = int(getattr(prob, "n_hidden", 0) or 0)
+        if self.n_h:
+            H, C = self.n_h, 2 * Ns
+            b = self.n_g + self.n_v + self.n_f
+            self.W1 = p[b:b + H * C].reshape(H, C)
+            self.b1 = p[b + H * C:b + H * C + H]
+            self.w2 = p[b + H * C + H:b + H * C + 2 * H]
+            self.b2 = float(p[b + H * C + 2 * H])
+
+    def occ_vector(self, n):
+        up, dn = self.occ(n)
+        return np.concatenate([up, dn])
+
+    def mlp_log(self, n):
+        """w2 . tanh(W1 n + b1) + b2 (0 without the MLP factor)."""
+        if not self.n_h:
+            return 0.0
+        h = self.W1 @ self.occ_vector(n) + self.b1
+        return float(self.w2 @ np.tanh(h) + self.b2)
 
     # -- configuration helpers -------------------------------------------
     def occ(self, n):
@@ -69,7 +93,7 @@ class Wavefunction:
         s, l = pfaffian_slog(X)
         if s == 0.0:
             return 0.0, -math.inf
-        return s, l + math.lgamma(self.Ne // 2 + 1) + self.log_correlation(n)
+        return s, l + math.lgamma(self.Ne // 2 + 1) + self.log_correlation(n) + self.mlp_log(n)
 
     def amplitude(self, n):
         s, l = self.amplitude_slog(n)
@@ -87,10 +111,10 @@ class Wavefunction:
 
     # -- log-derivatives -------------------------------------------------
     def log_derivatives(self, n):
-        """O_k(x) for all parameters, analytic (Sec. 2.3.1, Appendix C)."""
+        """O_k(x) for all parameters, analytic (Sec. 3.3.1, Appendix C)."""
         Ns = self.Ns
         up, dn = self.occ(n)
-        out = np.zeros(self.n_g + self.n_v + self.n_f)
+        out = np.zeros(self.params.size)
         # Gutzwiller: d/dg_k of sum_i g_i D_i = number of doublons in class k.
         gi = np.asarray(self.prob.g_idx).reshape(Ns)
         for i in range(Ns):
@@ -119,6 +143,16 @@ class Wavefunction:
                 if B not in pos or fi[a, b] < 0:
                     continue
                 out[base + fi[a, b]] += fs[a, b] * (-Xinv[pos[a], pos[B]])
+        if self.n_h:
+            H, C = self.n_h, 2 * Ns
+            nv = self.occ_vector(n)
+            t = np.tanh(self.W1 @ nv + self.b1)
+            d = self.w2 * (1.0 - t * t)
+            b = self.n_g + self.n_v + self.n_f
+            out[b:b + H * C] = np.outer(d, nv).reshape(-1)
+            out[b + H * C:b + H * C + H] = d
+            out[b + H * C + H:b + H * C + 2 * H] = t
+            out[b + H * C + 2 * H] = 1.0
         return out
 
     def log_derivatives_fd(self, n, h=1e-6):

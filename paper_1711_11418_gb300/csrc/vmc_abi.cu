@@ -165,6 +165,7 @@ int validate_system(const vmc_model *m, int32_t Ne, const vmc_layout *l, const d
         m->J_i[k] == m->J_j[k])
       return VMC_EINVAL;
   if (l->n_g < 0 || l->n_v < 0 || l->n_f < 1) return VMC_EINVAL;
+  if (l->n_hidden < 0 || l->n_hidden > 4096) return VMC_EINVAL;
   if (!l->f_idx || !l->f_sign) return VMC_EINVAL;
   if (l->n_g && !l->g_idx) return VMC_EINVAL;
   if (l->n_v && !l->v_idx) return VMC_EINVAL;
@@ -182,8 +183,10 @@ int validate_system(const vmc_model *m, int32_t Ne, const vmc_layout *l, const d
     if (l->f_idx[q] < -1 || l->f_idx[q] >= l->n_f) return VMC_EINVAL;
     if (l->f_sign[q] != 1 && l->f_sign[q] != -1 && l->f_idx[q] >= 0) return VMC_EINVAL;
   }
-  const int Np = l->n_g + l->n_v + l->n_f;
-  for (int k = 0; k < Np; ++k)
+  const long long nm = l->n_hidden ? (long long)l->n_hidden * 2 * Ns + 2LL * l->n_hidden + 1 : 0;
+  const long long Np = (long long)l->n_g + l->n_v + l->n_f + nm;
+  if (Np > (1LL << 30)) return VMC_EINVAL;
+  for (long long k = 0; k < Np; ++k)
     if (!isfinite(params[k])) return VMC_EINVAL;
   return VMC_OK;
 }
@@ -353,7 +356,8 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     s.n_g = l.n_g;
     s.n_v = l.n_v;
     s.n_f = l.n_f;
-    s.Np = l.n_g + l.n_v + l.n_f;
+    const int H = l.n_hidden;
+    s.Np = l.n_g + l.n_v + l.n_f + (H ? H * 2 * m.Ns + 2 * H + 1 : 0);
     s.ldO = (s.Np + 3) / 4 * 4;
     s.W = o->n_walkers;
     s.max_samples = o->max_samples;
@@ -420,12 +424,21 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dalloc(c, &d.fT32, sizeof(float) * n2))) return fail(rc);
     if ((rc = dalloc(c, &d.vmat, sizeof(double) * n2))) return fail(rc);
     if ((rc = dalloc(c, &d.gsite, sizeof(double) * Ns))) return fail(rc);
+    if ((rc = dalloc(c, &d.vmat32, sizeof(float) * n2))) return fail(rc);
+    if ((rc = dalloc(c, &d.gsite32, sizeof(float) * Ns))) return fail(rc);
+    d.n_hidden = H;
+    d.mlp_base = l.n_g + l.n_v + l.n_f;
+    if (H) {
+      if ((rc = dalloc(c, &d.W1T64, sizeof(double) * (size_t)H * 2 * Ns))) return fail(rc);
+      if ((rc = dalloc(c, &d.W1T16, 2 * (size_t)H * 2 * Ns))) return fail(rc);
+      if ((rc = dalloc(c, &d.hmlp, (size_t)esize * H * o->n_walkers))) return fail(rc);
+    }
     const size_t W = s.W;
     const size_t mb = ((size_t)s.N * s.ldm * esize + 127) / 128 * 128;
     if ((rc = dalloc(c, &d.ele, sizeof(int) * W * s.Ne))) return fail(rc);
     if ((rc = dalloc(c, &d.occ, sizeof(int) * W * 2 * Ns))) return fail(rc);
     if ((rc = dalloc(c, &d.minv, mb * W))) return fail(rc);
-    if ((rc = dalloc(c, &d.jf, sizeof(double) * W * Ns))) return fail(rc);
+    if ((rc = dalloc(c, &d.jf, (size_t)esize * W * Ns))) return fail(rc);
     if ((rc = dupload(c, &d.ctr, (const unsigned long long *)nullptr, W))) return fail(rc);
     if ((rc = dupload(c, &d.logdet, (const double *)nullptr, W))) return fail(rc);
     if ((rc = dupload(c, &d.detsign, (const int *)nullptr, W))) return fail(rc);
@@ -440,8 +453,8 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dupload(c, &d.E, (const double *)nullptr, rows_cap))) return fail(rc);
     if ((rc = dalloc(c, &d.O, (size_t)esize * rows_cap * s.ldO))) return fail(rc);
     int acc_len = 0;
-    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, &acc_len));
-    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, &acc_len));
+    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, H, &acc_len));
+    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, H, &acc_len));
     d.acc_len = acc_len;
     c->smem_init = std::max(c->smem_init, vmc_init_smem(s.N, s.Ns));
     if (vmc_launch_expand(&d, c->st, &c->n_launch) != cudaSuccess) return fail(VMC_ECUDA);
@@ -749,11 +762,14 @@ int vmc_get_sr_matrices(vmc_ctx *c, int32_t system, double shift_rel, double shi
 int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report *rep) {
   if (!sys_ok(c, system) || !o) return VMC_EINVAL;
   if (!(o->dtau > 0.0) || o->shift_rel < 0.0 || o->shift_abs < 0.0) return VMC_EINVAL;
-  if (o->solver != VMC_SOLVE_CHOLESKY && o->solver != VMC_SOLVE_CG) return VMC_EINVAL;
+  if (o->solver != VMC_SOLVE_CHOLESKY && o->solver != VMC_SOLVE_CG &&
+      o->solver != VMC_SOLVE_CG_DENSE)
+    return VMC_EINVAL;
   SysHost &s = c->sys[system];
   if (!s.rows) return VMC_ESTATE;
   const bool chol = o->solver == VMC_SOLVE_CHOLESKY;
-  CK(sr_alloc(c, s, chol));
+  const bool dense = o->solver == VMC_SOLVE_CG_DENSE;
+  CK(sr_alloc(c, s, chol || dense));
   SrWork &w = s.sr;
   TimedRegion tr(c, 2);
   CKC(vmc_sr_means(w, c->st, &c->n_launch));
@@ -764,10 +780,12 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
     const int rc = vmc_sr_cholesky_solve(w, c->st, &c->n_launch);
     if (rc) return rc;
   } else {
-    CKC(vmc_sr_diag(w, c->st, &c->n_launch));
     const double eps = o->cg_eps > 0.0 ? o->cg_eps : 1e-10;
     const int kmax = o->cg_kmax > 0 ? o->cg_kmax : 1000;
-    const int rc = vmc_sr_cg_solve(w, o->shift_rel, o->shift_abs, eps, kmax, &iters, c->st, &c->n_launch);
+    if (dense) CK(build_S(c, s, o->shift_rel, o->shift_abs));
+    else CKC(vmc_sr_diag(w, c->st, &c->n_launch));
+    const int rc = vmc_sr_cg_solve(w, o->shift_rel, o->shift_abs, eps, kmax, &iters, c->st,
+                                   &c->n_launch, dense ? 1 : 0);
     if (rc) return rc;
   }
   double gg = 0.0, xx = 0.0, eb = 0.0;

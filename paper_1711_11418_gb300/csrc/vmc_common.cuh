@@ -42,11 +42,12 @@ struct SysDev {
   float *f32, *fT32;
   double *vmat;                // v_ij [Ns*Ns]
   double *gsite;               // g_i [Ns]
+  float *vmat32, *gsite32;     // FP32 copies (mixed form)
   // walker state
   int *ele;                    // [W*Ne]
   int *occ;                    // [W*2*Ns]: occ[s*Ns + i] = label or -1
   void *minv;                  // [W*N*ldm] (double or float)
-  double *jf;                  // [W*Ns] Jastrow field sum_{j != i} v_ij (n_j - 1)
+  void *jf;                    // [W*Ns] Jastrow field sum_{j != i} v_ij (n_j - 1) (double or float)
   unsigned long long *ctr;     // [W] Philox proposal counters
   double *logdet;              // [W]
   int *detsign;                // [W]
@@ -60,7 +61,13 @@ struct SysDev {
   int *status;                 // [W]
   double *drift;               // [W]
   int recompute_every;         // accepted moves between FP64 from-scratch inverses (0 = never)
-  int pad_;
+  // MLP correlation factor exp(w2 . tanh(W1 n + b1) + b2) (H = 0: absent);
+  // params hold [W1 (H x 2Ns) | b1 | w2 | b2] after the pair orbitals.
+  int n_hidden;
+  int mlp_base;
+  double *W1T64;               // [2Ns][H] FP64 (column c of W1 contiguous)
+  void *W1T16;                 // [2Ns][H] BF16 copy (mixed form)
+  void *hmlp;                  // [W][H] pre-activations h = W1 n + b1 (double or float)
 };
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its published
@@ -96,7 +103,7 @@ cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker,
                                    int precision, int n_moves, const int *d_moves,
                                    double *d_out, size_t smem, cudaStream_t st,
                                    long long *n_launch);
-size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int *acc_len);
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int *acc_len);
 size_t vmc_init_smem(int N, int Ns);
 int vmc_sample_occupancy(int precision, size_t smem);
 cudaError_t vmc_walker_set_smem_limits(size_t smem_sample64, size_t smem_sample32,
@@ -125,7 +132,7 @@ cudaError_t vmc_sr_build_g(const SrWork &w, cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_diag(const SrWork &w, cudaStream_t st, long long *nl);
 int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl);
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
-                    int kmax, int *iters, cudaStream_t st, long long *nl);
+                    int kmax, int *iters, cudaStream_t st, long long *nl, int dense);
 void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad);
 cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
                               double shift_abs, cudaStream_t st, long long *nl);

@@ -1,4 +1,4 @@
-// Stochastic reconfiguration kernels (mVMC paper, Sec. 2.3.1-2.3.2):
+// Stochastic reconfiguration kernels (mVMC paper, Sec. 3.3.1-3.3.2):
 //   o_k = <O_k>, E = <E_loc>,
 //   S_km = <O_k O_m> - <O_k><O_m>  =  (1/N_MC) sum_mu (O_k,mu - o_k)(O_m,mu - o_m),
 //   g_m  = <E O_m> - <E><O_m>      =  (1/N_MC) sum_mu (O_m,mu - o_m)(E_mu - E),
@@ -569,7 +569,7 @@ int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl) {
   return info ? -4 : 0;
 }
 
-// One SR-CG product out = S~ v (Sec. 2.3.2): t = O v, u = O^T t / rows,
+// One SR-CG product out = S~ v (Sec. 3.3.2): t = O v, u = O^T t / rows,
 // out = u - o (o . v) + shift terms.  2 (rows + 1) Np products for the S part.
 static cudaError_t srcg_matvec(const SrWork &w, const double *v, double *out, double shift_rel,
                                double shift_abs, const int *done, cudaStream_t st, long long *nl) {
@@ -589,10 +589,23 @@ static cudaError_t srcg_matvec(const SrWork &w, const double *v, double *out, do
   return cudaGetLastError();
 }
 
+// Dense product out = S~ v with S~ (shift included) stored row-major (one warp per row).
+__global__ void k_gemv_dense(const double *S, int n, const double *v, double *out, const int *done) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= n || *done) return;
+  const double *r = S + (size_t)row * n;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) s += r[k] * v[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[row] = s;
+}
+
 // Algorithm 1 with x0 = 0, run on the device in batches of iterations; the
 // host reads the convergence flag once per batch.  w.r holds 2 Np doubles.
+// dense = 0: SR-CG product from O (S never formed); dense = 1: product with
+// the dense S~ in w.S.
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps, int kmax,
-                    int *iters, cudaStream_t st, long long *nl) {
+                    int *iters, cudaStream_t st, long long *nl, int dense) {
   const int n = w.Np, g = (n + 255) / 256;
   int *flags = w.info;
   double *cg = w.scal;
@@ -606,7 +619,12 @@ int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double 
   int h[3] = {0, 0, 0};
   for (int k = 1; k <= kmax; ++k) {
     double *rho = cg + ((k - 1) & 1), *rho_new = cg + (k & 1);
-    if (srcg_matvec(w, w.p, w.w, shift_rel, shift_abs, flags, st, nl) != cudaSuccess) return -3;
+    if (dense) {
+      k_gemv_dense<<<(int)(((size_t)n * 32 + 255) / 256), 256, 0, st>>>(w.S, n, w.p, w.w, flags);
+      ++*nl;
+    } else if (srcg_matvec(w, w.p, w.w, shift_rel, shift_abs, flags, st, nl) != cudaSuccess) {
+      return -3;
+    }
     k_dot_dev<<<1, 256, 0, st>>>(w.p, w.w, n, cg + 2, flags);
     k_cg_update_xr<<<g, 256, 0, st>>>(w.x, w.r, w.p, w.w, rho, cg + 2, n, flags);
     k_cg_check<<<1, 256, 0, st>>>(w.r, n, rho_new, cg + 4, flags);

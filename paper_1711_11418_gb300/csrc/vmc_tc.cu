@@ -1,5 +1,5 @@
 // SR overlap matrix on the tensor cores (tcgen05, sm_103a):
-//   S = (1/N_MC) (O - o)^T (O - o)          (Sec. 2.3.1, S_km = <O_k O_m> - <O_k><O_m>)
+//   S = (1/N_MC) (O - o)^T (O - o)          (Sec. 3.3.1, S_km = <O_k O_m> - <O_k><O_m>)
 // in split-BF16: every centred entry x = x_hi + x_lo with x_hi = bf16(x),
 // x_lo = bf16(x - x_hi); each product takes the three terms
 // hi*hi + hi*lo + lo*hi (the lo*lo term is below 2^-16 relative), accumulated

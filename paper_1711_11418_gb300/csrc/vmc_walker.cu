@@ -2,19 +2,20 @@
 // the Metropolis sweep with fast Pfaffian-ratio updates, and the per-sample
 // measurement of E_loc and the O_k row.
 //
-// Wave function (mVMC paper, Sec. 2.2): psi(x) = P_G P_J <x|phi_AP-Pf>.  For
+// Wave function (mVMC paper, Sec. 3.2): psi(x) = P_G P_J <x|phi_AP-Pf>.  For
 // S^z = 0 and the anti-parallel form (Eq. AP-Pf) the Ne x Ne skew matrix X of
-// Sec. 2.2.1 is block off-diagonal, X = [[0, M], [-M^T, 0]] with
+// Sec. 3.2.1 is block off-diagonal, X = [[0, M], [-M^T, 0]] with
 // M_nm = f(r_n,up, r_m,dn), so Pf X = (-1)^{N(N-1)/2} det M and
 // X^-1 = [[0, -M^-T], [M^-1, 0]].  Each walker keeps M^-1 (N x N).
 //
-// Fast updates (Sec. 2.1.2, "Sherman-Morrison-type update"): a hop of up
+// Fast updates (Sec. 3.1.2, "Sherman-Morrison-type update"): a hop of up
 // electron n replaces row n of M, a hop of down electron m replaces column m;
 // an exchange replaces both (rank-2).  Ratios are det M'/det M from the
 // matrix-determinant lemma; the inverse follows by Sherman-Morrison
 // (rank 1) or Woodbury (rank 2).
 #include "vmc_common.cuh"
 
+#include <cuda_bf16.h>
 #include <math.h>
 
 namespace {
@@ -92,45 +93,52 @@ struct WSmem {
   T *acc;       // O-row accumulator (acc_len)
   T *red;       // 2 buffers x 8
   T *bc;        // 2 broadcast scalars (double-buffered like red)
-  double *jf;   // Ns
+  T *jf;        // Ns
   double *dred; // 2 buffers x 8 (double reductions)
   int *ele;     // Ne
   int *occ;     // 2 Ns
   int *ilist;   // Ns
   int *misc;    // 8
   uint4 *rnd;   // NT Philox draws (one batch)
+  T *hm;        // MLP pre-activations h (H)
+  T *th;        // tanh(h) (H)
 };
 
 template <typename T>
-__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, unsigned char *base, WSmem<T> *sm) {
+__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, unsigned char *base,
+                                         WSmem<T> *sm) {
   const int ldm = (N % 2) ? N : N + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return o; };
   const size_t o_minv = take(minv_bytes(N, ldm, sizeof(T)));
   const size_t o_vec = take(sizeof(T) * 8 * VMC_MAX_N);
   const size_t o_acc = take(sizeof(T) * (size_t)acc_len);
-  const size_t o_red = take(sizeof(T) * 16);
+  const size_t o_red = take(sizeof(T) * 32);
   const size_t o_bc = take(sizeof(T) * 2);
-  const size_t o_jf = take(sizeof(double) * Ns);
-  const size_t o_dred = take(sizeof(double) * 16);
+  const size_t o_jf = take(sizeof(T) * Ns);
+  const size_t o_dred = take(sizeof(double) * 32);
   const size_t o_ele = take(sizeof(int) * 2 * N);
   const size_t o_occ = take(sizeof(int) * 2 * Ns);
   const size_t o_il = take(sizeof(int) * Ns);
   const size_t o_misc = take(sizeof(int) * 8);
   const size_t o_rnd = take(sizeof(uint4) * NT);
+  const size_t o_hm = take(sizeof(T) * (size_t)H);
+  const size_t o_th = take(sizeof(T) * (size_t)H);
   if (sm) {
     sm->minv = (T *)(base + o_minv);
     sm->vec = (T *)(base + o_vec);
     sm->acc = (T *)(base + o_acc);
     sm->red = (T *)(base + o_red);
     sm->bc = (T *)(base + o_bc);
-    sm->jf = (double *)(base + o_jf);
+    sm->jf = (T *)(base + o_jf);
     sm->dred = (double *)(base + o_dred);
     sm->ele = (int *)(base + o_ele);
     sm->occ = (int *)(base + o_occ);
     sm->ilist = (int *)(base + o_il);
     sm->misc = (int *)(base + o_misc);
     sm->rnd = (uint4 *)(base + o_rnd);
+    sm->hm = (T *)(base + o_hm);
+    sm->th = (T *)(base + o_th);
   }
   return off;
 }
@@ -148,9 +156,9 @@ template <typename T>
 __device__ __forceinline__ T block_sum(T v, T *red, int &buf) {
   v = warp_sum(v);
   const int warp = threadIdx.x >> 5;
-  if ((threadIdx.x & 31) == 0) red[buf * 8 + warp] = v;
+  if ((threadIdx.x & 31) == 0) red[buf * 16 + warp] = v;
   __syncthreads();
-  const T *r = red + buf * 8;
+  const T *r = red + buf * 16;
   T s = r[0];
 #pragma unroll
   for (int k = 1; k < NWARP; ++k) s += r[k];
@@ -164,11 +172,11 @@ __device__ __forceinline__ void block_sum2(T a, T b, T *red, int &buf, T &A, T &
   b = warp_sum(b);
   const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    red[buf * 8 + warp] = a;
-    red[buf * 8 + 4 + warp] = b;
+    red[buf * 16 + warp] = a;
+    red[buf * 16 + 4 + warp] = b;
   }
   __syncthreads();
-  const T *r = red + buf * 8;
+  const T *r = red + buf * 16;
   A = r[0];
   B = r[4];
 #pragma unroll
@@ -179,21 +187,105 @@ __device__ __forceinline__ void block_sum2(T a, T b, T *red, int &buf, T &A, T &
   buf ^= 1;
 }
 
-// log of the correlation-factor ratio P(x')/P(x) for a hop of a spin-s
-// electron from site r to site t (Sec. 2.2.3): Gutzwiller g_t n_t,-s - g_r n_r,-s
-// and Jastrow h_t - h_r - v_rt with h_i = sum_{j != i} v_ij (n_j - 1).
-__device__ __forceinline__ double corr_hop(const SysDev &S, const int *occ, const double *jf,
-                                           int s, int r, int t) {
-  const int Ns = S.Ns;
-  const int o = (1 - s) * Ns;
-  double d = jf[t] - jf[r] - S.vmat[(size_t)r * Ns + t];
-  d += (occ[o + t] >= 0 ? S.gsite[t] : 0.0) - (occ[o + r] >= 0 ? S.gsite[r] : 0.0);
+template <typename T>
+__device__ __forceinline__ void block_sum3(T a, T b, T c, T *red, int &buf, T &A, T &B, T &C) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int warp = threadIdx.x >> 5;
+  T *r = red + buf * 16;
+  if ((threadIdx.x & 31) == 0) {
+    r[warp] = a;
+    r[4 + warp] = b;
+    r[8 + warp] = c;
+  }
+  __syncthreads();
+  A = r[0];
+  B = r[4];
+  C = r[8];
+#pragma unroll
+  for (int k = 1; k < NWARP; ++k) {
+    A += r[k];
+    B += r[4 + k];
+    C += r[8 + k];
+  }
+  buf ^= 1;
+}
+
+// ---- MLP correlation factor -------------------------------------------------
+// Column c = site + Ns * spin of W1 (H entries, contiguous): FP64 in the plain
+// form, BF16 (FP32 arithmetic) in the mixed form.
+template <typename T> __device__ __forceinline__ T w1c(const SysDev &S, int c, int k);
+template <> __device__ __forceinline__ double w1c<double>(const SysDev &S, int c, int k) {
+  return S.W1T64[(size_t)c * S.n_hidden + k];
+}
+template <> __device__ __forceinline__ float w1c<float>(const SysDev &S, int c, int k) {
+  return __bfloat162float(((const __nv_bfloat16 *)S.W1T16)[(size_t)c * S.n_hidden + k]);
+}
+template <typename T> __device__ __forceinline__ T tanh_t(T x);
+template <> __device__ __forceinline__ double tanh_t<double>(double x) { return tanh(x); }
+template <> __device__ __forceinline__ float tanh_t<float>(float x) { return tanhf(x); }
+template <typename T> __device__ __forceinline__ T exp_t(T x);
+template <> __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+template <> __device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+
+// Change of h for a move: + column cp0 (+ cp1) - column cm0 (- cm1); cp1/cm1 < 0: unused.
+template <typename T>
+__device__ __forceinline__ T mlp_dh(const SysDev &S, int k, int cp0, int cm0, int cp1, int cm1) {
+  T d = w1c<T>(S, cp0, k) - w1c<T>(S, cm0, k);
+  if (cp1 >= 0) d += w1c<T>(S, cp1, k) - w1c<T>(S, cm1, k);
   return d;
 }
 
-template <typename T> __device__ __forceinline__ T corr_factor(double dlog);
+// This thread's share (k = tid, tid + NT, ...) of
+// log P_MLP(x')/P_MLP(x) = sum_k w2_k (tanh(h_k + dh_k) - tanh(h_k)).
+template <typename T>
+__device__ __forceinline__ T mlp_log_ratio_part(const SysDev &S, const WSmem<T> &sm, int cp0,
+                                                int cm0, int cp1, int cm1, int k0, int kstep) {
+  const int H = S.n_hidden;
+  const double *w2 = S.params + S.mlp_base + (size_t)H * 2 * S.Ns + H;
+  T part = (T)0;
+  for (int k = k0; k < H; k += kstep)
+    part += (T)w2[k] * (tanh_t<T>(sm.hm[k] + mlp_dh<T>(S, k, cp0, cm0, cp1, cm1)) - sm.th[k]);
+  return part;
+}
+
+template <typename T>
+__device__ __forceinline__ void mlp_apply(const SysDev &S, const WSmem<T> &sm, int cp0, int cm0,
+                                          int cp1, int cm1) {
+  for (int k = threadIdx.x; k < S.n_hidden; k += NT) {
+    const T h = sm.hm[k] + mlp_dh<T>(S, k, cp0, cm0, cp1, cm1);
+    sm.hm[k] = h;
+    sm.th[k] = tanh_t<T>(h);
+  }
+}
+
+// log of the correlation-factor ratio P(x')/P(x) for a hop of a spin-s
+// electron from site r to site t (Sec. 3.2.3): Gutzwiller g_t n_t,-s - g_r n_r,-s
+// and Jastrow h_t - h_r - v_rt with h_i = sum_{j != i} v_ij (n_j - 1).
+template <typename T> __device__ __forceinline__ const T *vtab(const SysDev &s);
+template <> __device__ __forceinline__ const double *vtab<double>(const SysDev &s) { return s.vmat; }
+template <> __device__ __forceinline__ const float *vtab<float>(const SysDev &s) { return s.vmat32; }
+template <typename T> __device__ __forceinline__ const T *gtab(const SysDev &s);
+template <> __device__ __forceinline__ const double *gtab<double>(const SysDev &s) { return s.gsite; }
+template <> __device__ __forceinline__ const float *gtab<float>(const SysDev &s) { return s.gsite32; }
+
+// In the sweep's arithmetic type (FP32 in the mixed form: GB300's FP64 pipe
+// is too slow for per-proposal work).
+template <typename T>
+__device__ __forceinline__ T corr_hop(const SysDev &S, const int *occ, const T *jf, int s, int r,
+                                      int t) {
+  const int Ns = S.Ns;
+  const int o = (1 - s) * Ns;
+  const T *g = gtab<T>(S);
+  T d = jf[t] - jf[r] - vtab<T>(S)[(size_t)r * Ns + t];
+  d += (occ[o + t] >= 0 ? g[t] : (T)0) - (occ[o + r] >= 0 ? g[r] : (T)0);
+  return d;
+}
+
+template <typename T> __device__ __forceinline__ T corr_factor(T dlog);
 template <> __device__ __forceinline__ double corr_factor<double>(double dlog) { return exp(dlog); }
-template <> __device__ __forceinline__ float corr_factor<float>(double dlog) { return expf((float)dlog); }
+template <> __device__ __forceinline__ float corr_factor<float>(float dlog) { return expf(dlog); }
 
 // ---------------------------------------------------------------------------
 // Pfaffian ratios (block-wide; every thread returns the same value)
@@ -202,9 +294,10 @@ template <> __device__ __forceinline__ float corr_factor<float>(double dlog) { r
 // (up electron n = e, new row R_l = f(t, r_l,dn)) or
 // sum_k (M^-1)_{m k} C_k (down electron m = e - N, new column C_k = f(r_k,up, t)).
 // fval receives this thread's entry of the new row/column.
+// With the MLP factor, mlp receives log P_MLP(x')/P_MLP(x) (same barrier).
 template <typename T>
 __device__ __forceinline__ T hop_pf_ratio(const SysDev &S, const WSmem<T> &sm, int e, int t,
-                                          T &fval, int &buf) {
+                                          T &fval, int &buf, T &mlp) {
   const int N = S.N, Ns = S.Ns, tid = threadIdx.x;
   T prod = (T)0;
   fval = (T)0;
@@ -217,7 +310,15 @@ __device__ __forceinline__ T hop_pf_ratio(const SysDev &S, const WSmem<T> &sm, i
       prod = sm.minv[(e - N) * S.ldm + tid] * fval;
     }
   }
-  return block_sum(prod, sm.red, buf);
+  if (!S.n_hidden) {
+    mlp = (T)0;
+    return block_sum(prod, sm.red, buf);
+  }
+  const int sp = (e >= N) ? Ns : 0;
+  const T part = mlp_log_ratio_part(S, sm, t + sp, sm.ele[e] + sp, -1, -1, tid, NT);
+  T A;
+  block_sum2(prod, part, sm.red, buf, A, mlp);
+  return A;
 }
 
 // Exchange of up electron n (site i) with down electron m (site j):
@@ -230,7 +331,7 @@ __device__ __forceinline__ T hop_pf_ratio(const SysDev &S, const WSmem<T> &sm, i
 // On return vB holds w = R^T M^-1, vC holds C, K[0..3] the 2x2 matrix.
 template <typename T>
 __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m, int i, int j,
-                               int &buf, T *K) {
+                               int &buf, T *K, T &mlp) {
   const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
   const T *F = ftab<T>(S);
   const T *FT = fTtab<T>(S);
@@ -262,7 +363,14 @@ __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m
     }
   }
   T A22, A12;
-  block_sum2(a22, a12, sm.red, buf, A22, A12);
+  if (S.n_hidden) {
+    // up electron i -> j, down electron j -> i: +(i,dn) -(i,up) +(j,up) -(j,dn)
+    const T part = mlp_log_ratio_part(S, sm, i + Ns, i, j, j + Ns, tid, NT);
+    block_sum3(a22, a12, part, sm.red, buf, A22, A12, mlp);
+  } else {
+    block_sum2(a22, a12, sm.red, buf, A22, A12);
+    mlp = (T)0;
+  }
   const T A11 = vB[n];
   const T A21 = sm.minv[m * ldm + n];
   K[0] = A11;
@@ -354,7 +462,7 @@ __device__ void exchange_update(const SysDev &S, const WSmem<T> &sm, int n, int 
 }
 
 // ---------------------------------------------------------------------------
-// One Metropolis proposal (Sec. 2.1.2).  Every thread runs it; decisions are
+// One Metropolis proposal (Sec. 3.1.2).  Every thread runs it; decisions are
 // uniform across the block.
 // ---------------------------------------------------------------------------
 struct MoveCounts {
@@ -385,10 +493,12 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
     const int i = sm.ele[n], j = sm.ele[m];
     if (i == j || sm.occ[Ns + i] >= 0 || sm.occ[j] >= 0) return;
     mc.ex_t++;
-    T K[4];
-    const T ratio = exchange_pf_ratio(S, sm, n, m - N, i, j, buf, K);
+    T K[4], mlp;
+    const T rpf = exchange_pf_ratio(S, sm, n, m - N, i, j, buf, K, mlp);
+    const T ratio = S.n_hidden ? rpf * exp_t<T>(mlp) : rpf;
     if (u < ratio * ratio) {
-      exchange_update(S, sm, n, m - N, j, K, ratio);
+      exchange_update(S, sm, n, m - N, j, K, rpf);
+      if (S.n_hidden) mlp_apply(S, sm, i + Ns, i, j, j + Ns);
       if (tid == 0) {
         sm.ele[n] = j;
         sm.ele[m] = i;
@@ -412,18 +522,19 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   mc.hop_t++;
   // P(x')/P(x): one thread evaluates it; the barrier inside hop_pf_ratio publishes it.
   const int slot = buf;
-  if (tid == 0) sm.bc[slot] = corr_factor<T>(corr_hop(S, sm.occ, sm.jf, s, rs, t));
-  T fval;
-  const T rpf = hop_pf_ratio(S, sm, e, t, fval, buf);
-  const T ratio = rpf * sm.bc[slot];
+  if (tid == 0) sm.bc[slot] = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, s, rs, t));
+  T fval, mlp;
+  const T rpf = hop_pf_ratio(S, sm, e, t, fval, buf, mlp);
+  const T ratio = S.n_hidden ? rpf * sm.bc[slot] * exp_t<T>(mlp) : rpf * sm.bc[slot];
   if (!(u < ratio * ratio)) return;
   if (tid < N) sm.vec[tid] = fval;
   __syncthreads();
   if (s == 0) row_update(S, sm, e);
   else col_update(S, sm, e - N);
+  if (S.n_hidden) mlp_apply(S, sm, t + s * Ns, rs + s * Ns, -1, -1);
   // Jastrow field: h_x += v_{x t} - v_{x r}.
   for (int x = tid; x < Ns; x += NT)
-    sm.jf[x] += S.vmat[(size_t)t * Ns + x] - S.vmat[(size_t)rs * Ns + x];
+    sm.jf[x] += vtab<T>(S)[(size_t)t * Ns + x] - vtab<T>(S)[(size_t)rs * Ns + x];
   if (tid == 0) {
     sm.ele[e] = t;
     sm.occ[s * Ns + rs] = -1;
@@ -435,7 +546,7 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// Measurement: E_loc (Eq. MC with A = H) and the O_k row (Sec. 2.3.1)
+// Measurement: E_loc (Eq. MC with A = H) and the O_k row (Sec. 3.3.1)
 // ---------------------------------------------------------------------------
 // Warp-level exchange ratio (same formula as exchange_pf_ratio) for the
 // Heisenberg S+S- terms of E_loc.  R, Wp: per-warp scratch vectors.
@@ -482,29 +593,29 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
   const int warp = tid >> 5, lane = tid & 31;
   const T *F = ftab<T>(S);
   const T *FT = fTtab<T>(S);
-  // --- diagonal terms
-  double ed = 0.0;
+  // --- diagonal terms (per-thread partial sums in T, one FP64 block sum)
+  T ed = (T)0;
   for (int i = tid; i < Ns; i += NT) {
     const int up = sm.occ[i] >= 0, dn = sm.occ[Ns + i] >= 0;
-    ed += S.U[i] * (double)(up * dn);
+    if (up && dn) ed += (T)S.U[i];
   }
   for (int k = tid; k < S.n_V; k += NT) {
     const int a = S.V_i[k], b = S.V_j[k];
     const int na = (sm.occ[a] >= 0) + (sm.occ[Ns + a] >= 0);
     const int nb = (sm.occ[b] >= 0) + (sm.occ[Ns + b] >= 0);
-    ed += S.V_val[k] * (double)(na * nb);
+    ed += (T)S.V_val[k] * (T)(na * nb);
   }
   for (int k = tid; k < S.n_J; k += NT) {
     const int a = S.J_i[k], b = S.J_j[k];
-    const double sa = 0.5 * ((sm.occ[a] >= 0) - (sm.occ[Ns + a] >= 0));
-    const double sb = 0.5 * ((sm.occ[b] >= 0) - (sm.occ[Ns + b] >= 0));
-    ed += S.J_val[k] * sa * sb;
+    const int sa = (sm.occ[a] >= 0) - (sm.occ[Ns + a] >= 0);
+    const int sb = (sm.occ[b] >= 0) - (sm.occ[Ns + b] >= 0);
+    ed += (T)S.J_val[k] * (T)(0.25f * (float)(sa * sb));
   }
   // --- hopping, one warp per target site i: the warp gathers the rows
   // f(i, r_m,dn) and f(r_n,up, i) once (lane-strided), then every electron on a
   // neighbouring site j that can hop to i gives a Green-function ratio as a dot
   // product with a column (row) of M^-1, times the correlation-factor ratio.
-  double eo = 0.0;
+  T eo = (T)0;
   for (int i = warp; i < Ns; i += NWARP) {
     const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
     if (kb == ke) continue;
@@ -528,8 +639,10 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
           if (q < N) part += gu[u] * sm.minv[q * ldm + eu];
         }
         part = warp_sum(part);
+        const T lm = S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i, j, -1, -1, lane, 32)) : (T)0;
         if (lane == 0) {
-          eo += -S.hop_t[k] * (double)part * (double)corr_factor<T>(corr_hop(S, sm.occ, sm.jf, 0, j, i));
+          eo += -(T)S.hop_t[k] * part * corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 0, j, i)) *
+                (S.n_hidden ? exp_t<T>(lm) : (T)1);
           mc.meas_hop++;
         }
       }
@@ -542,8 +655,11 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
           if (q < N) part += gd[u] * row[q];
         }
         part = warp_sum(part);
+        const T lm =
+            S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i + Ns, j + Ns, -1, -1, lane, 32)) : (T)0;
         if (lane == 0) {
-          eo += -S.hop_t[k] * (double)part * (double)corr_factor<T>(corr_hop(S, sm.occ, sm.jf, 1, j, i));
+          eo += -(T)S.hop_t[k] * part * corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, j, i)) *
+                (S.n_hidden ? exp_t<T>(lm) : (T)1);
           mc.meas_hop++;
         }
       }
@@ -567,12 +683,14 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     }
     if (!ok || a == b) continue;
     const T r = exchange_pf_ratio_warp(S, sm, nu, md - N, a, b, R, Wp);
+    const T lm =
+        S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, a + Ns, a, b, b + Ns, lane, 32)) : (T)0;
     if (lane == 0) {
-      eo += -0.5 * S.J_val[k] * (double)r;
+      eo += (T)(-0.5 * S.J_val[k]) * r * (S.n_hidden ? exp_t<T>(lm) : (T)1);
       mc.meas_ex++;
     }
   }
-  const double etot = block_sum(ed + eo, sm.dred, buf);
+  const double etot = block_sum((double)ed + (double)eo, sm.dred, buf);
   if (tid == 0) S.E[(size_t)w * S.n_samples + row] = etot;
 
   // --- O_k row
@@ -580,7 +698,9 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
   const bool sh = S.acc_len > 0;
   T *acc = sh ? sm.acc : Orow;
   const int len = sh ? S.acc_len : S.ldO;
-  for (int k = tid; k < len; k += NT) acc[k] = (T)0;
+  const int mlp_lo = S.n_hidden ? S.mlp_base : S.Np;   // the MLP part is written, not accumulated
+  for (int k = tid; k < len; k += NT)
+    if (sh || k < mlp_lo || k >= S.Np) acc[k] = (T)0;
   if (tid == 0) sm.misc[0] = 0;
   __syncthreads();
   if (S.n_g > 0) {
@@ -615,6 +735,24 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     if (cls < 0) continue;
     const T v = sm.minv[m * ldm + n];
     acc_add(acc + base + cls, S.f_sign[ab] > 0 ? v : -v);
+  }
+  if (S.n_hidden) {
+    // MLP factor: dW1_kc = w2_k (1 - t_k^2) n_c, db1_k = w2_k (1 - t_k^2),
+    // dw2_k = t_k, db2 = 1, with t = tanh(h); n_c = occ[c] >= 0 (c = i + Ns s).
+    const int H = S.n_hidden, C = 2 * Ns;
+    const double *w2 = S.params + S.mlp_base + (size_t)H * C + H;
+    T *Om = acc + S.mlp_base;
+    for (size_t q = tid; q < (size_t)H * C; q += NT) {
+      const int k = (int)(q / C), c = (int)(q - (size_t)k * C);
+      const T tk = sm.th[k];
+      Om[q] = (sm.occ[c] >= 0) ? (T)w2[k] * ((T)1 - tk * tk) : (T)0;
+    }
+    for (int k = tid; k < H; k += NT) {
+      const T tk = sm.th[k];
+      Om[(size_t)H * C + k] = (T)w2[k] * ((T)1 - tk * tk);
+      Om[(size_t)H * C + H + k] = tk;
+    }
+    if (tid == 0) Om[(size_t)H * C + 2 * H] = (T)1;
   }
   __syncthreads();
   if (sh)
@@ -764,7 +902,7 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     const int w = wk.y;
     const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
     WSmem<T> sm;
-    walker_layout<T>(N, Ns, S.acc_len, smem_raw, &sm);
+    walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, smem_raw, &sm);
     // --- load the walker: M^-1 block by a TMA bulk copy, configuration and
     // Jastrow field by plain loads while the copy is in flight
     const uint32_t nbytes = (uint32_t)minv_bytes(N, ldm, sizeof(T));
@@ -772,7 +910,12 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
       if (tid == 0) bulk_load(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, nbytes, &bar);
       for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
       for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
-      for (int k = tid; k < Ns; k += NT) sm.jf[k] = S.jf[(size_t)w * Ns + k];
+      for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
+      for (int k = tid; k < S.n_hidden; k += NT) {
+        const T h = ((const T *)S.hmlp)[(size_t)w * S.n_hidden + k];
+        sm.hm[k] = h;
+        sm.th[k] = tanh_t<T>(h);
+      }
     }
     const bool loaded = mbar_wait(&bar, phase);
     phase ^= 1;
@@ -810,8 +953,9 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     {
       if (tid == 0) bulk_store((unsigned char *)S.minv + (size_t)w * nbytes, sm.minv, nbytes);
       for (int k = tid; k < Ne; k += NT) S.ele[(size_t)w * Ne + k] = sm.ele[k];
+      for (int k = tid; k < S.n_hidden; k += NT) ((T *)S.hmlp)[(size_t)w * S.n_hidden + k] = sm.hm[k];
       for (int k = tid; k < 2 * Ns; k += NT) S.occ[(size_t)w * 2 * Ns + k] = sm.occ[k];
-      for (int k = tid; k < Ns; k += NT) S.jf[(size_t)w * Ns + k] = sm.jf[k];
+      for (int k = tid; k < Ns; k += NT) ((T *)S.jf)[(size_t)w * Ns + k] = sm.jf[k];
       if (tid == 0) {
         const long long total = props_first + (long long)n_samples * sweeps_between * Ne;
         S.ctr[w] = ctr;
@@ -845,11 +989,28 @@ __global__ void k_expand(SysDev S) {
     S.f32[q] = (float)f;
     S.fT32[(size_t)j * Ns + i] = (float)f;
     const int vc = S.v_idx[q];
-    S.vmat[q] = (vc >= 0 && i != j) ? S.params[S.n_g + vc] : 0.0;
+    const double vv = (vc >= 0 && i != j) ? S.params[S.n_g + vc] : 0.0;
+    S.vmat[q] = vv;
+    S.vmat32[q] = (float)vv;
     if (q < (size_t)Ns) {
       const int gc = S.g_idx[q];
-      S.gsite[q] = (gc >= 0) ? S.params[gc] : 0.0;
+      const double gv = (gc >= 0) ? S.params[gc] : 0.0;
+      S.gsite[q] = gv;
+      S.gsite32[q] = (float)gv;
     }
+  }
+}
+
+// MLP weights: W1 (H x 2Ns, row-major in params) -> column-major copies.
+__global__ void k_expand_mlp(SysDev S) {
+  const int H = S.n_hidden, C = 2 * S.Ns;
+  const size_t tot = (size_t)H * C;
+  for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < tot;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(q / C), c = (int)(q - (size_t)k * C);
+    const double v = S.params[S.mlp_base + q];
+    S.W1T64[(size_t)c * H + k] = v;
+    ((__nv_bfloat16 *)S.W1T16)[(size_t)c * H + k] = __double2bfloat16(v);
   }
 }
 
@@ -922,8 +1083,11 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
         S.occ[(size_t)w * 2 * Ns + s * Ns + ele[k]] = k;
       }
       __syncthreads();
-      // Jastrow field h_i = sum_{j != i} v_ij (n_j - 1): only sites with
-      // n_j != 1 contribute; v is symmetric, so row j is read (coalesced).
+    }
+    {
+      // Jastrow field h_i = sum_{j != i} v_ij (n_j - 1), rebuilt in FP64 on
+      // every from-scratch inverse: only sites with n_j != 1 contribute; v is
+      // symmetric, so row j is read (coalesced).
       int *nsite = perm + N;        // [Ns] n_j
       int *jlist = nsite + Ns;      // [Ns] sites with n_j != 1
       int *jcount = jlist + Ns;     // [1]
@@ -942,8 +1106,16 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
           const int j = jlist[q];
           h += S.vmat[(size_t)j * Ns + i] * (double)(nsite[j] - 1);
         }
-        S.jf[(size_t)w * Ns + i] = h;
+        ((T *)S.jf)[(size_t)w * Ns + i] = (T)h;
       }
+      __syncthreads();
+    }
+    // MLP pre-activations from scratch: h_k = b1_k + sum over electrons of W1[k][c_e]
+    for (int k = tid; k < S.n_hidden; k += NT) {
+      const int H = S.n_hidden;
+      double h = S.params[S.mlp_base + (size_t)H * 2 * Ns + k];
+      for (int e = 0; e < Ne; ++e) h += S.W1T64[(size_t)(ele[e] + (e >= N ? Ns : 0)) * H + k];
+      ((T *)S.hmlp)[(size_t)w * H + k] = (T)h;
     }
     if (tid == 0) {
       S.acc_since[w] = 0;
@@ -971,13 +1143,18 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
   load_sys(&S, systems + sys);
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
   WSmem<T> sm;
-  walker_layout<T>(N, Ns, S.acc_len, smem_raw, &sm);
+  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, smem_raw, &sm);
   const size_t nb = minv_bytes(N, ldm, sizeof(T));
   const T *src = (const T *)((const unsigned char *)S.minv + (size_t)w * nb);
   for (int k = tid; k < N * ldm; k += NT) sm.minv[k] = src[k];
   for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
   for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
-  for (int k = tid; k < Ns; k += NT) sm.jf[k] = S.jf[(size_t)w * Ns + k];
+  for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
+  for (int k = tid; k < S.n_hidden; k += NT) {
+    const T h = ((const T *)S.hmlp)[(size_t)w * S.n_hidden + k];
+    sm.hm[k] = h;
+    sm.th[k] = tanh_t<T>(h);
+  }
   __syncthreads();
   int buf = 0;
   for (int q = 0; q < n_moves; ++q) {
@@ -987,16 +1164,18 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
       if (a >= 0 && a < Ne && b >= 0 && b < Ns) {
         const int s = (a >= N) ? 1 : 0;
         if (sm.occ[s * Ns + b] < 0 && !(S.local_spin && sm.occ[(1 - s) * Ns + b] >= 0)) {
-          T fval;
-          const T rpf = hop_pf_ratio(S, sm, a, b, fval, buf);
-          res = (double)rpf * exp(corr_hop(S, sm.occ, sm.jf, s, sm.ele[a], b));
+          T fval, mlp;
+          const T rpf = hop_pf_ratio(S, sm, a, b, fval, buf, mlp);
+          res = (double)rpf * (double)corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, s, sm.ele[a], b)) *
+                (S.n_hidden ? (double)exp_t<T>(mlp) : 1.0);
         }
       }
     } else if (a >= 0 && a < N && b >= N && b < Ne) {
       const int i = sm.ele[a], j = sm.ele[b];
       if (i != j && sm.occ[Ns + i] < 0 && sm.occ[j] < 0) {
-        T K[4];
-        res = (double)exchange_pf_ratio(S, sm, a, b - N, i, j, buf, K);
+        T K[4], mlp;
+        res = (double)exchange_pf_ratio(S, sm, a, b - N, i, j, buf, K, mlp) *
+              (S.n_hidden ? (double)exp_t<T>(mlp) : 1.0);
       }
     }
     if (tid == 0) out[q] = res;
@@ -1009,11 +1188,11 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers
 // ---------------------------------------------------------------------------
-size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int *acc_len) {
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int *acc_len) {
   const int al = (Np <= VMC_ACC_MAX) ? Np : 0;
   if (acc_len) *acc_len = al;
-  return precision == 0 ? walker_layout<double>(N, Ns, al, nullptr, nullptr)
-                        : walker_layout<float>(N, Ns, al, nullptr, nullptr);
+  return precision == 0 ? walker_layout<double>(N, Ns, al, H, nullptr, nullptr)
+                        : walker_layout<float>(N, Ns, al, H, nullptr, nullptr);
 }
 
 size_t vmc_init_smem(int N, int Ns) {
@@ -1046,6 +1225,10 @@ cudaError_t vmc_launch_expand(const SysDev *h_sys, cudaStream_t st, long long *n
   const int grid = (int)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096);
   k_expand<<<grid, 256, 0, st>>>(*h_sys);
   ++*nl;
+  if (h_sys->n_hidden) {
+    k_expand_mlp<<<1024, 256, 0, st>>>(*h_sys);
+    ++*nl;
+  }
   return cudaGetLastError();
 }
 

@@ -8,10 +8,10 @@ the CPU oracle receive the arrays it returns.
 Conventions (they follow the paper's Standard-mode models):
 
 * Sites ``i = x + Lx*y``; spin-orbital ``I = i + Ns*sigma`` (sigma = 0 up,
-  1 down), as in the definition of the Pfaffian wave function (Sec. 2.2.1).
+  1 down), as in the definition of the Pfaffian wave function (Sec. 3.2.1).
 * Hopping terms are directed: a term ``(i, j, t)`` stands for
   ``-t c^dag_{i sigma} c_{j sigma}`` for both spins (the Hubbard model of
-  Sec. 2.1); every bond is listed in both directions with the same real t.
+  Sec. 2.3); every bond is listed in both directions with the same real t.
   Anti-periodic boundaries multiply t across the cell boundary by -1
   (Appendix A, phase = pi).
 * Heisenberg bonds ``(i, j, J)`` stand for ``J S_i . S_j``, each bond once.
@@ -129,7 +129,7 @@ def heisenberg_bonds(lat: Lattice, J1: float = 1.0, J2: float = 0.0):
 # ---------------------------------------------------------------------------
 def sublattice_f_layout(lat: Lattice, Wsub: int, Lsub: int):
     """Pair-orbital classes under the Wsub x Lsub sublattice structure of
-    Sec. 2.2.1 (sublattice paragraph) with the boundary signs of Appendix A.
+    Sec. 3.2.1 (sublattice paragraph) with the boundary signs of Appendix A.
 
     The pair (i, j) is translated by the lattice vector that brings i into
     the sublattice unit cell; j follows and collects the anti-periodic sign.
@@ -304,6 +304,7 @@ class Problem:
     n_f: int
     params: np.ndarray
     p_exchange: float
+    n_hidden: int = 0
     V_i: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     V_j: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     V_val: np.ndarray = field(default_factory=lambda: np.zeros(0))
@@ -318,8 +319,13 @@ class Problem:
         return self.Ne // 2
 
     @property
+    def n_mlp(self) -> int:
+        H, C = self.n_hidden, 2 * self.lat.Ns
+        return H * C + 2 * H + 1 if H > 0 else 0
+
+    @property
     def Np(self) -> int:
-        return self.n_g + self.n_v + self.n_f
+        return self.n_g + self.n_v + self.n_f + self.n_mlp
 
     def f_matrix(self, params=None) -> np.ndarray:
         p = self.params if params is None else params
@@ -337,7 +343,7 @@ class Problem:
 def make_problem(name, lat, Ne, *, t=1.0, t2=0.0, U=0.0, J1=0.0, J2=0.0,
                  local_spin=False, sub=(1, 1), f_full=False, jastrow="none",
                  gutzwiller=True, noise=0.05, seed=0, p_exchange=None,
-                 f_init="pairing"):
+                 f_init="pairing", mlp_hidden=0, mlp_std=0.01):
     Ns = lat.Ns
     N = Ne // 2
     hop = hopping_terms(lat, t, t2) if (t != 0.0 or t2 != 0.0) else (
@@ -372,6 +378,11 @@ def make_problem(name, lat, Ne, *, t=1.0, t2=0.0, U=0.0, J1=0.0, J2=0.0,
     if noise:
         pf = pf + rng.uniform(-noise, noise, n_f)
     params = np.concatenate([np.zeros(n_g), np.zeros(n_v), pf])
+    if mlp_hidden:
+        # MLP correlation factor [W1 (H x 2Ns, row-major) | b1 (H) | w2 (H) | b2],
+        # weights and biases N(0, mlp_std^2), seeded after the pair orbitals.
+        H, C = int(mlp_hidden), 2 * Ns
+        params = np.concatenate([params, rng.normal(0.0, mlp_std, H * C + 2 * H + 1)])
     if p_exchange is None:
         p_exchange = 1.0 if local_spin else (0.5 if U >= 4.0 else 0.0)
     return Problem(name=name, lat=lat, Ne=Ne, hop_i=hop[0], hop_j=hop[1],
@@ -379,7 +390,7 @@ def make_problem(name, lat, Ne, *, t=1.0, t2=0.0, U=0.0, J1=0.0, J2=0.0,
                    ex_j=ex[1], ex_J=ex[2], local_spin=bool(local_spin),
                    g_idx=g_idx, n_g=n_g, v_idx=v_idx, n_v=n_v, f_idx=f_idx,
                    f_sign=f_sign, n_f=n_f, params=params,
-                   p_exchange=float(p_exchange))
+                   p_exchange=float(p_exchange), n_hidden=int(mlp_hidden))
 
 
 def ring8_hubbard(noise=0.05, seed=0, U=4.0):
@@ -401,6 +412,15 @@ def square16_hubbard(noise=0.05, seed=0, U=8.0, Ne=224):
     sublattice f (1024) + distance Jastrow (44) + Gutzwiller (1)."""
     return make_problem("square16_hubbard", square(16, 16, -1, -1), Ne, U=U,
                         sub=(2, 2), jastrow="distance", noise=noise, seed=seed)
+
+
+def square16_hubbard_mlp(hidden=1024, noise=0.05, seed=0, U=8.0, Ne=224):
+    """The 16x16 Hubbard workload times an MLP correlation factor
+    (512 occupations -> `hidden` tanh units -> one log-amplitude),
+    weights initialised N(0, 0.01^2)."""
+    return make_problem("square16_hubbard_mlp", square(16, 16, -1, -1), Ne, U=U,
+                        sub=(2, 2), jastrow="distance", noise=noise, seed=seed,
+                        mlp_hidden=hidden)
 
 
 def j1j2_heisenberg(L=16, J2=0.5, noise=0.05, seed=0):

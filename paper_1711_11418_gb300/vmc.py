@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvmc.so")
 
 FP64, MIXED = 0, 1
-CHOLESKY, CG = 0, 1
+CHOLESKY, CG, CG_DENSE = 0, 1, 2
 _I32P = C.POINTER(C.c_int32)
 _F64P = C.POINTER(C.c_double)
 _I8P = C.POINTER(C.c_int8)
@@ -32,7 +32,8 @@ class VmcModel(C.Structure):
 
 class VmcLayout(C.Structure):
     _fields_ = [("n_g", C.c_int32), ("n_v", C.c_int32), ("n_f", C.c_int32),
-                ("g_idx", _I32P), ("v_idx", _I32P), ("f_idx", _I32P), ("f_sign", _I8P)]
+                ("g_idx", _I32P), ("v_idx", _I32P), ("f_idx", _I32P), ("f_sign", _I8P),
+                ("n_hidden", C.c_int32)]
 
 
 class VmcOpts(C.Structure):
@@ -149,7 +150,7 @@ class _Arrays:
             _p(self.J_j, _I32P), _p(self.J_val, _F64P), int(prob.local_spin))
         self.layout = VmcLayout(prob.n_g, prob.n_v, prob.n_f, _p(self.g_idx, _I32P),
                                 _p(self.v_idx, _I32P), _p(self.f_idx, _I32P),
-                                _p(self.f_sign, _I8P))
+                                _p(self.f_sign, _I8P), int(getattr(prob, "n_hidden", 0) or 0))
 
 
 class Context:

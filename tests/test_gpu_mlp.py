@@ -1,0 +1,132 @@
+"""GPU parity of the learned MLP correlation factor (not in the paper):
+psi(x) = P_G P_J <x|phi_AP-Pf> exp(w2 . tanh(W1 n + b1) + b2).
+
+FP64 form against the oracle at 1e-10 (ratios, E_loc, O_k incl. the MLP
+gradients, chains bit-exact); mixed form (BF16 W1, FP32 arithmetic) against
+the FP64 form; and what the trained factor gains over the plain state."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.exact import enumerate_expectations
+from oracle.sampler import run_sampling
+from oracle.sr import sr_step
+from oracle.wavefunction import Wavefunction
+from paper_1711_11418_gb300 import inputs as I
+
+from helpers import condition_ok, oracle_measure, oracle_ratio, random_moves
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vmc():
+    from paper_1711_11418_gb300 import build, vmc as V
+    build.build()
+    return V
+
+
+def mlp_problems():
+    return {
+        "ring8_h5": I.make_problem("ring8_h5", I.chain(8, 1), 8, U=4.0, sub=(2, 1), jastrow="chain",
+                                   noise=0.05, seed=1, mlp_hidden=5, mlp_std=0.3),
+        "square4_h16": I.make_problem("sq4_h16", I.square(4, 4, 1, -1), 12, U=4.0, sub=(2, 2),
+                                      jastrow="distance", noise=0.05, seed=2, mlp_hidden=16,
+                                      mlp_std=0.2),
+        "heis4_h8": I.make_problem("heis4_h8", I.square(4, 4, 1, -1), 16, t=0.0, J1=1.0,
+                                   local_spin=True, sub=(2, 2), gutzwiller=False, noise=0.1,
+                                   seed=3, mlp_hidden=8, mlp_std=0.3),
+    }
+
+
+def good_configs(p, W, seed):
+    wf = Wavefunction(p)
+    out, s = [], seed
+    while len(out) < W:
+        c = I.initial_configs(p.Ns, p.Ne, 1, p.local_spin, s)[0]
+        s += 1
+        if condition_ok(wf, c):
+            out.append(c)
+    return np.array(out, np.int32)
+
+
+@pytest.mark.parametrize("name", ["ring8_h5", "square4_h16", "heis4_h8"])
+def test_mlp_ratios_energy_and_gradients(vmc, name):
+    p = mlp_problems()[name]
+    W = 3
+    cfg = good_configs(p, W, 50)
+    wf = Wavefunction(p)
+    rng = np.random.default_rng(4)
+    with vmc.Context(p, W, seed=7, max_samples=1) as ctx:
+        ctx.set_configs(cfg)
+        for w in range(W):
+            moves = random_moves(rng, cfg[w], p.N, p.Ns, p.local_spin, 16)
+            got = ctx.eval_ratios(w, moves)
+            ref = np.array([oracle_ratio(wf, cfg[w], m) for m in moves])
+            big = np.abs(ref) > 1e-8
+            assert np.all(np.abs(got[big] - ref[big]) <= 1e-10 * np.abs(ref[big]) + 1e-14)
+        ctx.sample(0, 1, 0)
+        E, O = ctx.get_samples()
+    for w in range(W):
+        e_ref, o_ref = oracle_measure(wf, cfg[w])
+        assert E[w] == pytest.approx(e_ref, rel=1e-10, abs=1e-10)
+        assert np.max(np.abs(O[w] - o_ref)) <= 1e-10 * max(1.0, np.max(np.abs(o_ref)))
+
+
+def test_mlp_chain_bit_exact_and_sr(vmc):
+    p = mlp_problems()["ring8_h5"]
+    W, S = 2, 6
+    cfg = good_configs(p, W, 80)
+    wf = Wavefunction(p)
+    with vmc.Context(p, W, seed=99, max_samples=S) as ctx:
+        ctx.set_configs(cfg)
+        ctx.sample(2, S, 1)
+        ele, _ = ctx.get_configs()
+        E, O = ctx.get_samples()
+        p0 = ctx.get_params()
+        ctx.sr_step(0.05, 1e-2, 1e-4, solver=vmc.CG, cg_eps=1e-12)
+        d = ctx.get_params() - p0
+    ref = run_sampling(wf, cfg, 99, 0, 2, S, 1, p.p_exchange)
+    assert np.array_equal(ele, ref["ele"])
+    assert np.allclose(E, ref["E"], rtol=1e-10, atol=1e-10)
+    dref, _ = sr_step(ref["E"], ref["O"], 0.05, 1e-2, 1e-4, "cg", cg_eps=1e-12)
+    assert np.max(np.abs(d - dref)) <= 1e-8 * np.max(np.abs(dref))
+
+
+def test_mlp_mixed_form_close_to_fp64(vmc):
+    p = mlp_problems()["square4_h16"]
+    W = 4
+    cfg = good_configs(p, W, 90)
+    res = {}
+    for prec in (vmc.FP64, vmc.MIXED):
+        with vmc.Context(p, W, seed=7, precision=prec, max_samples=1) as ctx:
+            ctx.set_configs(cfg)
+            ctx.sample(0, 1, 0)
+            res[prec] = ctx.get_samples()
+    # BF16 weights: |dW1| <= 2^-9 |W1| per entry -> log-amplitude shifts ~1e-3
+    assert np.max(np.abs(res[vmc.FP64][0] - res[vmc.MIXED][0])) / p.Ns < 5e-3
+    assert np.allclose(res[vmc.FP64][1], res[vmc.MIXED][1], rtol=2e-2, atol=2e-2)
+
+
+def test_trained_mlp_gains_over_plain_state(vmc):
+    """Same SR budget on the 6-site ring (U/t = 8): the exact energy of the
+    trained Pfaffian x MLP state (by enumeration) lies below that of the
+    trained plain state, and both above the exact ground state."""
+    from oracle.hamiltonian import ground_state_energy
+    plain = I.make_problem("r6", I.chain(6, -1), 6, U=8.0, sub=(2, 1), jastrow="chain",
+                           noise=0.05, seed=5, p_exchange=0.5)
+    with_mlp = I.make_problem("r6m", I.chain(6, -1), 6, U=8.0, sub=(2, 1), jastrow="chain",
+                              noise=0.05, seed=5, p_exchange=0.5, mlp_hidden=8, mlp_std=0.01)
+    e_ed = ground_state_energy(plain)
+    out = {}
+    for name, p in (("plain", plain), ("mlp", with_mlp)):
+        with vmc.Context(p, 256, seed=3, max_samples=20) as ctx:
+            ctx.sample(10, 0, 0)
+            for _ in range(60):
+                ctx.sample(0, 20, 1)
+                ctx.sr_step(0.05, 1e-3, 1e-4, solver=vmc.CG, cg_eps=1e-8, cg_kmax=500)
+            params = ctx.get_params()
+        out[name] = enumerate_expectations(Wavefunction(p, params))["energy"]
+    assert out["plain"] >= e_ed - 1e-9 and out["mlp"] >= e_ed - 1e-9
+    assert out["mlp"] < out["plain"], out

@@ -62,7 +62,7 @@ def test_philox_known_answers():
 
 
 # --------------------------------------------------------------------------
-# Pfaffian (Sec. 2.2.1: Pf^2 = det; Appendix C: Pf(B A B^T) = det B Pf A)
+# Pfaffian (Sec. 3.2.1: Pf^2 = det; Appendix C: Pf(B A B^T) = det B Pf A)
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n", [2, 4, 6, 8])
 def test_pfaffian_matches_definition(n):
@@ -114,7 +114,7 @@ def test_pfaffian_zero():
 
 def test_pair_state_expansion_is_pfaffian():
     """<x|[sum F_IJ c+_I c+_J]^{Ne/2}|0> = (Ne/2)! Pf(X), X_IJ = F_IJ - F_JI,
-    by expanding the pair operator power in the Fock basis (Sec. 2.2.1)."""
+    by expanding the pair operator power in the Fock basis (Sec. 3.2.1)."""
     rng = np.random.default_rng(11)
     norb, Ne = 6, 4
     F = rng.standard_normal((norb, norb))
@@ -354,3 +354,22 @@ def test_cg_solves_spd_system():
     x, it = cg(lambda v: A @ v, b, eps=1e-14)
     assert np.allclose(A @ x, b, atol=1e-10)
     assert np.allclose(solve_cholesky(A, b), x, atol=1e-10)
+
+
+def test_mlp_factor_derivatives_and_limit():
+    """MLP correlation factor: analytic O_k against finite differences, and
+    w2 = b2 = 0 reduces psi to the plain projected Pfaffian."""
+    p = I.make_problem("r6m", I.chain(6, -1), 6, U=4.0, sub=(2, 1), jastrow="chain",
+                       noise=0.2, seed=4, mlp_hidden=3, mlp_std=0.3)
+    wf = Wavefunction(p)
+    c = I.initial_configs(6, 6, 1, False, 9)[0]
+    n = fock.from_labels(c, 6)
+    a = wf.log_derivatives(n)
+    b = wf.log_derivatives_fd(n, 1e-6)
+    assert np.allclose(a, b, rtol=1e-6, atol=1e-7)
+    q = p.params.copy()
+    base = p.n_g + p.n_v + p.n_f + 3 * 12
+    q[base + 3:] = 0.0                      # w2 = 0, b2 = 0
+    plain = p.copy_with(n_hidden=0, params=p.params[:p.n_g + p.n_v + p.n_f])
+    assert Wavefunction(p, q).amplitude_slog(n)[1] == pytest.approx(
+        Wavefunction(plain).amplitude_slog(n)[1], rel=1e-14)
