@@ -241,6 +241,38 @@ int64_t vmc_kernel_launches(vmc_ctx *ctx);
 int vmc_enable_timing(vmc_ctx *ctx, int32_t on);
 int vmc_kernel_times(vmc_ctx *ctx, double *ms, int64_t *count);
 
+/* Allocation-free SR means and force.  No counterpart in the paper: it is an
+ * access path for callers that cannot let this library allocate device memory
+ * (for example because another allocator already owns the GPU's memory, or
+ * because cudaMalloc/cudaFree may synchronise the device inside a
+ * latency-sensitive loop).  It computes, from caller-owned DEVICE arrays,
+ *   ebar[0] = <E>,  obar[k] = <O_k>,  g[k] = <(O_k - obar_k)(E - ebar)>
+ * over `rows` samples -- the quantities vmc_sr_step and vmc_get_sr_matrices
+ * form from a context's stored FP32 samples, with the same chunked FP64 sums.
+ *   O: rows x ldO FP32, row-major (ldO >= Np); E: rows FP64;
+ *   obar, g: Np FP64 outputs; ebar: 1 FP64 output; stream: cudaStream_t or
+ *   NULL for the default stream.  The work is queued on `stream`; the call
+ *   returns without synchronising.
+ * It calls no cudaMalloc, cudaFree or other allocating routine.  Its only
+ * scratch (partial column sums over 2048-row chunks) is a fixed array of
+ * VMC_FORCE_STATIC_MAX_DOUBLES doubles (8 MiB) inside the library, present
+ * on every GPU that loads the library until the process exits.
+ * Requirements and limits:
+ *  - ceil(rows / 2048) * Np <= VMC_FORCE_STATIC_MAX_DOUBLES, else VMC_EINVAL
+ *    (nothing is launched); VMC_EINVAL also for NULL pointers, rows < 1,
+ *    Np < 1 or ldO < Np.
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current); make that first call before any stream capture.
+ *  - Every call uses the same array.  Each call writes every scratch entry it
+ *    reads, so no state carries over, but calls that overlap on the GPU (on
+ *    different streams or host threads) race on it and must be serialised by
+ *    the caller.
+ * Errors: VMC_EINVAL as above, VMC_ECUDA if a CUDA call fails. */
+#define VMC_FORCE_STATIC_MAX_DOUBLES (1 << 20)
+int vmc_sr_force_static(const float *O, int32_t ldO, int32_t rows, int32_t Np,
+                        const double *E, double *obar, double *g, double *ebar,
+                        void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvmc.so")
 
 FP64, MIXED = 0, 1
+FORCE_STATIC_MAX_DOUBLES = 1 << 20
 CHOLESKY, CG, CG_DENSE = 0, 1, 2
 _I32P = C.POINTER(C.c_int32)
 _F64P = C.POINTER(C.c_double)
@@ -75,7 +76,7 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_get_configs", "vmc_sample", "vmc_measure", "vmc_get_samples", "vmc_set_samples",
            "vmc_sr_step", "vmc_get_sr_matrices", "vmc_get_params", "vmc_set_params",
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
-           "vmc_enable_timing", "vmc_kernel_times"]
+           "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static"]
 
 
 def load(path: str = LIB_PATH):
@@ -111,6 +112,7 @@ def load(path: str = LIB_PATH):
     L.vmc_get_inverse.argtypes = [P, C.c_int32, C.c_int32, _F64P, _F64P, _I32P]
     L.vmc_enable_timing.argtypes = [P, C.c_int32]
     L.vmc_kernel_times.argtypes = [P, _F64P, C.POINTER(C.c_int64)]
+    L.vmc_sr_force_static.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P]
     L.vmc_kernel_launches.argtypes = [P]
     L.vmc_kernel_launches.restype = C.c_int64
     for name in EXPORTS:
