@@ -235,9 +235,10 @@ int64_t vmc_kernel_launches(vmc_ctx *ctx);
 /* Kernel timing with CUDA events on the context's stream (no counterpart in
  * the paper; used to report achieved throughput).  vmc_enable_timing(ctx, 1)
  * starts recording; vmc_kernel_times writes the accumulated milliseconds and
- * launch counts since the last reset into ms[3] and count[3], indexed by
+ * launch counts since the last reset into ms[4] and count[4], indexed by
  * 0 = sweep/measure kernel, 1 = from-scratch inverse kernel, 2 = SR step
- * (all its kernels), and resets them.  Synchronises the stream. */
+ * (all its kernels), 3 = dense S build (within 2, or by vmc_get_sr_matrices),
+ * and resets them.  Synchronises the stream. */
 int vmc_enable_timing(vmc_ctx *ctx, int32_t on);
 int vmc_kernel_times(vmc_ctx *ctx, double *ms, int64_t *count);
 

@@ -27,6 +27,7 @@ struct SysHost {
   bool S_alloc = false;
   void *tc_hi = nullptr, *tc_lo = nullptr;   // split-BF16 operands (mixed form)
   int *tc_status = nullptr;
+  int2 *tc_tiles = nullptr;                   // tile order of the S GEMM
 };
 
 }  // namespace
@@ -47,11 +48,11 @@ struct vmc_ctx {
   long long n_launch = 0;
   double *d_scalar = nullptr;
   int recompute_every = 0;
-  // timing (CUDA events on st): 0 sweep, 1 init, 2 SR
+  // timing (CUDA events on st): 0 sweep, 1 init, 2 SR step, 3 S GEMM
   bool timing = false;
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
-  double ms[3] = {0, 0, 0};
-  long long cnt[3] = {0, 0, 0};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
+  double ms[4] = {0, 0, 0, 0};
+  long long cnt[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -209,7 +210,7 @@ struct TimedRegion {
 };
 
 void collect_times(vmc_ctx *c) {
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     for (auto &p : c->ev[k]) {
       float t = 0.f;
       if (cudaEventSynchronize(p.second) == cudaSuccess &&
@@ -286,6 +287,10 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
       CK(dalloc(c, &s.tc_hi, 2 * (size_t)Np_pad * ldK));
       CK(dalloc(c, &s.tc_lo, 2 * (size_t)Np_pad * ldK));
       CK(dalloc(c, &s.tc_status, sizeof(int) * 4));
+      const int ntile = vmc_tc_tile_list(s.Np, nullptr);
+      std::vector<int2> tl(ntile);
+      vmc_tc_tile_list(s.Np, tl.data());
+      CK(dupload(c, &s.tc_tiles, tl.data(), tl.size()));
     }
     s.S_alloc = true;
   }
@@ -300,9 +305,10 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
 
 // Dense S~: FP64 SIMT GEMM (plain form) or split-BF16 tensor-core GEMM (mixed).
 int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
+  TimedRegion tr(c, 3);
   if (c->precision == VMC_MIXED) {
-    CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, c->st,
-                          &c->n_launch));
+    CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, s.tc_tiles,
+                          c->st, &c->n_launch));
     int bad = 0;
     CKC(cudaMemcpyAsync(&bad, s.tc_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CKC(cudaStreamSynchronize(c->st));
@@ -402,6 +408,16 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
       for (int k = 0; k < m.n_hop; ++k) term[fill[m.hop_i[k]]++] = k;
       if ((rc = dupload(c, (int **)&d.tgt_ptr, ptr.data(), Ns + 1))) return fail(rc);
       if ((rc = dupload(c, (int **)&d.tgt_term, term.data(), m.n_hop))) return fail(rc);
+      std::vector<int> tj(m.n_hop);
+      std::vector<double> tt(m.n_hop);
+      for (int q = 0; q < m.n_hop; ++q) {
+        tj[q] = m.hop_j[term[q]];
+        tt[q] = m.hop_t[term[q]];
+      }
+      if ((rc = dupload(c, (int **)&d.tgt_j, tj.data(), m.n_hop))) return fail(rc);
+      if ((rc = dupload(c, (double **)&d.tgt_t, tt.data(), m.n_hop))) return fail(rc);
+      if ((rc = dalloc(c, &d.tgt_v64, sizeof(double) * (m.n_hop ? m.n_hop : 1)))) return fail(rc);
+      if ((rc = dalloc(c, &d.tgt_v32, sizeof(float) * (m.n_hop ? m.n_hop : 1)))) return fail(rc);
     }
     d.hop_t = ht;
     if ((rc = dupload(c, (double **)&d.U, m.U ? m.U : Uz.data(), Ns))) return fail(rc);
@@ -896,7 +912,7 @@ int vmc_enable_timing(vmc_ctx *c, int32_t on) {
 int vmc_kernel_times(vmc_ctx *c, double *ms, int64_t *count) {
   if (!c || !ms || !count) return VMC_EINVAL;
   collect_times(c);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < 4; ++k) {
     ms[k] = c->ms[k];
     count[k] = c->cnt[k];
     c->ms[k] = 0.0;

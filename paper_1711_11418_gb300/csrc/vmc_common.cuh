@@ -30,6 +30,10 @@ struct SysDev {
   const double *hop_t;
   const int *tgt_ptr;          // [Ns+1] hopping terms grouped by target site i (CSR)
   const int *tgt_term;         // [n_hop] term indices
+  const int *tgt_j;            // [n_hop] source site of each grouped term
+  const double *tgt_t;         // [n_hop] its t
+  double *tgt_v64;             // [n_hop] v(j, i) of each grouped term (refreshed with v)
+  float *tgt_v32;
   const double *U;
   const int *V_i, *V_j;
   const double *V_val;
@@ -134,8 +138,9 @@ int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl);
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
                     int kmax, int *iters, cudaStream_t st, long long *nl, int dense);
 void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad);
+int vmc_tc_tile_list(int Np, int2 *out);
 cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
-                              double shift_abs, cudaStream_t st, long long *nl);
+                              double shift_abs, const int2 *tiles, cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_update_params(double *params, const double *x, double dtau, int Np,
                                  cudaStream_t st, long long *nl);
 cudaError_t vmc_dot_host(const double *a, const double *b, int n, double *out_host,

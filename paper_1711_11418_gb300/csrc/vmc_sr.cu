@@ -297,56 +297,53 @@ __global__ void __launch_bounds__(256) k_syrk_trailing(double *A, int n, int j0,
     }
 }
 
-// Blocked triangular solves with the Cholesky factor (lower, row-major):
-// forward L y = b and backward L^T x = y, panels of CB rows.  The diagonal
-// block is solved by one CTA in shared memory; the rest of the vector is
-// updated by a matrix-vector product over the panel (coalesced row reads).
-__global__ void k_trsv_diag(const double *L, int n, int p0, int nb, double *y, int backward) {
-  __shared__ double D[CB][CB + 1];
-  __shared__ double v[CB];
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    D[r][c] = L[(size_t)(p0 + r) * n + p0 + c];
-  }
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) v[q] = y[p0 + q];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    if (!backward) {
+
+// Both triangular solves in one CTA of 1024 threads (x holds b on entry):
+// per panel of CB rows, warp 0 solves the diagonal block (lane-parallel dot
+// products), then all warps update the rest of the vector -- forward: one
+// warp per row over the panel's columns; backward: one thread per entry over
+// the panel's rows (both coalesced).
+__global__ void __launch_bounds__(1024) k_chol_solve_blocked(const double *L, int n, double *x) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int p0 = 0; p0 < n; p0 += CB) {
+    const int nb = min(CB, n - p0);
+    if (warp == 0) {
       for (int k = 0; k < nb; ++k) {
-        double s = v[k];
-        for (int l = 0; l < k; ++l) s -= D[k][l] * v[l];
-        v[k] = s / D[k][k];
-      }
-    } else {
-      for (int k = nb - 1; k >= 0; --k) {
-        double s = v[k];
-        for (int l = k + 1; l < nb; ++l) s -= D[l][k] * v[l];
-        v[k] = s / D[k][k];
+        double s = (lane < k) ? L[(size_t)(p0 + k) * n + p0 + lane] * x[p0 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[p0 + k] = (x[p0 + k] - s) / L[(size_t)(p0 + k) * n + p0 + k];
+        __syncwarp();
       }
     }
+    __syncthreads();
+    for (int i = p0 + nb + warp; i < n; i += nw) {
+      double s = (lane < nb) ? L[(size_t)i * n + p0 + lane] * x[p0 + lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) x[i] -= s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int q = threadIdx.x; q < nb; q += blockDim.x) y[p0 + q] = v[q];
+  for (int p0 = ((n - 1) / CB) * CB; p0 >= 0; p0 -= CB) {
+    const int nb = min(CB, n - p0);
+    if (warp == 0) {
+      for (int k = nb - 1; k >= 0; --k) {
+        double s = (lane > k && lane < nb) ? L[(size_t)(p0 + lane) * n + p0 + k] * x[p0 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) x[p0 + k] = (x[p0 + k] - s) / L[(size_t)(p0 + k) * n + p0 + k];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < p0; i += blockDim.x) {
+      double s = 0.0;
+      for (int l = 0; l < nb; ++l) s += L[(size_t)(p0 + l) * n + i] * x[p0 + l];
+      x[i] -= s;
+    }
+    __syncthreads();
+  }
 }
 
-// forward: y[i] -= sum_l L[i][p0+l] y[p0+l] for i >= p0 + nb (one warp per row)
-__global__ void k_trsv_fwd_update(const double *L, int n, int p0, int nb, double *y) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int i = p0 + nb + warp;
-  if (i >= n) return;
-  double s = (lane < nb) ? L[(size_t)i * n + p0 + lane] * y[p0 + lane] : 0.0;
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) y[i] -= s;
-}
 
-// backward: y[i] -= sum_l L[p0+l][i] x[p0+l] for i < p0 (rows p0+l read contiguously)
-__global__ void k_trsv_bwd_update(const double *L, int n, int p0, int nb, double *y) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p0) return;
-  double s = 0.0;
-  for (int l = 0; l < nb; ++l) s += L[(size_t)(p0 + l) * n + i] * y[p0 + l];
-  y[i] -= s;
-}
 
 // t = O v (one warp per row)
 template <typename TO>
@@ -548,19 +545,8 @@ int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl) {
     }
   }
   cudaMemcpyAsync(w.x, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  for (int p0 = 0; p0 < n; p0 += CB) {
-    const int nb = n - p0 < CB ? n - p0 : CB;
-    k_trsv_diag<<<1, 32, 0, st>>>(w.S, n, p0, nb, w.x, 0);
-    const int rem = n - p0 - nb;
-    if (rem > 0) k_trsv_fwd_update<<<(rem * 32 + 255) / 256, 256, 0, st>>>(w.S, n, p0, nb, w.x);
-    *nl += 1 + (rem > 0);
-  }
-  for (int p0 = ((n - 1) / CB) * CB; p0 >= 0; p0 -= CB) {
-    const int nb = n - p0 < CB ? n - p0 : CB;
-    k_trsv_diag<<<1, 32, 0, st>>>(w.S, n, p0, nb, w.x, 1);
-    if (p0 > 0) k_trsv_bwd_update<<<(p0 + 255) / 256, 256, 0, st>>>(w.S, n, p0, nb, w.x);
-    *nl += 1 + (p0 > 0);
-  }
+  k_chol_solve_blocked<<<1, 1024, 0, st>>>(w.S, n, w.x);
+  *nl += 1;
   if (cudaGetLastError() != cudaSuccess) return -3;
   int info = 0;
   if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)

@@ -25,7 +25,7 @@ namespace {
 
 constexpr int TM = 128;              // tile edge (M = N)
 constexpr int TKC = 64;              // samples per chunk (64 BF16 = 128 B per row)
-constexpr int STAGES = 2;
+constexpr int STAGES = 3;
 constexpr int TILE_BYTES = TM * TKC * 2;          // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
 constexpr int TC_SMEM = STAGES * STAGE_BYTES + 1024;
@@ -104,22 +104,34 @@ __device__ __forceinline__ uint32_t tile_off(int r, int kg) {
   return (uint32_t)((r >> 3) * 1024 + kg * 128 + (r & 7) * 16);
 }
 
+// Issue the cp.async copies of chunk kc (4 operand tiles x 128 rows x 8
+// pieces of 16 B) into one stage; 8 consecutive threads fill one core matrix.
+__device__ __forceinline__ void load_chunk(unsigned char *stage, const __nv_bfloat16 *const *src,
+                                           int ldK, int kc) {
+#pragma unroll 4
+  for (int q = threadIdx.x; q < 4 * TM * 8; q += 128) {
+    const int op = q >> 10, rem = q & 1023;
+    const int r = (rem & 7) + ((rem >> 6) << 3);
+    const int kg = (rem >> 3) & 7;
+    const __nv_bfloat16 *g = src[op] + (size_t)r * ldK + (size_t)kc * TKC + kg * 8;
+    const uint32_t d = su32(stage + op * TILE_BYTES + tile_off(r, kg));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+  }
+}
+
+// One CTA per tile of `tiles` (bi <= bj; the host orders them for L2 reuse).
+// Pipeline: STAGES - 1 chunks are in flight while the tensor cores work on
+// the current one; a stage is refilled once the MMAs that read it committed.
 template <typename TS>
 __global__ void __launch_bounds__(128, 1) k_syrk_tc(const __nv_bfloat16 *Hi, const __nv_bfloat16 *Lo,
                                                     int ldK, int K, int Np, double scale, TS *S,
-                                                    int ldS, int *status) {
+                                                    int ldS, const int2 *tiles, int *status) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t mma_bar[STAGES];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int fail;
-  // upper-triangular tile (bi <= bj)
-  const int nt = (Np + TM - 1) / TM;
-  int t = blockIdx.x, bi = 0;
-  while (t >= nt - bi) {
-    t -= nt - bi;
-    ++bi;
-  }
-  const int bj = bi + t;
+  const int2 tile = tiles[blockIdx.x];
+  const int bi = tile.x, bj = tile.y;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *base = (unsigned char *)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
   if (tid == 0) {
@@ -141,31 +153,22 @@ __global__ void __launch_bounds__(128, 1) k_syrk_tc(const __nv_bfloat16 *Hi, con
   const int nchunks = (K + TKC - 1) / TKC;
   const __nv_bfloat16 *src[4] = {Hi + (size_t)bi * TM * ldK, Lo + (size_t)bi * TM * ldK,
                                  Hi + (size_t)bj * TM * ldK, Lo + (size_t)bj * TM * ldK};
-  uint32_t phase[STAGES] = {0, 0};
+  uint32_t phase[STAGES];
+#pragma unroll
+  for (int s2 = 0; s2 < STAGES; ++s2) phase[s2] = 0;
+  // prologue: chunks 0 .. STAGES-2
+#pragma unroll
+  for (int s2 = 0; s2 < STAGES - 1; ++s2) {
+    if (s2 < nchunks) load_chunk(base + s2 * STAGE_BYTES, src, ldK, s2);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   for (int kc = 0; kc < nchunks; ++kc) {
     const int st = kc % STAGES;
     unsigned char *stage = base + st * STAGE_BYTES;
-    if (kc >= STAGES) {
-      // the MMAs that last read this stage must have completed
-      const bool ok = bar_wait(&mma_bar[st], phase[st]);
-      phase[st] ^= 1;
-      if (!ok) atomicExch(&fail, 1);
-    }
-    if (__syncthreads_or(fail)) break;
-    // producers: 4 tiles x 128 rows x 8 chunks of 16 B (cp.async, 16 B each)
-#pragma unroll 4
-    for (int q = tid; q < 4 * TM * 8; q += 128) {
-      const int op = q >> 10, rem = q & 1023;
-      const int r = (rem & 7) + ((rem >> 6) << 3);   // 8 lanes cover one core matrix
-      const int kg = (rem >> 3) & 7;
-      const __nv_bfloat16 *g = src[op] + (size_t)r * ldK + (size_t)kc * TKC + kg * 8;
-      const uint32_t d = su32(stage + op * TILE_BYTES + tile_off(r, kg));
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // chunk kc has landed when at most STAGES-2 newer groups are pending
+    asm volatile("cp.async.wait_group %0;" ::"n"(STAGES - 2) : "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    if (__syncthreads_or(fail)) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_hi = su32(stage), a_lo = su32(stage + TILE_BYTES);
@@ -180,8 +183,23 @@ __global__ void __launch_bounds__(128, 1) k_syrk_tc(const __nv_bfloat16 *Hi, con
       }
       mma_commit(&mma_bar[st]);
     }
+    // refill the stage of chunk kc-1 with chunk kc+STAGES-1, once its MMAs are done
+    const int nxt = kc + STAGES - 1;
+    if (nxt < nchunks) {
+      const int ps = nxt % STAGES;   // == (kc - 1) mod STAGES
+      bool ok = true;
+      if (kc >= 1) {
+        ok = bar_wait(&mma_bar[ps], phase[ps]);
+        phase[ps] ^= 1;
+        if (!ok) atomicExch(&fail, 1);
+      }
+      if (ok) load_chunk(base + ps * STAGE_BYTES, src, ldK, nxt);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
   }
-  // wait for the last chunk of each stage still in flight
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  // commits not yet waited for: chunks max(0, nchunks - STAGES) .. nchunks-1
+  // (the loop waited for chunks 0 .. nchunks-STAGES-1)
   if (!fail) {
     for (int kc = (nchunks > STAGES ? nchunks - STAGES : 0); kc < nchunks; ++kc) {
       const int st = kc % STAGES;
@@ -192,13 +210,15 @@ __global__ void __launch_bounds__(128, 1) k_syrk_tc(const __nv_bfloat16 *Hi, con
   if (fail && tid == 0) {
     // a wait expired: give the tensor cores a bounded chance to finish what
     // was issued before the memory they read or write is released
-    for (int s = 0; s < STAGES; ++s) bar_wait(&mma_bar[s], phase[s]);
+    for (int s2 = 0; s2 < STAGES; ++s2) bar_wait(&mma_bar[s2], phase[s2]);
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const bool bad = __syncthreads_or(fail);
   if (!bad) {
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 = tile rows
-    const int row = bi * TM + warp * 32 + lane;
+    // epilogue: TMEM -> shared tile (row-major, padded) -> coalesced rows of S
+    // and, off the diagonal, coalesced rows of the mirror image.
+    float *Ts = (float *)base;                 // 128 x 129 floats (66 KB), stages are free
+    constexpr int LDT = TM + 1;
 #pragma unroll 1
     for (int cc = 0; cc < TM; cc += 32) {
       uint32_t v[32];
@@ -214,16 +234,18 @@ __global__ void __launch_bounds__(128, 1) k_syrk_tc(const __nv_bfloat16 *Hi, con
             "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (row < Np) {
+      const int r = warp * 32 + lane;
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          const int col = bj * TM + cc + u;
-          if (col < Np) {
-            const TS val = (TS)((double)__uint_as_float(v[u]) * scale);
-            S[(size_t)row * ldS + col] = val;
-            if (bi != bj) S[(size_t)col * ldS + row] = val;
-          }
-        }
+      for (int u = 0; u < 32; ++u) Ts[r * LDT + cc + u] = __uint_as_float(v[u]);
+    }
+    __syncthreads();
+    for (int q = tid; q < TM * TM; q += 128) {
+      const int r = q >> 7, c = q & (TM - 1);     // row-major: consecutive threads, consecutive columns
+      const int row = bi * TM + r, col = bj * TM + c;
+      if (row < Np && col < Np) S[(size_t)row * ldS + col] = (TS)((double)Ts[r * LDT + c] * scale);
+      if (bi != bj) {
+        const int mrow = bj * TM + r, mcol = bi * TM + c;   // S[mrow][mcol] = tile[c][r]
+        if (mrow < Np && mcol < Np) S[(size_t)mrow * ldS + mcol] = (TS)((double)Ts[c * LDT + r] * scale);
       }
     }
   } else if (tid == 0) {
@@ -250,8 +272,22 @@ void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad) {
 
 // S (FP64, Np x Np, shifted) from O via split-BF16 tensor-core products.
 // hi/lo: device buffers of Np_pad * ldK BF16 each; status: device int.
+// Tile order for L2 reuse: groups of 8 block-rows; within a group, for each
+// block-column bj the tiles (bi, bj), bi in the group and bi <= bj, are
+// consecutive, so a wave of CTAs shares few operand blocks.
+int vmc_tc_tile_list(int Np, int2 *out) {
+  const int nt = (Np + TM - 1) / TM;
+  int k = 0;
+  for (int g0 = 0; g0 < nt; g0 += 8)
+    for (int bj = g0; bj < nt; ++bj)
+      for (int bi = g0; bi < g0 + 8 && bi <= bj; ++bi)
+        if (out) out[k++] = make_int2(bi, bj);
+        else ++k;
+  return k;
+}
+
 cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
-                              double shift_abs, cudaStream_t st, long long *nl) {
+                              double shift_abs, const int2 *tiles, cudaStream_t st, long long *nl) {
   int ldK, Np_pad;
   vmc_tc_dims(w.rows, w.Np, &ldK, &Np_pad);
   cudaError_t e = cudaMemsetAsync(hi, 0, sizeof(__nv_bfloat16) * (size_t)Np_pad * ldK, st);
@@ -276,7 +312,7 @@ cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, 
   const int nt = Np_pad / TM;
   k_syrk_tc<double><<<nt * (nt + 1) / 2, 128, TC_SMEM, st>>>(
       (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, ldK, ldK, w.Np, 1.0 / w.rows, w.S,
-      w.Np, status);
+      w.Np, tiles, status);
   k_shift_diag<<<(w.Np + 255) / 256, 256, 0, st>>>(w.S, w.Np, shift_rel, shift_abs);
   *nl += 2;
   return cudaGetLastError();

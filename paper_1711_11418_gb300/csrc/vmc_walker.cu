@@ -102,6 +102,7 @@ struct WSmem {
   uint4 *rnd;   // NT Philox draws (one batch)
   T *hm;        // MLP pre-activations h (H)
   T *th;        // tanh(h) (H)
+  T *g;         // Gutzwiller g_i (Ns)
 };
 
 template <typename T>
@@ -124,6 +125,7 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, unsi
   const size_t o_rnd = take(sizeof(uint4) * NT);
   const size_t o_hm = take(sizeof(T) * (size_t)H);
   const size_t o_th = take(sizeof(T) * (size_t)H);
+  const size_t o_g = take(sizeof(T) * (size_t)Ns);
   if (sm) {
     sm->minv = (T *)(base + o_minv);
     sm->vec = (T *)(base + o_vec);
@@ -139,6 +141,7 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, unsi
     sm->rnd = (uint4 *)(base + o_rnd);
     sm->hm = (T *)(base + o_hm);
     sm->th = (T *)(base + o_th);
+    sm->g = (T *)(base + o_g);
   }
   return off;
 }
@@ -283,9 +286,91 @@ __device__ __forceinline__ T corr_hop(const SysDev &S, const int *occ, const T *
   return d;
 }
 
+template <typename T> __device__ __forceinline__ const T *tvtab(const SysDev &s);
+template <> __device__ __forceinline__ const double *tvtab<double>(const SysDev &s) { return s.tgt_v64; }
+template <> __device__ __forceinline__ const float *tvtab<float>(const SysDev &s) { return s.tgt_v32; }
+
+// Same, with g from shared memory and v_rt given.
+template <typename T>
+__device__ __forceinline__ T corr_hop_v(const int *occ, const T *jf, const T *g, int Ns, int s,
+                                        int r, int t, T vrt) {
+  const int o = (1 - s) * Ns;
+  T d = jf[t] - jf[r] - vrt;
+  d += (occ[o + t] >= 0 ? g[t] : (T)0) - (occ[o + r] >= 0 ? g[r] : (T)0);
+  return d;
+}
+
 template <typename T> __device__ __forceinline__ T corr_factor(T dlog);
 template <> __device__ __forceinline__ double corr_factor<double>(double dlog) { return exp(dlog); }
 template <> __device__ __forceinline__ float corr_factor<float>(float dlog) { return expf(dlog); }
+
+// The shared-memory row loops are staged through registers CH elements at a
+// time, so a chunk's loads are all issued before its stores (the compiler
+// cannot reorder loads of one array past stores to another shared array).
+constexpr int CH = 16;
+
+template <typename T>
+__device__ __forceinline__ void row_axpy(T *row, const T *x, T c, int N) {
+  int k = 0;
+  for (; k + CH <= N; k += CH) {
+    T a[CH], b[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      a[u] = row[k + u];
+      b[u] = x[k + u];
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) row[k + u] = a[u] - c * b[u];
+  }
+  for (; k < N; ++k) row[k] -= c * x[k];
+}
+
+template <typename T>
+__device__ __forceinline__ void row_axpy2(T *row, const T *x, const T *y, T c1, T c2, int N) {
+  int k = 0;
+  for (; k + CH <= N; k += CH) {
+    T a[CH], b[CH], d[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      a[u] = row[k + u];
+      b[u] = x[k + u];
+      d[u] = y[k + u];
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) row[k + u] = a[u] - (c1 * b[u] + c2 * d[u]);
+  }
+  for (; k < N; ++k) row[k] -= c1 * x[k] + c2 * y[k];
+}
+
+// sum_k row[k] x[k] with four accumulators
+template <typename T>
+__device__ __forceinline__ T row_dot(const T *row, const T *x, int N) {
+  T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+  int k = 0;
+  for (; k + 4 <= N; k += 4) {
+    a0 += row[k] * x[k];
+    a1 += row[k + 1] * x[k + 1];
+    a2 += row[k + 2] * x[k + 2];
+    a3 += row[k + 3] * x[k + 3];
+  }
+  for (; k < N; ++k) a0 += row[k] * x[k];
+  return (a0 + a1) + (a2 + a3);
+}
+
+// sum_l x[l] M[l][col] (column of the shared matrix) with four accumulators
+template <typename T>
+__device__ __forceinline__ T col_dot(const T *M, int ldm, int col, const T *x, int N) {
+  T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+  int l = 0;
+  for (; l + 4 <= N; l += 4) {
+    a0 += x[l] * M[l * ldm + col];
+    a1 += x[l + 1] * M[(l + 1) * ldm + col];
+    a2 += x[l + 2] * M[(l + 2) * ldm + col];
+    a3 += x[l + 3] * M[(l + 3) * ldm + col];
+  }
+  for (; l < N; ++l) a0 += x[l] * M[l * ldm + col];
+  return (a0 + a1) + (a2 + a3);
+}
 
 // ---------------------------------------------------------------------------
 // Pfaffian ratios (block-wide; every thread returns the same value)
@@ -340,15 +425,7 @@ __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m
   __syncthreads();
   T a22 = (T)0, a12 = (T)0;
   if (tid < N) {
-    T w0 = (T)0, w1 = (T)0;
-    int l = 0;
-#pragma unroll 4
-    for (; l + 1 < N; l += 2) {
-      w0 += vA[l] * sm.minv[l * ldm + tid];
-      w1 += vA[l + 1] * sm.minv[(l + 1) * ldm + tid];
-    }
-    if (l < N) w0 += vA[l] * sm.minv[l * ldm + tid];
-    const T w = w0 + w1;
+    const T w = col_dot(sm.minv, ldm, tid, vA, N);
     vB[tid] = w;
     const int site = (tid == n) ? j : sm.ele[tid];
     const T c = FT[(size_t)i * Ns + site];
@@ -383,23 +460,20 @@ __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m
 // ---------------------------------------------------------------------------
 // Inverse updates on acceptance
 // ---------------------------------------------------------------------------
+
 // Row n replaced by the row in vA (up-electron hop): with w = R^T M^-1,
 // M'^-1 = M^-1 - M^-1[:,n] (w - e_n)^T / w_n.
 template <typename T>
 __device__ void row_update(const SysDev &S, const WSmem<T> &sm, int n) {
   const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
   T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N;
-  if (tid < N) {
-    T w = (T)0;
-    for (int l = 0; l < N; ++l) w += vA[l] * sm.minv[l * ldm + tid];
-    vB[tid] = w;
-  }
+  if (tid < N) vB[tid] = col_dot(sm.minv, ldm, tid, vA, N);
   __syncthreads();
   const T inv = (T)1 / vB[n];
   if (tid < N) {
     T *row = sm.minv + tid * ldm;
     const T c = row[n] * inv;
-    for (int k = 0; k < N; ++k) row[k] -= c * vB[k];
+    row_axpy(row, vB, c, N);
     row[n] = c;
   }
   __syncthreads();
@@ -412,10 +486,7 @@ __device__ void col_update(const SysDev &S, const WSmem<T> &sm, int m) {
   const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
   T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N;
   if (tid < N) {
-    const T *row = sm.minv + tid * ldm;
-    T v = (T)0;
-    for (int k = 0; k < N; ++k) v += row[k] * vA[k];
-    vB[tid] = v;
+    vB[tid] = row_dot(sm.minv + tid * ldm, vA, N);
     vC[tid] = sm.minv[m * ldm + tid];
   }
   __syncthreads();
@@ -425,8 +496,7 @@ __device__ void col_update(const SysDev &S, const WSmem<T> &sm, int m) {
     if (tid == m) {
       for (int k = 0; k < N; ++k) row[k] = vC[k] * inv;
     } else {
-      const T c = vB[tid] * inv;
-      for (int k = 0; k < N; ++k) row[k] -= c * vC[k];
+      row_axpy(row, vC, vB[tid] * inv, N);
     }
   }
   __syncthreads();
@@ -449,13 +519,12 @@ __device__ void exchange_update(const SysDev &S, const WSmem<T> &sm, int n, int 
   __syncthreads();
   if (tid < N) {
     T *row = sm.minv + tid * ldm;
-    T q = (T)0;
-    for (int k = 0; k < N; ++k) q += row[k] * vA[k];
+    const T q = row_dot(row, vA, N);
     const T p = row[n];
     const T inv = (T)1 / det;
     const T c1 = (p * K[3] - q * K[2]) * inv;
     const T c2 = (q * K[0] - p * K[1]) * inv;
-    for (int k = 0; k < N; ++k) row[k] -= c1 * vB[k] + c2 * vD[k];
+    row_axpy2(row, vB, vD, c1, c2, N);
     row[n] += c1;
   }
   __syncthreads();
@@ -522,7 +591,17 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   mc.hop_t++;
   // P(x')/P(x): one thread evaluates it; the barrier inside hop_pf_ratio publishes it.
   const int slot = buf;
-  if (tid == 0) sm.bc[slot] = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, s, rs, t));
+  if (tid == 0)
+    sm.bc[slot] = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, s, rs, t,
+                                            vtab<T>(S)[(size_t)rs * Ns + t]));
+  // rows t and r of v for the Jastrow-field update, fetched while the ratio is formed
+  T vt[2], vr[2];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int x = tid + u * NT;
+    vt[u] = (x < Ns) ? vtab<T>(S)[(size_t)t * Ns + x] : (T)0;
+    vr[u] = (x < Ns) ? vtab<T>(S)[(size_t)rs * Ns + x] : (T)0;
+  }
   T fval, mlp;
   const T rpf = hop_pf_ratio(S, sm, e, t, fval, buf, mlp);
   const T ratio = S.n_hidden ? rpf * sm.bc[slot] * exp_t<T>(mlp) : rpf * sm.bc[slot];
@@ -533,7 +612,12 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   else col_update(S, sm, e - N);
   if (S.n_hidden) mlp_apply(S, sm, t + s * Ns, rs + s * Ns, -1, -1);
   // Jastrow field: h_x += v_{x t} - v_{x r}.
-  for (int x = tid; x < Ns; x += NT)
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int x = tid + u * NT;
+    if (x < Ns) sm.jf[x] += vt[u] - vr[u];
+  }
+  for (int x = tid + 2 * NT; x < Ns; x += NT)
     sm.jf[x] += vtab<T>(S)[(size_t)t * Ns + x] - vtab<T>(S)[(size_t)rs * Ns + x];
   if (tid == 0) {
     sm.ele[e] = t;
@@ -612,58 +696,102 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     ed += (T)S.J_val[k] * (T)(0.25f * (float)(sa * sb));
   }
   // --- hopping, one warp per target site i: the warp gathers the rows
-  // f(i, r_m,dn) and f(r_n,up, i) once (lane-strided), then every electron on a
-  // neighbouring site j that can hop to i gives a Green-function ratio as a dot
-  // product with a column (row) of M^-1, times the correlation-factor ratio.
+  // f(i, r_m,dn) and f(r_n,up, i) once (lane-strided) and, one term per lane,
+  // the source sites j, t_ij and v_ji; then every electron on a neighbouring
+  // site j that can hop to i gives a Green-function ratio as a dot product
+  // with a column (row) of M^-1, times the correlation-factor ratio.
   T eo = (T)0;
-  for (int i = warp; i < Ns; i += NWARP) {
-    const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
-    if (kb == ke) continue;
-    const bool up_free = sm.occ[i] < 0, dn_free = sm.occ[Ns + i] < 0;
-    T gu[4], gd[4];
+  const T *TV = tvtab<T>(S);
+  // Gathers for site i are issued one site ahead (software pipelining).
+  T gu[4], gd[4], nu[4], nd[4];
+  int jl = 0, njl = 0;
+  T tl = (T)0, vl = (T)0, ntl = (T)0, nvl = (T)0;
+  auto fetch = [&](int i, T *u4, T *d4, int &jj, T &tt, T &vv) {
+    const bool uf = sm.occ[i] < 0, df = sm.occ[Ns + i] < 0;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int q = lane + 32 * u;
-      gu[u] = (up_free && q < N) ? F[(size_t)i * Ns + sm.ele[N + q]] : (T)0;
-      gd[u] = (dn_free && q < N) ? FT[(size_t)i * Ns + sm.ele[q]] : (T)0;
+      u4[u] = (uf && q < N) ? F[(size_t)i * Ns + sm.ele[N + q]] : (T)0;
+      d4[u] = (df && q < N) ? FT[(size_t)i * Ns + sm.ele[q]] : (T)0;
     }
-    for (int kk = kb; kk < ke; ++kk) {
-      const int k = S.tgt_term[kk];
-      const int j = S.hop_j[k];
-      const int eu = sm.occ[j], ed = sm.occ[Ns + j];
-      if (up_free && eu >= 0) {
-        T part = (T)0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int q = lane + 32 * u;
-          if (q < N) part += gu[u] * sm.minv[q * ldm + eu];
+    const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
+    jj = 0;
+    tt = vv = (T)0;
+    if (kb + lane < ke && lane < 32) {
+      jj = S.tgt_j[kb + lane];
+      tt = (T)S.tgt_t[kb + lane];
+      vv = TV[kb + lane];
+    }
+  };
+  if (warp < Ns) fetch(warp, gu, gd, jl, tl, vl);
+  for (int i = warp; i < Ns; i += NWARP) {
+    const int inext = i + NWARP;
+    if (inext < Ns) fetch(inext, nu, nd, njl, ntl, nvl);
+    const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
+    const bool up_free = sm.occ[i] < 0, dn_free = sm.occ[Ns + i] < 0;
+    if (kb < ke && (up_free || dn_free)) {
+      for (int q0 = kb; q0 < ke; q0 += 32) {
+        int jc = jl;
+        T tc = tl, vc = vl;
+        if (q0 > kb) {   // more than 32 terms: load this chunk directly
+          jc = 0;
+          tc = vc = (T)0;
+          if (q0 + lane < ke) {
+            jc = S.tgt_j[q0 + lane];
+            tc = (T)S.tgt_t[q0 + lane];
+            vc = TV[q0 + lane];
+          }
         }
-        part = warp_sum(part);
-        const T lm = S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i, j, -1, -1, lane, 32)) : (T)0;
-        if (lane == 0) {
-          eo += -(T)S.hop_t[k] * part * corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 0, j, i)) *
-                (S.n_hidden ? exp_t<T>(lm) : (T)1);
-          mc.meas_hop++;
+        const int nq = min(32, ke - q0);
+        for (int qq = 0; qq < nq; ++qq) {
+          const int j = __shfl_sync(0xffffffffu, jc, qq);
+          const T tij = __shfl_sync(0xffffffffu, tc, qq);
+          const T vji = __shfl_sync(0xffffffffu, vc, qq);
+          const int eu = sm.occ[j], ed = sm.occ[Ns + j];
+          if (up_free && eu >= 0) {
+            T part = (T)0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = lane + 32 * u;
+              if (q < N) part += gu[u] * sm.minv[q * ldm + eu];
+            }
+            part = warp_sum(part);
+            const T lm =
+                S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i, j, -1, -1, lane, 32)) : (T)0;
+            if (lane == 0) {
+              eo += -tij * part * corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, 0, j, i, vji)) *
+                    (S.n_hidden ? exp_t<T>(lm) : (T)1);
+              mc.meas_hop++;
+            }
+          }
+          if (dn_free && ed >= 0) {
+            const T *row = sm.minv + (ed - N) * ldm;
+            T part = (T)0;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int q = lane + 32 * u;
+              if (q < N) part += gd[u] * row[q];
+            }
+            part = warp_sum(part);
+            const T lm =
+                S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i + Ns, j + Ns, -1, -1, lane, 32)) : (T)0;
+            if (lane == 0) {
+              eo += -tij * part * corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, 1, j, i, vji)) *
+                    (S.n_hidden ? exp_t<T>(lm) : (T)1);
+              mc.meas_hop++;
+            }
+          }
         }
       }
-      if (dn_free && ed >= 0) {
-        const T *row = sm.minv + (ed - N) * ldm;
-        T part = (T)0;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int q = lane + 32 * u;
-          if (q < N) part += gd[u] * row[q];
-        }
-        part = warp_sum(part);
-        const T lm =
-            S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i + Ns, j + Ns, -1, -1, lane, 32)) : (T)0;
-        if (lane == 0) {
-          eo += -(T)S.hop_t[k] * part * corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, j, i)) *
-                (S.n_hidden ? exp_t<T>(lm) : (T)1);
-          mc.meas_hop++;
-        }
-      }
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      gu[u] = nu[u];
+      gd[u] = nd[u];
+    }
+    jl = njl;
+    tl = ntl;
+    vl = nvl;
   }
   // --- Heisenberg exchange: J/2 (S+_a S-_b + S-_a S+_b) = -J/2 x (labelled swap ratio)
   T *R = sm.vec + (2 * warp) * VMC_MAX_N;
@@ -714,27 +842,55 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     }
     __syncthreads();
     const int K = sm.misc[0];
-    for (int p = tid; p < K * K; p += NT) {
-      const int a = p / K, b = p - a * K;
-      if (a >= b) continue;
-      const int i = sm.ilist[a], j = sm.ilist[b];
-      const int cls = S.v_idx[(size_t)i * Ns + j];
-      if (cls < 0) continue;
-      const int mi = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
-      const int mj = (sm.occ[j] >= 0) + (sm.occ[Ns + j] >= 0) - 1;
-      acc_add(acc + S.n_g + cls, (T)(mi * mj));
+    const int npair = K * (K - 1) / 2;
+    constexpr int VB = 8;   // class gathers issued before the atomics of a batch
+    for (int p0 = tid; p0 < npair; p0 += VB * NT) {
+      int cls[VB], mm[VB];
+#pragma unroll
+      for (int u = 0; u < VB; ++u) {
+        const int p = p0 + u * NT;
+        cls[u] = -1;
+        if (p < npair) {
+          // unordered pair p -> (a, b), a < b, row-major over the strict upper triangle
+          int a = (int)((2.0f * K - 1.0f - sqrtf((2.0f * K - 1.0f) * (2.0f * K - 1.0f) - 8.0f * p)) * 0.5f);
+          if (a < 0) a = 0;
+          while (a > 0 && a * (2 * K - a - 1) / 2 > p) --a;
+          while ((a + 1) * (2 * K - a - 2) / 2 <= p) ++a;
+          const int b = p - a * (2 * K - a - 1) / 2 + a + 1;
+          const int i = sm.ilist[a], j = sm.ilist[b];
+          cls[u] = S.v_idx[(size_t)i * Ns + j];
+          const int mi = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
+          const int mj = (sm.occ[j] >= 0) + (sm.occ[Ns + j] >= 0) - 1;
+          mm[u] = mi * mj;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < VB; ++u)
+        if (cls[u] >= 0) acc_add(acc + S.n_g + cls[u], (T)mm[u]);
     }
   }
   // Pair orbital: d ln Pf / d f_ab = (M^-1)_{mn} for a = r_n,up, b = r_m,dn
   // (= -(X^-1)_{n, N+m}, Eq. DiffPf / Appendix C), times the class sign.
   const int base = S.n_g + S.n_v;
-  for (int p = tid; p < N * N; p += NT) {
-    const int n = p / N, m = p - n * N;
-    const size_t ab = (size_t)sm.ele[n] * Ns + sm.ele[N + m];
-    const int cls = S.f_idx[ab];
-    if (cls < 0) continue;
-    const T v = sm.minv[m * ldm + n];
-    acc_add(acc + base + cls, S.f_sign[ab] > 0 ? v : -v);
+  constexpr int OB = 16;  // gathers issued before the atomics of a batch
+  for (int p0 = tid; p0 < N * N; p0 += OB * NT) {
+    int cls[OB];
+    T val[OB];
+#pragma unroll
+    for (int u = 0; u < OB; ++u) {
+      const int p = p0 + u * NT;
+      cls[u] = -1;
+      if (p < N * N) {
+        const int n = p / N, m = p - n * N;
+        const size_t ab = (size_t)sm.ele[n] * Ns + sm.ele[N + m];
+        cls[u] = S.f_idx[ab];
+        const T v = sm.minv[m * ldm + n];
+        val[u] = S.f_sign[ab] > 0 ? v : -v;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < OB; ++u)
+      if (cls[u] >= 0) acc_add(acc + base + cls[u], val[u]);
   }
   if (S.n_hidden) {
     // MLP factor: dW1_kc = w2_k (1 - t_k^2) n_c, db1_k = w2_k (1 - t_k^2),
@@ -774,9 +930,11 @@ struct GJShared {
   int sign;
   double logdet;
   double pmin, pmax;   // smallest / largest |pivot|
+  double ipiv;
+  double colk[VMC_MAX_N];   // pivot column of the current step (row k zeroed)
 };
 
-__device__ __noinline__ void gj_invert(double *A, int lda, int N, int *perm, GJShared &g) {
+__device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, GJShared &g) {
   const int tid = threadIdx.x;
   if (tid == 0) {
     g.logdet = 0.0;
@@ -787,12 +945,14 @@ __device__ __noinline__ void gj_invert(double *A, int lda, int N, int *perm, GJS
   }
   __syncthreads();
   for (int k = 0; k < N; ++k) {
+    // (1) copy column k and find the pivot among rows >= k
     double v = -1.0;
     int vi = N;
-    for (int i = k + tid; i < N; i += NT) {
-      const double a = fabs(A[(size_t)i * lda + k]);
-      if (a > v) {
-        v = a;
+    for (int i = tid; i < N; i += NT) {
+      const double a = A[(size_t)i * lda + k];
+      g.colk[i] = a;
+      if (i >= k && fabs(a) > v) {
+        v = fabs(a);
         vi = i;
       }
     }
@@ -809,6 +969,7 @@ __device__ __noinline__ void gj_invert(double *A, int lda, int N, int *perm, GJS
       g.idx[tid >> 5] = vi;
     }
     __syncthreads();
+    // (2) one thread: pivot row p, swap it into the pivot column copy, 1/pivot
     if (tid == 0) {
       double bv = g.val[0];
       int bi = g.idx[0];
@@ -823,39 +984,44 @@ __device__ __noinline__ void gj_invert(double *A, int lda, int N, int *perm, GJS
       }
       g.piv = bi;
       perm[k] = bi;
+      const double piv = g.colk[bi];
+      g.colk[bi] = g.colk[k];
+      g.colk[k] = 0.0;   // row k is scaled, not eliminated
+      g.ipiv = 1.0 / piv;
+      g.logdet += log(fabs(piv));
+      g.pmin = fmin(g.pmin, fabs(piv));
+      g.pmax = fmax(g.pmax, fabs(piv));
+      if ((piv < 0.0) != (bi != k)) g.sign = -g.sign;
     }
     __syncthreads();
     if (g.bad) return;
     const int p = g.piv;
-    if (p != k) {
-      for (int c = tid; c < N; c += NT) {
-        const double t0 = A[(size_t)k * lda + c];
-        A[(size_t)k * lda + c] = A[(size_t)p * lda + c];
-        A[(size_t)p * lda + c] = t0;
-      }
-      __syncthreads();
-    }
-    const double piv = A[(size_t)k * lda + k];
-    const double ipiv = 1.0 / piv;
-    if (tid == 0) {
-      g.logdet += log(fabs(piv));
-      g.pmin = fmin(g.pmin, fabs(piv));
-      g.pmax = fmax(g.pmax, fabs(piv));
-      if ((piv < 0.0) != (p != k)) g.sign = -g.sign;
-    }
-    __syncthreads();
-    for (int c = tid; c < N; c += NT)
-      if (c != k) A[(size_t)k * lda + c] *= ipiv;
-    __syncthreads();
+    const double ipiv = g.ipiv;
+    // (3) the new column k, one row per thread (from the copy, so no conflict
+    // with the elimination below); then each thread owns columns c != k: swap
+    // rows k and p, scale row k, eliminate every other row with the copy.
+    for (int i = tid; i < N; i += NT) A[(size_t)i * lda + k] = (i == k) ? ipiv : -g.colk[i] * ipiv;
     for (int c = tid; c < N; c += NT) {
       if (c == k) continue;
-      const double rkc = A[(size_t)k * lda + c];
-      for (int i = 0; i < N; ++i)
-        if (i != k) A[(size_t)i * lda + c] -= A[(size_t)i * lda + k] * rkc;
+      double rkc = A[(size_t)p * lda + c];
+      if (p != k) A[(size_t)p * lda + c] = A[(size_t)k * lda + c];
+      rkc *= ipiv;
+      A[(size_t)k * lda + c] = rkc;
+      int i = 0;
+      for (; i + 4 <= N; i += 4) {
+        double a0 = A[(size_t)i * lda + c], a1 = A[(size_t)(i + 1) * lda + c];
+        double a2 = A[(size_t)(i + 2) * lda + c], a3 = A[(size_t)(i + 3) * lda + c];
+        a0 -= g.colk[i] * rkc;
+        a1 -= g.colk[i + 1] * rkc;
+        a2 -= g.colk[i + 2] * rkc;
+        a3 -= g.colk[i + 3] * rkc;
+        A[(size_t)i * lda + c] = a0;
+        A[(size_t)(i + 1) * lda + c] = a1;
+        A[(size_t)(i + 2) * lda + c] = a2;
+        A[(size_t)(i + 3) * lda + c] = a3;
+      }
+      for (; i < N; ++i) A[(size_t)i * lda + c] -= g.colk[i] * rkc;
     }
-    __syncthreads();
-    for (int i = tid; i < N; i += NT)
-      A[(size_t)i * lda + k] = (i == k) ? ipiv : -A[(size_t)i * lda + k] * ipiv;
     __syncthreads();
   }
   for (int k = N - 1; k >= 0; --k) {
@@ -911,6 +1077,7 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
       for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
       for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
       for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
+      for (int k = tid; k < Ns; k += NT) sm.g[k] = gtab<T>(S)[k];
       for (int k = tid; k < S.n_hidden; k += NT) {
         const T h = ((const T *)S.hmlp)[(size_t)w * S.n_hidden + k];
         sm.hm[k] = h;
@@ -998,6 +1165,22 @@ __global__ void k_expand(SysDev S) {
       S.gsite[q] = gv;
       S.gsite32[q] = (float)gv;
     }
+  }
+}
+
+// v(j, i) of every hopping term grouped by target site (after k_expand).
+__global__ void k_expand_terms(SysDev S) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < S.n_hop; q += gridDim.x * blockDim.x) {
+    // target site i of grouped term q: the CSR row that contains q
+    int lo = 0, hi = S.Ns;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (S.tgt_ptr[mid] <= q) lo = mid;
+      else hi = mid;
+    }
+    const double v = S.vmat[(size_t)S.tgt_j[q] * S.Ns + lo];
+    S.tgt_v64[q] = v;
+    S.tgt_v32[q] = (float)v;
   }
 }
 
@@ -1150,6 +1333,7 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
   for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
   for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
   for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
+  for (int k = tid; k < Ns; k += NT) sm.g[k] = gtab<T>(S)[k];
   for (int k = tid; k < S.n_hidden; k += NT) {
     const T h = ((const T *)S.hmlp)[(size_t)w * S.n_hidden + k];
     sm.hm[k] = h;
@@ -1225,6 +1409,10 @@ cudaError_t vmc_launch_expand(const SysDev *h_sys, cudaStream_t st, long long *n
   const int grid = (int)((n2 + 255) / 256 < 4096 ? (n2 + 255) / 256 : 4096);
   k_expand<<<grid, 256, 0, st>>>(*h_sys);
   ++*nl;
+  if (h_sys->n_hop) {
+    k_expand_terms<<<(h_sys->n_hop + 255) / 256, 256, 0, st>>>(*h_sys);
+    ++*nl;
+  }
   if (h_sys->n_hidden) {
     k_expand_mlp<<<1024, 256, 0, st>>>(*h_sys);
     ++*nl;

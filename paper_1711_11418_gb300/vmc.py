@@ -304,9 +304,9 @@ class Context:
         _check(self._L.vmc_enable_timing(self._h, 1 if on else 0), "vmc_enable_timing")
 
     def kernel_times(self):
-        """{'sweep'|'init'|'sr': (milliseconds, launches)} since the last call."""
-        ms = np.zeros(3)
-        cnt = np.zeros(3, np.int64)
+        """{'sweep'|'init'|'sr'|'sr_gemm': (milliseconds, launches)} since the last call."""
+        ms = np.zeros(4)
+        cnt = np.zeros(4, np.int64)
         _check(self._L.vmc_kernel_times(self._h, _p(ms, _F64P), cnt.ctypes.data_as(C.POINTER(C.c_int64))),
                "vmc_kernel_times")
-        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(("sweep", "init", "sr"))}
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(("sweep", "init", "sr", "sr_gemm"))}
