@@ -97,7 +97,9 @@ typedef struct {
   int32_t n_walkers;             /* walkers per system (>= 1) */
   uint64_t seed;                 /* Philox4x32-10 key */
   int32_t precision;             /* VMC_FP64 or VMC_MIXED */
-  int32_t delay_k;               /* mixed: delayed-update depth (0 = default) */
+  int32_t delay_k;               /* delayed-update depth k of the sweep (0 or 1 =
+                                    immediate updates, 2..VMC_DELAY_MAX); see
+                                    vmc_set_delay */
   int32_t recompute_every;       /* FP64 from-scratch inverse inside the sweep once a
                                     walker has this many accepted moves since the
                                     last one; 0 = default (mixed: 256, FP64: never),
@@ -241,6 +243,33 @@ int64_t vmc_kernel_launches(vmc_ctx *ctx);
  * and resets them.  Synchronises the stream. */
 int vmc_enable_timing(vmc_ctx *ctx, int32_t on);
 int vmc_kernel_times(vmc_ctx *ctx, double *ms, int64_t *count);
+
+/* Delayed inverse updates (the fast updates of Sec. 3.1.2 applied in
+ * batches).  With depth k >= 2 the sweep keeps up to k accepted hops as
+ * rank-1 pairs (u_i, v_i), so the current inverse is
+ * M^-1 = G0 - sum_i u_i v_i^T with G0 the stored one; proposal ratios are
+ * corrected by the sum (O(N k) per ratio instead of reading an updated G),
+ * and the pairs are folded into G0 by one rank-k product when k are pending,
+ * before an accepted exchange, before each measurement and at the end of a
+ * walker's turn.  Mathematically identical to immediate updates; rounding
+ * differs.  k = 0 or 1: immediate rank-1 / rank-2 updates.
+ * vmc_set_delay returns VMC_EINVAL for k outside [0, VMC_DELAY_MAX] or when
+ * the walker state with k pending pairs no longer fits in shared memory. */
+#define VMC_DELAY_MAX 32
+int vmc_set_delay(vmc_ctx *ctx, int32_t k);
+int32_t vmc_get_delay(vmc_ctx *ctx);
+
+/* Autotuner for the delay depth (no counterpart in the paper).  For each
+ * candidate depth cand[0..n_cand) (NULL: 1, 4, 8, 16, 32) runs `sweeps`
+ * Metropolis sweeps per walker as vmc_sample(ctx, sweeps, 0, 0) does -- they
+ * advance the chains and count as warm-up -- timed with CUDA events on the
+ * context's stream, then keeps the fastest depth.  In-sweep FP64 recomputes
+ * are held off while timing; walkers that fall due meanwhile are rebuilt by
+ * the next vmc_sample.  *chosen receives
+ * it; ms (optional, n_cand entries) the milliseconds per sweep of each
+ * candidate (negative where the depth does not fit). */
+int vmc_tune_delay(vmc_ctx *ctx, int32_t sweeps, const int32_t *cand, int32_t n_cand,
+                   int32_t *chosen, double *ms);
 
 /* Allocation-free SR means and force.  No counterpart in the paper: it is an
  * access path for callers that cannot let this library allocate device memory

@@ -48,6 +48,8 @@ struct vmc_ctx {
   long long n_launch = 0;
   double *d_scalar = nullptr;
   int recompute_every = 0;
+  int delay_k = 0;            // as set by the caller (0/1 = immediate)
+  size_t smem_cap = 0;        // dynamic shared-memory limit set on the sweep kernels
   // timing (CUDA events on st): 0 sweep, 1 init, 2 SR step, 3 S GEMM
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
@@ -59,6 +61,7 @@ namespace {
 
 void ctx_free(vmc_ctx *c) {
   if (!c) return;
+  for (SysHost &s : c->sys) vmc_sr_release(s.sr);
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
 }
@@ -232,6 +235,27 @@ int upload_sysdesc(vmc_ctx *c) {
   return VMC_OK;
 }
 
+// Delay depth k: shared-memory size and grid of the sweep kernel follow it.
+int set_delay_impl(vmc_ctx *c, int k) {
+  if (k < 0 || k > VMC_DELAY_MAX) return VMC_EINVAL;
+  const int kd = k <= 1 ? 0 : k;
+  size_t smem = 0;
+  for (auto &s : c->sys)
+    smem = std::max(smem, vmc_walker_smem(c->precision == VMC_FP64 ? 0 : 1, s.N, s.Ns, s.Np,
+                                          s.dev.n_hidden, kd, nullptr));
+  if (smem > c->smem_cap) return VMC_EINVAL;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int occ = vmc_sample_occupancy(c->precision, smem);
+  if (occ < 1) return VMC_EINVAL;
+  for (auto &s : c->sys) s.dev.delay_k = kd;
+  c->smem_sample = smem;
+  c->grid_sample = std::min(c->n_work, nsm * occ);
+  c->delay_k = k;
+  return VMC_OK;
+}
+
 // Rebuild the walkers' inverses from scratch (FP64) where needed; returns
 // VMC_ESINGULAR if any walker's M is singular.
 int ensure_init(vmc_ctx *c, bool redraw_illcond = false) {
@@ -275,7 +299,8 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
     CK(dalloc(c, &w.t, sizeof(double) * rows_cap));
     CK(dalloc(c, &w.scal, sizeof(double) * 8));
     CK(dalloc(c, &w.info, sizeof(int) * 4));
-    const size_t nparts = (size_t)(rows_cap + 2047) / 2048;
+    CK(dalloc(c, &w.dblk, sizeof(double) * 32 * 32));
+    const size_t nparts = (size_t)vmc_colreduce_parts(rows_cap, Np);
     CK(dalloc(c, &w.part, sizeof(double) * nparts * Np));
     s.sr_alloc = true;
   }
@@ -469,8 +494,8 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dupload(c, &d.E, (const double *)nullptr, rows_cap))) return fail(rc);
     if ((rc = dalloc(c, &d.O, (size_t)esize * rows_cap * s.ldO))) return fail(rc);
     int acc_len = 0;
-    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, H, &acc_len));
-    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, H, &acc_len));
+    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, H, 0, &acc_len));
+    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, H, 0, &acc_len));
     d.acc_len = acc_len;
     c->smem_init = std::max(c->smem_init, vmc_init_smem(s.N, s.Ns));
     if (vmc_launch_expand(&d, c->st, &c->n_launch) != cudaSuccess) return fail(VMC_ECUDA);
@@ -484,9 +509,17 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
       return fail(VMC_ECUDA);
   }
   c->smem_sample = (c->precision == VMC_FP64) ? smem64 : smem32;
-  if (vmc_walker_set_smem_limits(smem64, smem32, c->smem_init) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(VMC_EINVAL);  // does not fit in shared memory
+  {
+    // The sweep kernels may use up to the device's opt-in limit (less the
+    // static part): delayed updates enlarge the walker's shared state.
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    c->smem_cap = optin > 4096 ? (size_t)optin - 4096 : 0;
+    if (c->smem_sample > c->smem_cap || c->smem_init > (size_t)optin) return fail(VMC_EINVAL);
+    if (vmc_walker_set_smem_limits(c->smem_cap, c->smem_cap, c->smem_init) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(VMC_EINVAL);  // does not fit in shared memory
+    }
   }
   // work list: (system, walker), larger N first
   std::vector<int2> work;
@@ -505,6 +538,7 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int occ = std::max(1, vmc_sample_occupancy(c->precision, c->smem_sample));
   c->grid_sample = std::min(c->n_work, nsm * occ);
+  if ((rc = set_delay_impl(c, o->delay_k))) return fail(rc);
   c->recompute_every = o->recompute_every > 0 ? o->recompute_every
                        : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 256 : 0;
   // Initial inverses; re-draw placements whose M is singular (bounded).
@@ -901,6 +935,67 @@ int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, do
 }
 
 int64_t vmc_kernel_launches(vmc_ctx *c) { return c ? c->n_launch : -1; }
+
+int vmc_set_delay(vmc_ctx *c, int32_t k) {
+  if (!c) return VMC_EINVAL;
+  return set_delay_impl(c, k);
+}
+
+int32_t vmc_get_delay(vmc_ctx *c) { return c ? c->delay_k : -1; }
+
+int vmc_tune_delay(vmc_ctx *c, int32_t sweeps, const int32_t *cand, int32_t n_cand,
+                   int32_t *chosen, double *ms) {
+  static const int32_t def[] = {1, 4, 8, 16, 32};
+  if (!c || sweeps < 1 || (cand && n_cand < 1) || !chosen) return VMC_EINVAL;
+  if (!cand) {
+    cand = def;
+    n_cand = 5;
+  }
+  for (int q = 0; q < n_cand; ++q)
+    if (cand[q] < 0 || cand[q] > VMC_DELAY_MAX) return VMC_EINVAL;
+  CK(ensure_init(c));
+  const int prev = c->delay_k;
+  // In-sweep recomputes come in bursts and would swamp the timing: they are
+  // off while tuning (the accepted-move counts keep running, so walkers that
+  // fall due are rebuilt by the next vmc_sample).
+  const int rec = c->recompute_every;
+  c->recompute_every = 0;
+  cudaEvent_t e0, e1;
+  CKC(cudaEventCreate(&e0));
+  CKC(cudaEventCreate(&e1));
+  int best = -1;
+  double best_ms = 0.0;
+  int rc = VMC_OK;
+  for (int q = 0; q < n_cand && rc == VMC_OK; ++q) {
+    if (ms) ms[q] = -1.0;
+    if (set_delay_impl(c, cand[q]) != VMC_OK) continue;
+    cudaEventRecord(e0, c->st);
+    rc = vmc_sample(c, sweeps, 0, 0);
+    cudaEventRecord(e1, c->st);
+    if (rc != VMC_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = VMC_ECUDA;
+      break;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    const double per = (double)t / sweeps;
+    if (ms) ms[q] = per;
+    if (best < 0 || per < best_ms) {
+      best = cand[q];
+      best_ms = per;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->recompute_every = rec;
+  if (rc != VMC_OK || best < 0) {
+    set_delay_impl(c, prev);
+    return rc != VMC_OK ? rc : VMC_EINVAL;
+  }
+  *chosen = best;
+  return set_delay_impl(c, best);
+}
 
 int vmc_enable_timing(vmc_ctx *c, int32_t on) {
   if (!c) return VMC_EINVAL;

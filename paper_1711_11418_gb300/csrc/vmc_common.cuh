@@ -65,6 +65,7 @@ struct SysDev {
   int *status;                 // [W]
   double *drift;               // [W]
   int recompute_every;         // accepted moves between FP64 from-scratch inverses (0 = never)
+  int delay_k;                 // pending delayed updates before a flush (<= 1: immediate)
   // MLP correlation factor exp(w2 . tanh(W1 n + b1) + b2) (H = 0: absent);
   // params hold [W1 (H x 2Ns) | b1 | w2 | b2] after the pair orbitals.
   int n_hidden;
@@ -107,7 +108,7 @@ cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker,
                                    int precision, int n_moves, const int *d_moves,
                                    double *d_out, size_t smem, cudaStream_t st,
                                    long long *n_launch);
-size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int *acc_len);
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len);
 size_t vmc_init_smem(int N, int Ns);
 int vmc_sample_occupancy(int precision, size_t smem);
 cudaError_t vmc_walker_set_smem_limits(size_t smem_sample64, size_t smem_sample32,
@@ -127,14 +128,18 @@ struct SrWork {
   double *x, *r, *p, *w, *t;   // CG vectors (t: [rows])
   double *scal;                // device scalars
   int *info;                   // device status
-  double *part;                // column-reduction partials [ceil(rows/2048) * Np]
+  double *dblk;                // [32*32] factored diagonal block in flight (Cholesky)
+  double *part;                // column-reduction partials [vmc_colreduce_parts(rows, Np) * Np]
+  void *chol_graph;            // cudaGraphExec_t of the Cholesky factor + solve (lazily built)
 };
+int vmc_colreduce_parts(int rows, int Np);
 cudaError_t vmc_sr_means(const SrWork &w, cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_build_S(const SrWork &w, double shift_rel, double shift_abs,
                            cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_build_g(const SrWork &w, cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_diag(const SrWork &w, cudaStream_t st, long long *nl);
-int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl);
+int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl);
+void vmc_sr_release(SrWork &w);
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
                     int kmax, int *iters, cudaStream_t st, long long *nl, int dense);
 void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad);

@@ -16,37 +16,76 @@
 namespace {
 
 constexpr int RB = 256;        // threads of the column-reduction kernels
-constexpr int ROWCHUNK = 2048; // rows per partial of a column reduction
+constexpr int RMIN = 64;       // fewest rows per partial of a column reduction
+
+}  // namespace
+
+// Row chunks of a column reduction: enough CTAs to cover the SMs several
+// times over, at least RMIN rows each.  Monotone in rows, so the partial
+// buffer sized for the largest row count serves every smaller one.
+int vmc_colreduce_parts(int rows, int Np) {
+  const int ctiles = (Np + RB - 1) / RB;
+  int target = (8 * 152 + ctiles - 1) / ctiles;
+  const int most = (rows + RMIN - 1) / RMIN;
+  if (target > most) target = most;
+  return target < 1 ? 1 : target;
+}
+
+namespace {
 
 template <typename TO>
 __device__ __forceinline__ double ld(const TO *p) { return (double)*p; }
 
-// Partial column reductions: part[c][k] = sum over rows of chunk c of
+// Partial column reductions: part[c][k] = sum over the rows of chunk c of
 //   mode 0: O_rk                      (mean)
 //   mode 1: (O_rk - o_k) (E_r - ebar)  (force g)
 //   mode 2: (O_rk - o_k)^2             (diagonal of S)
 //   mode 3: O_rk t_r                   (CG: O^T t)
+// One thread per column, rows unrolled by 4 for independent loads.
 template <typename TO>
-__global__ void k_colreduce(const TO *O, int ldO, int rows, int Np, const double *obar,
-                            const double *wvec, double wshift, int mode, double *part,
-                            const int *done) {
+__global__ void __launch_bounds__(RB) k_colreduce(const TO *O, int ldO, int rows, int Np,
+                                                  const double *obar, const double *wvec,
+                                                  double wshift, int mode, int chunk,
+                                                  double *part, const int *done) {
   const int k = blockIdx.x * RB + threadIdx.x;
   const int c = blockIdx.y;
   if (k >= Np || (done && *done)) return;
-  const int r0 = c * ROWCHUNK;
-  const int r1 = min(rows, r0 + ROWCHUNK);
+  const int r0 = c * chunk;
+  const int r1 = min(rows, r0 + chunk);
   const double ok = (mode == 1 || mode == 2) ? obar[k] : 0.0;
-  double s = 0.0;
-  for (int r = r0; r < r1; ++r) {
-    const double o = ld(O + (size_t)r * ldO + k);
+  const TO *col = O + k;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int r = r0;
+  for (; r + 4 <= r1; r += 4) {
+    const double o0 = ld(col + (size_t)r * ldO), o1 = ld(col + (size_t)(r + 1) * ldO);
+    const double o2 = ld(col + (size_t)(r + 2) * ldO), o3 = ld(col + (size_t)(r + 3) * ldO);
     switch (mode) {
-      case 0: s += o; break;
-      case 1: s += (o - ok) * (wvec[r] - wshift); break;
-      case 2: s += (o - ok) * (o - ok); break;
-      default: s += o * wvec[r]; break;
+      case 0: s0 += o0; s1 += o1; s2 += o2; s3 += o3; break;
+      case 1:
+        s0 += (o0 - ok) * (wvec[r] - wshift);
+        s1 += (o1 - ok) * (wvec[r + 1] - wshift);
+        s2 += (o2 - ok) * (wvec[r + 2] - wshift);
+        s3 += (o3 - ok) * (wvec[r + 3] - wshift);
+        break;
+      case 2:
+        s0 += (o0 - ok) * (o0 - ok); s1 += (o1 - ok) * (o1 - ok);
+        s2 += (o2 - ok) * (o2 - ok); s3 += (o3 - ok) * (o3 - ok);
+        break;
+      default:
+        s0 += o0 * wvec[r]; s1 += o1 * wvec[r + 1]; s2 += o2 * wvec[r + 2]; s3 += o3 * wvec[r + 3];
+        break;
     }
   }
-  part[(size_t)c * Np + k] = s;
+  for (; r < r1; ++r) {
+    const double o = ld(col + (size_t)r * ldO);
+    switch (mode) {
+      case 0: s0 += o; break;
+      case 1: s0 += (o - ok) * (wvec[r] - wshift); break;
+      case 2: s0 += (o - ok) * (o - ok); break;
+      default: s0 += o * wvec[r]; break;
+    }
+  }
+  part[(size_t)c * Np + k] = (s0 + s1) + (s2 + s3);
 }
 
 __global__ void k_sum_parts(const double *part, int nparts, int Np, double scale, double *out,
@@ -188,161 +227,211 @@ __global__ void k_mirror_shift(double *S, int Np, double shift_rel, double shift
 }
 
 // Blocked right-looking Cholesky (lower triangle in place), panels of CB
-// columns: factor the diagonal block (one CTA), solve the panel below it
-// (L_ij = A_ij L_jj^-T), update the trailing lower triangle (A -= L L^T).
+// columns.  Per panel: k_chol_panel factors the diagonal block and solves the
+// panel below it (L_ij = A_ij L_jj^-T); k_syrk_trailing updates the trailing
+// lower triangle (A -= L L^T) in 32x32 tiles.  FP64 throughput per SM is low
+// on this part, so small tiles keep every SM busy on the late panels.
 constexpr int CB = 32;
 
-__global__ void k_potrf_diag(double *A, int n, int j0, int nb, int *info) {
-  __shared__ double D[CB][CB + 1];
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    D[r][c] = A[(size_t)(j0 + r) * n + j0 + c];
-  }
-  __syncthreads();
+// Cholesky of the nb x nb diagonal block D (lower part, shared memory) by one
+// warp: right-looking, column k scaled by 1/L_kk, then the packed triangle
+// {(r, c): k < c <= r < nb} updated with one entry per lane (the triangle is
+// walked by a linear index, so no lane idles on masked entries).  invd[k]
+// receives 1/L_kk; returns the first non-positive pivot (1-based) or 0.
+__device__ int warp_potrf(double (*D)[CB + 1], double *invd, int nb) {
+  const int lane = threadIdx.x & 31;
+  int bad = 0;
   for (int k = 0; k < nb; ++k) {
-    if (threadIdx.x == 0) {
-      const double a = D[k][k];
+    if (lane == 0) {
+      double a = D[k][k];
       if (!(a > 0.0) || !isfinite(a)) {
-        if (*info == 0) *info = j0 + k + 1;
-        D[k][k] = 1.0;
-      } else {
-        D[k][k] = sqrt(a);
+        if (!bad) bad = k + 1;
+        a = 1.0;
       }
+      const double d = sqrt(a);
+      D[k][k] = d;
+      invd[k] = 1.0 / d;
     }
-    __syncthreads();
-    const double inv = 1.0 / D[k][k];
-    for (int r = k + 1 + threadIdx.x; r < nb; r += blockDim.x) D[r][k] *= inv;
-    __syncthreads();
-    for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-      const int r = q / nb, c = q % nb;
-      if (c > k && r >= c) D[r][c] -= D[r][k] * D[c][k];
+    __syncwarp();
+    const double iv = invd[k];
+    if (lane > k && lane < nb) D[lane][k] *= iv;
+    __syncwarp();
+    const int m = nb - k - 1;
+    const int T = m * (m + 1) / 2;
+    for (int q = lane; q < T; q += 32) {
+      int i = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+      while (i * (i + 1) / 2 > q) --i;
+      while ((i + 1) * (i + 2) / 2 <= q) ++i;
+      const int r = k + 1 + i, c = k + 1 + (q - i * (i + 1) / 2);
+      D[r][c] -= D[r][k] * D[c][k];
     }
-    __syncthreads();
+    __syncwarp();
   }
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    if (r >= c) A[(size_t)(j0 + r) * n + j0 + c] = D[r][c];
-  }
+  return __shfl_sync(0xffffffffu, bad, 0);
 }
 
-__global__ void k_trsm_panel(double *A, int n, int j0, int nb) {
-  __shared__ double L[CB][CB + 1];
-  for (int q = threadIdx.x; q < nb * nb; q += blockDim.x) {
-    const int r = q / nb, c = q % nb;
-    L[r][c] = (r >= c) ? A[(size_t)(j0 + r) * n + j0 + c] : 0.0;
+// Panel step: every CTA (one warp) factors the diagonal block in shared
+// memory and solves CB rows of the panel below it, X_i = A_i L_jj^-T, by
+// forward substitution with one row per lane (X_ic = (A_ic - sum_{l<c} X_il
+// L_cl) / L_cc).  CTA 0 records the first non-positive pivot in *info
+// (1-based) and stores the factored block: straight into A when it is the
+// only CTA, else into dblk, from where the trailing update copies it (another
+// CTA may still be reading the block).
+__global__ void __launch_bounds__(32) k_chol_panel(double *A, int n, int j0, int nb, int *info,
+                                                   double *dblk) {
+  __shared__ double D[CB][CB + 1];
+  __shared__ double invd[CB];
+  const int lane = threadIdx.x;
+  for (int r = 0; r < CB; ++r)
+    D[r][lane] = (r < nb && lane <= r) ? A[(size_t)(j0 + r) * n + j0 + lane] : (r == lane ? 1.0 : 0.0);
+  __syncwarp();
+  const int bad = warp_potrf(D, invd, nb);
+  if (blockIdx.x == 0) {
+    const bool direct = gridDim.x == 1;
+    for (int r = 0; r < nb; ++r) {
+      if (lane > r) continue;
+      if (direct) A[(size_t)(j0 + r) * n + j0 + lane] = D[r][lane];
+      else dblk[r * nb + lane] = D[r][lane];
+    }
+    if (lane == 0 && bad && *info == 0) *info = j0 + bad;
   }
-  __syncthreads();
-  const int i = j0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = j0 + nb + blockIdx.x * CB + lane;
   if (i >= n) return;
-  double x[CB];
   double *row = A + (size_t)i * n + j0;
+  double x[CB];
 #pragma unroll
-  for (int k = 0; k < CB; ++k) x[k] = (k < nb) ? row[k] : 0.0;
+  for (int c = 0; c < CB; ++c) x[c] = (c < nb) ? row[c] : 0.0;
 #pragma unroll
-  for (int k = 0; k < CB; ++k) {
-    if (k < nb) {
-      double v = x[k];
+  for (int c = 0; c < CB; ++c) {
+    if (c < nb) {
+      double v = x[c];
 #pragma unroll
-      for (int l = 0; l < CB; ++l)
-        if (l < k) v -= x[l] * L[k][l];
-      x[k] = v / L[k][k];
+      for (int l = 0; l < c; ++l) v -= x[l] * D[c][l];
+      x[c] = v * invd[c];
     }
   }
 #pragma unroll
-  for (int k = 0; k < CB; ++k)
-    if (k < nb) row[k] = x[k];
+  for (int c = 0; c < CB; ++c)
+    if (c < nb) row[c] = x[c];
 }
 
-// trailing A[i][k] -= sum_l L[i][j0+l] L[k][j0+l], j1 <= k <= i < n (j1 = j0 + nb)
-__global__ void __launch_bounds__(256) k_syrk_trailing(double *A, int n, int j0, int nb) {
+// Trailing update A[i][k] -= sum_l L[i][j0+l] L[k][j0+l] for j1 <= k <= i < n
+// (j1 = j0 + nb): one 32x32 lower tile per CTA, tile (bi, bj) with bj <= bi
+// decoded from the linear block index.  With copy_diag, CTA 0 also stores
+// the factored diagonal block from dblk (no CTA here reads that block).
+__global__ void __launch_bounds__(256) k_syrk_trailing(double *A, int n, int j0, int nb,
+                                                       int copy_diag, const double *dblk) {
   const int j1 = j0 + nb;
-  const int m = n - j1;
-  const int nt = (m + 63) / 64;
+  if (copy_diag && blockIdx.x == 0)
+    for (int q = threadIdx.x; q < nb * nb; q += 256) {
+      const int r = q / nb, c = q % nb;
+      if (c <= r) A[(size_t)(j0 + r) * n + j0 + c] = dblk[q];
+    }
   int t = blockIdx.x, bi = 0;
   while (t >= bi + 1) {
     t -= bi + 1;
     ++bi;
   }
-  const int bj = t;   // bj <= bi: lower tiles
-  __shared__ double Pi[CB][65];
-  __shared__ double Pk[CB][65];
-  for (int q = threadIdx.x; q < CB * 64; q += 256) {
-    const int l = q / 64, r = q % 64;
-    const int ii = j1 + bi * 64 + r, kk = j1 + bj * 64 + r;
+  const int bj = t;
+  __shared__ double Pi[CB][33];
+  __shared__ double Pk[CB][33];
+  for (int q = threadIdx.x; q < CB * 32; q += 256) {
+    const int r = q / CB, l = q % CB;
+    const int ii = j1 + bi * 32 + r, kk = j1 + bj * 32 + r;
     Pi[l][r] = (l < nb && ii < n) ? A[(size_t)ii * n + j0 + l] : 0.0;
     Pk[l][r] = (l < nb && kk < n) ? A[(size_t)kk * n + j0 + l] : 0.0;
   }
   __syncthreads();
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
-  for (int l = 0; l < nb; ++l) {
-    double a[4], b[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      a[u] = Pi[l][ty + 16 * u];
-      b[u] = Pk[l][tx + 16 * u];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+  double a00 = 0, a01 = 0, a10 = 0, a11 = 0;
+#pragma unroll 8
+  for (int l = 0; l < CB; ++l) {
+    const double x0 = Pi[l][ty], x1 = Pi[l][ty + 16];
+    const double y0 = Pk[l][tx], y1 = Pk[l][tx + 16];
+    a00 += x0 * y0; a01 += x0 * y1; a10 += x1 * y0; a11 += x1 * y1;
   }
-  (void)nt;
+  const double acc[2][2] = {{a00, a01}, {a10, a11}};
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < 2; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i = j1 + bi * 64 + ty + 16 * u, k = j1 + bj * 64 + tx + 16 * v;
+    for (int v = 0; v < 2; ++v) {
+      const int i = j1 + bi * 32 + ty + 16 * u, k = j1 + bj * 32 + tx + 16 * v;
       if (i < n && k < n && k <= i) A[(size_t)i * n + k] -= acc[u][v];
     }
 }
 
+// Triangular solves L y = b and L^T x = y, one launch per panel of CB
+// unknowns and direction.  Every CTA stages the panel's diagonal block and
+// solves it redundantly with one unknown per lane (column sweep: lane k
+// finishes its unknown and broadcasts it, the others subtract), then applies
+// the panel to its share of the remaining entries.  The right-hand side is
+// read from one vector and the finished panel written to another, so no CTA
+// reads a value another CTA of the same launch writes.
+//   forward:  rows i >= p0 + nb: y_i -= sum_l L_{i,p0+l} z_{p0+l}   (warp per row);
+//             CTA 0 writes z[p0 .. p0+nb).
+//   backward: rows i < p0:       y_i -= sum_l L_{p0+l,i} x_{p0+l}   (thread per row);
+//             CTA 0 writes x[p0 .. p0+nb).
+constexpr int SV_ROWS = 64;    // forward rows per CTA (8 warps x 8 rows)
+constexpr int SV_COLS = 256;   // backward rows per CTA (one per thread)
 
-// Both triangular solves in one CTA of 1024 threads (x holds b on entry):
-// per panel of CB rows, warp 0 solves the diagonal block (lane-parallel dot
-// products), then all warps update the rest of the vector -- forward: one
-// warp per row over the panel's columns; backward: one thread per entry over
-// the panel's rows (both coalesced).
-__global__ void __launch_bounds__(1024) k_chol_solve_blocked(const double *L, int n, double *x) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int p0 = 0; p0 < n; p0 += CB) {
-    const int nb = min(CB, n - p0);
-    if (warp == 0) {
-      for (int k = 0; k < nb; ++k) {
-        double s = (lane < k) ? L[(size_t)(p0 + k) * n + p0 + lane] * x[p0 + lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[p0 + k] = (x[p0 + k] - s) / L[(size_t)(p0 + k) * n + p0 + k];
-        __syncwarp();
-      }
+__device__ __forceinline__ double panel_solve_lane(const double (*Dg)[CB + 1], double v, int nb,
+                                                   bool transpose) {
+  const int lane = threadIdx.x & 31;
+  if (!transpose) {
+    for (int k = 0; k < nb; ++k) {
+      if (lane == k) v /= Dg[k][k];
+      const double xk = __shfl_sync(0xffffffffu, v, k);
+      if (lane > k) v -= Dg[lane][k] * xk;
     }
-    __syncthreads();
-    for (int i = p0 + nb + warp; i < n; i += nw) {
-      double s = (lane < nb) ? L[(size_t)i * n + p0 + lane] * x[p0 + lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) x[i] -= s;
+  } else {
+    for (int k = nb - 1; k >= 0; --k) {
+      if (lane == k) v /= Dg[k][k];
+      const double xk = __shfl_sync(0xffffffffu, v, k);
+      if (lane < k) v -= Dg[k][lane] * xk;
     }
-    __syncthreads();
   }
-  for (int p0 = ((n - 1) / CB) * CB; p0 >= 0; p0 -= CB) {
-    const int nb = min(CB, n - p0);
-    if (warp == 0) {
-      for (int k = nb - 1; k >= 0; --k) {
-        double s = (lane > k && lane < nb) ? L[(size_t)(p0 + lane) * n + p0 + k] * x[p0 + lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) x[p0 + k] = (x[p0 + k] - s) / L[(size_t)(p0 + k) * n + p0 + k];
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    for (int i = tid; i < p0; i += blockDim.x) {
-      double s = 0.0;
-      for (int l = 0; l < nb; ++l) s += L[(size_t)(p0 + l) * n + i] * x[p0 + l];
-      x[i] -= s;
-    }
-    __syncthreads();
-  }
+  return v;
 }
 
+__global__ void __launch_bounds__(256) k_trsv_panel(const double *L, int n, int p0, int fwd,
+                                                    double *y, double *out) {
+  __shared__ double Dg[CB][CB + 1];
+  __shared__ double xp[CB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = min(CB, n - p0);
+  for (int q = tid; q < CB * CB; q += 256) {
+    const int r = q / CB, c = q % CB;
+    Dg[r][c] = (r < nb && c <= r) ? L[(size_t)(p0 + r) * n + p0 + c] : (r == c ? 1.0 : 0.0);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double v = lane < nb ? y[p0 + lane] : 0.0;
+    v = panel_solve_lane(Dg, v, nb, !fwd);
+    xp[lane] = lane < nb ? v : 0.0;
+    if (blockIdx.x == 0 && lane < nb) out[p0 + lane] = v;
+  }
+  __syncthreads();
+  if (fwd) {
+    const int r0 = p0 + nb + blockIdx.x * SV_ROWS;
+    for (int i = r0 + warp; i < min(n, r0 + SV_ROWS); i += 8) {
+      double s = (lane < nb) ? L[(size_t)i * n + p0 + lane] * xp[lane] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) y[i] -= s;
+    }
+  } else {
+    const int i = blockIdx.x * SV_COLS + tid;
+    if (i < p0) {
+      double s0 = 0.0, s1 = 0.0;
+      int l = 0;
+      for (; l + 2 <= nb; l += 2) {
+        s0 += L[(size_t)(p0 + l) * n + i] * xp[l];
+        s1 += L[(size_t)(p0 + l + 1) * n + i] * xp[l + 1];
+      }
+      if (l < nb) s0 += L[(size_t)(p0 + l) * n + i] * xp[l];
+      y[i] -= s0 + s1;
+    }
+  }
+}
 
 
 // t = O v (one warp per row)
@@ -461,10 +550,11 @@ template <typename TO>
 cudaError_t colreduce(const SrWork &w, const TO *O, int mode, const double *wvec, double wshift,
                       double scale, double *out, cudaStream_t st, long long *nl,
                       const int *done = nullptr) {
-  const int nparts = (w.rows + ROWCHUNK - 1) / ROWCHUNK;
+  const int nparts = vmc_colreduce_parts(w.rows, w.Np);
+  const int chunk = (w.rows + nparts - 1) / nparts;
   dim3 grid((w.Np + RB - 1) / RB, nparts);
-  k_colreduce<TO><<<grid, RB, 0, st>>>(O, w.ldO, w.rows, w.Np, w.obar, wvec, wshift, mode, w.part,
-                                       done);
+  k_colreduce<TO><<<grid, RB, 0, st>>>(O, w.ldO, w.rows, w.Np, w.obar, wvec, wshift, mode, chunk,
+                                       w.part, done);
   k_sum_parts<<<(w.Np + 255) / 256, 256, 0, st>>>(w.part, nparts, w.Np, scale, out, done);
   *nl += 2;
   return cudaGetLastError();
@@ -529,30 +619,75 @@ cudaError_t vmc_sr_build_S(const SrWork &w, double shift_rel, double shift_abs, 
   return cudaGetLastError();
 }
 
-int vmc_sr_cholesky_solve(const SrWork &w, cudaStream_t st, long long *nl) {
+// The launch sequence of the factorisation and both solves: 2 launches per
+// panel plus the solve.  Pointers are fixed for the life of the work area, so
+// the sequence is captured once into a CUDA graph and replayed.
+static void chol_sequence(const SrWork &w, cudaStream_t st) {
   const int n = w.Np;
   cudaMemsetAsync(w.info, 0, sizeof(int), st);
   for (int j0 = 0; j0 < n; j0 += CB) {
     const int nb = n - j0 < CB ? n - j0 : CB;
-    k_potrf_diag<<<1, 256, 0, st>>>(w.S, n, j0, nb, w.info);
-    ++*nl;
     const int rem = n - j0 - nb;
+    const int pg = rem > 0 ? (rem + CB - 1) / CB : 1;
+    k_chol_panel<<<pg, 32, 0, st>>>(w.S, n, j0, nb, w.info, w.dblk);
     if (rem > 0) {
-      k_trsm_panel<<<(rem + 127) / 128, 128, 0, st>>>(w.S, n, j0, nb);
-      const int nt = (rem + 63) / 64;
-      k_syrk_trailing<<<nt * (nt + 1) / 2, 256, 0, st>>>(w.S, n, j0, nb);
-      *nl += 2;
+      const int nt = (rem + 31) / 32;
+      k_syrk_trailing<<<nt * (nt + 1) / 2, 256, 0, st>>>(w.S, n, j0, nb, pg > 1, w.dblk);
     }
   }
-  cudaMemcpyAsync(w.x, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  k_chol_solve_blocked<<<1, 1024, 0, st>>>(w.S, n, w.x);
-  *nl += 1;
-  if (cudaGetLastError() != cudaSuccess) return -3;
+  // forward: y (= w.p, starts as g) -> z (= w.w); backward: z -> x.
+  cudaMemcpyAsync(w.p, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  for (int p0 = 0; p0 < n; p0 += CB) {
+    const int rem = n - p0 - (n - p0 < CB ? n - p0 : CB);
+    const int grid = rem > 0 ? (rem + SV_ROWS - 1) / SV_ROWS : 1;
+    k_trsv_panel<<<grid, 256, 0, st>>>(w.S, n, p0, 1, w.p, w.w);
+  }
+  for (int p0 = ((n - 1) / CB) * CB; p0 >= 0; p0 -= CB) {
+    const int grid = p0 > 0 ? (p0 + SV_COLS - 1) / SV_COLS : 1;
+    k_trsv_panel<<<grid, 256, 0, st>>>(w.S, n, p0, 0, w.w, w.x);
+  }
+}
+
+static long long chol_launches(int n) {
+  long long c = 0;
+  for (int j0 = 0; j0 < n; j0 += CB) c += (n - j0 > CB) ? 4 : 3;
+  return c;
+}
+
+int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl) {
+  if (!w.chol_graph) {
+    // Capture on a private stream (the caller's may be the legacy stream,
+    // which cannot be captured).
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return -3;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      chol_sequence(w, cs);
+      ok = cudaStreamEndCapture(cs, &g) == cudaSuccess && g;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    if (!ok) {
+      cudaGetLastError();
+      return -3;
+    }
+    w.chol_graph = (void *)ge;
+  }
+  if (cudaGraphLaunch((cudaGraphExec_t)w.chol_graph, st) != cudaSuccess) return -3;
+  *nl += chol_launches(w.Np);
   int info = 0;
   if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return -3;
   if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
   return info ? -4 : 0;
+}
+
+void vmc_sr_release(SrWork &w) {
+  if (w.chol_graph) cudaGraphExecDestroy((cudaGraphExec_t)w.chol_graph);
+  w.chol_graph = nullptr;
 }
 
 // One SR-CG product out = S~ v (Sec. 3.3.2): t = O v, u = O^T t / rows,

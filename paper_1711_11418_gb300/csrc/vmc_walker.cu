@@ -90,7 +90,9 @@ template <typename T>
 struct WSmem {
   T *minv;      // N x ldm
   T *vec;       // 8 x VMC_MAX_N: block vectors vA..vD, or 2 per warp
-  T *acc;       // O-row accumulator (acc_len)
+  T *acc;       // O-row accumulator (acc_len); shares its space with ut/vt
+  T *ut;        // delayed updates: u_i = ut[i*N ..], i < pending (measurement flushes first)
+  T *vt;        //                  v_i = vt[i*N ..]
   T *red;       // 2 buffers x 8
   T *bc;        // 2 broadcast scalars (double-buffered like red)
   T *jf;        // Ns
@@ -106,14 +108,15 @@ struct WSmem {
 };
 
 template <typename T>
-__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, unsigned char *base,
-                                         WSmem<T> *sm) {
+__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int kd,
+                                         unsigned char *base, WSmem<T> *sm) {
   const int ldm = (N % 2) ? N : N + 1;
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 16); return o; };
   const size_t o_minv = take(minv_bytes(N, ldm, sizeof(T)));
   const size_t o_vec = take(sizeof(T) * 8 * VMC_MAX_N);
-  const size_t o_acc = take(sizeof(T) * (size_t)acc_len);
+  const size_t dly = (kd > 1) ? sizeof(T) * 2 * (size_t)kd * N : 0;
+  const size_t o_acc = take(sizeof(T) * (size_t)acc_len > dly ? sizeof(T) * (size_t)acc_len : dly);
   const size_t o_red = take(sizeof(T) * 32);
   const size_t o_bc = take(sizeof(T) * 2);
   const size_t o_jf = take(sizeof(T) * Ns);
@@ -130,6 +133,8 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, unsi
     sm->minv = (T *)(base + o_minv);
     sm->vec = (T *)(base + o_vec);
     sm->acc = (T *)(base + o_acc);
+    sm->ut = (T *)(base + o_acc);
+    sm->vt = sm->ut + (size_t)(kd > 1 ? kd : 0) * N;
     sm->red = (T *)(base + o_red);
     sm->bc = (T *)(base + o_bc);
     sm->jf = (T *)(base + o_jf);
@@ -380,20 +385,29 @@ __device__ __forceinline__ T col_dot(const T *M, int ldm, int col, const T *x, i
 // sum_k (M^-1)_{m k} C_k (down electron m = e - N, new column C_k = f(r_k,up, t)).
 // fval receives this thread's entry of the new row/column.
 // With the MLP factor, mlp receives log P_MLP(x')/P_MLP(x) (same barrier).
+// With np pending delayed updates the current inverse is G = G0 - sum_i u_i v_i^T
+// (G0 = sm.minv): the column / row entry used here is corrected by the sum, and
+// kept in vec slot 4 for the update on acceptance.
 template <typename T>
 __device__ __forceinline__ T hop_pf_ratio(const SysDev &S, const WSmem<T> &sm, int e, int t,
-                                          T &fval, int &buf, T &mlp) {
+                                          T &fval, int &buf, T &mlp, int np) {
   const int N = S.N, Ns = S.Ns, tid = threadIdx.x;
   T prod = (T)0;
   fval = (T)0;
   if (tid < N) {
+    T gent;
     if (e < N) {
       fval = ftab<T>(S)[(size_t)t * Ns + sm.ele[N + tid]];
-      prod = sm.minv[tid * S.ldm + e] * fval;
+      gent = sm.minv[tid * S.ldm + e];
+      for (int i = 0; i < np; ++i) gent -= sm.ut[i * N + tid] * sm.vt[i * N + e];
     } else {
+      const int m = e - N;
       fval = fTtab<T>(S)[(size_t)t * Ns + sm.ele[tid]];
-      prod = sm.minv[(e - N) * S.ldm + tid] * fval;
+      gent = sm.minv[m * S.ldm + tid];
+      for (int i = 0; i < np; ++i) gent -= sm.ut[i * N + m] * sm.vt[i * N + tid];
     }
+    prod = gent * fval;
+    if (S.delay_k > 1) sm.vec[4 * VMC_MAX_N + tid] = gent;
   }
   if (!S.n_hidden) {
     mlp = (T)0;
@@ -414,24 +428,47 @@ __device__ __forceinline__ T hop_pf_ratio(const SysDev &S, const WSmem<T> &sm, i
 //   K11 = (R^T M^-1)_n, K12 = sum_{k != n} (R^T M^-1)_k b_k,
 //   K21 = (M^-1)_{mn},  K22 = sum_k (M^-1)_{mk} C'_k (C'_n = M_nm).
 // On return vB holds w = R^T M^-1, vC holds C, K[0..3] the 2x2 matrix.
+// z_i = x_i . y for the np pending vectors x_i = X[i*N ..] (warp per i),
+// written to out[i]; the caller synchronises before reading out.
+template <typename T>
+__device__ __forceinline__ void pending_dots(const T *X, const T *y, int N, int np, T *out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i = warp; i < np; i += NWARP) {
+    T s = (T)0;
+    for (int l = lane; l < N; l += 32) s += X[i * N + l] * y[l];
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+}
+
 template <typename T>
 __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m, int i, int j,
-                               int &buf, T *K, T &mlp) {
+                               int &buf, T *K, T &mlp, int np) {
   const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
   const T *F = ftab<T>(S);
   const T *FT = fTtab<T>(S);
   T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N;
+  T *vz = sm.vec + 5 * VMC_MAX_N;
   if (tid < N) vA[tid] = (tid == m) ? F[(size_t)j * Ns + i] : F[(size_t)j * Ns + sm.ele[N + tid]];
   __syncthreads();
+  T w = (T)0;
+  if (tid < N) w = col_dot(sm.minv, ldm, tid, vA, N);
+  if (np > 0) {
+    // R^T G = R^T G0 - sum_i (R . u_i) v_i^T
+    pending_dots(sm.ut, vA, N, np, vz);
+    __syncthreads();
+    if (tid < N)
+      for (int q = 0; q < np; ++q) w -= vz[q] * sm.vt[q * N + tid];
+  }
   T a22 = (T)0, a12 = (T)0;
   if (tid < N) {
-    const T w = col_dot(sm.minv, ldm, tid, vA, N);
     vB[tid] = w;
     const int site = (tid == n) ? j : sm.ele[tid];
     const T c = FT[(size_t)i * Ns + site];
     const T mkm = FT[(size_t)j * Ns + sm.ele[tid]];
     vC[tid] = c;
-    const T mrow = sm.minv[m * ldm + tid];
+    T mrow = sm.minv[m * ldm + tid];
+    for (int q = 0; q < np; ++q) mrow -= sm.ut[q * N + m] * sm.vt[q * N + tid];
     if (tid == n) {
       a22 = mrow * mkm;
     } else {
@@ -449,7 +486,8 @@ __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m
     mlp = (T)0;
   }
   const T A11 = vB[n];
-  const T A21 = sm.minv[m * ldm + n];
+  T A21 = sm.minv[m * ldm + n];
+  for (int q = 0; q < np; ++q) A21 -= sm.ut[q * N + m] * sm.vt[q * N + n];
   K[0] = A11;
   K[1] = A12;
   K[2] = A21;
@@ -531,6 +569,84 @@ __device__ void exchange_update(const SysDev &S, const WSmem<T> &sm, int n, int 
 }
 
 // ---------------------------------------------------------------------------
+// Delayed updates: up to kd accepted hops are kept as rank-1 pairs, so that
+// G = G0 - sum_{i<np} u_i v_i^T; ratios read G through the correction above
+// and the pairs are folded into G0 by one rank-np product (flush).
+// ---------------------------------------------------------------------------
+
+// G0 <- G0 - U V^T: thread l owns row l, CH columns at a time in registers;
+// the v_i entries are broadcast reads.
+template <typename T>
+__device__ void delayed_flush(const SysDev &S, const WSmem<T> &sm, int &np) {
+  if (np == 0) return;
+  const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
+  if (tid < N) {
+    T *row = sm.minv + tid * ldm;
+    int c = 0;
+    for (; c + CH <= N; c += CH) {
+      T a[CH];
+#pragma unroll
+      for (int u = 0; u < CH; ++u) a[u] = row[c + u];
+      for (int i = 0; i < np; ++i) {
+        const T ul = sm.ut[i * N + tid];
+        const T *v = sm.vt + i * N + c;
+#pragma unroll
+        for (int u = 0; u < CH; ++u) a[u] -= ul * v[u];
+      }
+#pragma unroll
+      for (int u = 0; u < CH; ++u) row[c + u] = a[u];
+    }
+    for (; c < N; ++c) {
+      T a = row[c];
+      for (int i = 0; i < np; ++i) a -= sm.ut[i * N + tid] * sm.vt[i * N + c];
+      row[c] = a;
+    }
+  }
+  np = 0;
+  __syncthreads();
+}
+
+// Accepted hop of electron e (new row / column of M in vA), delayed form.
+// Up electron n = e (row n of M replaced by R): w = R^T G, u = G[:,n] / w_n,
+// v = w - e_n.  Down electron m = e - N (column m replaced by C): y = G C,
+// u = (y - e_m) / y_m, v = G[m,:].  Both are the rank-1 updates of
+// row_update / col_update; G[:,n] or G[m,:] was kept by hop_pf_ratio.
+template <typename T>
+__device__ void delayed_hop_update(const SysDev &S, const WSmem<T> &sm, int e, int &np) {
+  const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
+  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vE = sm.vec + 4 * VMC_MAX_N,
+    *vz = sm.vec + 5 * VMC_MAX_N;
+  const bool up = e < N;
+  T d = (T)0;
+  if (tid < N) d = up ? col_dot(sm.minv, ldm, tid, vA, N) : row_dot(sm.minv + tid * ldm, vA, N);
+  if (np > 0) {
+    pending_dots(up ? sm.ut : sm.vt, vA, N, np, vz);
+    __syncthreads();
+    if (tid < N) {
+      const T *y = up ? sm.vt : sm.ut;
+      for (int i = 0; i < np; ++i) d -= vz[i] * y[i * N + tid];
+    }
+  }
+  if (tid < N) vB[tid] = d;
+  __syncthreads();
+  const int k = up ? e : e - N;
+  const T inv = (T)1 / vB[k];
+  if (tid < N) {
+    const T dk = (tid == k) ? (T)1 : (T)0;
+    if (up) {
+      sm.ut[np * N + tid] = vE[tid] * inv;
+      sm.vt[np * N + tid] = d - dk;
+    } else {
+      sm.ut[np * N + tid] = (d - dk) * inv;
+      sm.vt[np * N + tid] = vE[tid];
+    }
+  }
+  ++np;
+  __syncthreads();
+  if (np >= S.delay_k) delayed_flush(S, sm, np);
+}
+
+// ---------------------------------------------------------------------------
 // One Metropolis proposal (Sec. 3.1.2).  Every thread runs it; decisions are
 // uniform across the block.
 // ---------------------------------------------------------------------------
@@ -542,7 +658,7 @@ struct MoveCounts {
 template <typename T>
 __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t walker,
                         unsigned long long &ctr, int &rpos, MoveCounts &mc, int &acc_since,
-                        int &buf) {
+                        int &buf, int &np) {
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, tid = threadIdx.x;
   if (rpos == NT) {
     // Next NT draws of this walker's stream, one per thread.
@@ -563,9 +679,10 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
     if (i == j || sm.occ[Ns + i] >= 0 || sm.occ[j] >= 0) return;
     mc.ex_t++;
     T K[4], mlp;
-    const T rpf = exchange_pf_ratio(S, sm, n, m - N, i, j, buf, K, mlp);
+    const T rpf = exchange_pf_ratio(S, sm, n, m - N, i, j, buf, K, mlp, np);
     const T ratio = S.n_hidden ? rpf * exp_t<T>(mlp) : rpf;
     if (u < ratio * ratio) {
+      delayed_flush(S, sm, np);
       exchange_update(S, sm, n, m - N, j, K, rpf);
       if (S.n_hidden) mlp_apply(S, sm, i + Ns, i, j, j + Ns);
       if (tid == 0) {
@@ -603,12 +720,13 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
     vr[u] = (x < Ns) ? vtab<T>(S)[(size_t)rs * Ns + x] : (T)0;
   }
   T fval, mlp;
-  const T rpf = hop_pf_ratio(S, sm, e, t, fval, buf, mlp);
+  const T rpf = hop_pf_ratio(S, sm, e, t, fval, buf, mlp, np);
   const T ratio = S.n_hidden ? rpf * sm.bc[slot] * exp_t<T>(mlp) : rpf * sm.bc[slot];
   if (!(u < ratio * ratio)) return;
   if (tid < N) sm.vec[tid] = fval;
   __syncthreads();
-  if (s == 0) row_update(S, sm, e);
+  if (S.delay_k > 1) delayed_hop_update(S, sm, e, np);
+  else if (s == 0) row_update(S, sm, e);
   else col_update(S, sm, e - N);
   if (S.n_hidden) mlp_apply(S, sm, t + s * Ns, rs + s * Ns, -1, -1);
   // Jastrow field: h_x += v_{x t} - v_{x r}.
@@ -1068,7 +1186,7 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     const int w = wk.y;
     const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
     WSmem<T> sm;
-    walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, smem_raw, &sm);
+    walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, S.delay_k, smem_raw, &sm);
     // --- load the walker: M^-1 block by a TMA bulk copy, configuration and
     // Jastrow field by plain loads while the copy is in flight
     const uint32_t nbytes = (uint32_t)minv_bytes(N, ldm, sizeof(T));
@@ -1102,15 +1220,21 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     int buf = 0;
     const uint32_t key_w = (uint32_t)w;
     __syncthreads();
+    int np = 0;   // pending delayed updates
     const long long props_first = (long long)n_first * Ne;
-    for (long long p = 0; p < props_first; ++p) propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf);
+    for (long long p = 0; p < props_first; ++p)
+      propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf, np);
     for (int s = 0; s < n_samples; ++s) {
       const long long props = (long long)sweeps_between * Ne;
-      for (long long p = 0; p < props; ++p) propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf);
+      for (long long p = 0; p < props; ++p)
+        propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf, np);
       __syncthreads();
+      delayed_flush(S, sm, np);
       measure(S, sm, w, sample_base + s, buf, mc);
       mc.samples++;
     }
+    __syncthreads();
+    delayed_flush(S, sm, np);
     if (mc.meas_hop) atomicAdd((unsigned long long *)&S.cnt[8 * w + 4], (unsigned long long)mc.meas_hop);
     if (mc.meas_ex) atomicAdd((unsigned long long *)&S.cnt[8 * w + 5], (unsigned long long)mc.meas_ex);
     __syncthreads();
@@ -1326,7 +1450,7 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
   load_sys(&S, systems + sys);
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
   WSmem<T> sm;
-  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, smem_raw, &sm);
+  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, smem_raw, &sm);
   const size_t nb = minv_bytes(N, ldm, sizeof(T));
   const T *src = (const T *)((const unsigned char *)S.minv + (size_t)w * nb);
   for (int k = tid; k < N * ldm; k += NT) sm.minv[k] = src[k];
@@ -1349,7 +1473,7 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
         const int s = (a >= N) ? 1 : 0;
         if (sm.occ[s * Ns + b] < 0 && !(S.local_spin && sm.occ[(1 - s) * Ns + b] >= 0)) {
           T fval, mlp;
-          const T rpf = hop_pf_ratio(S, sm, a, b, fval, buf, mlp);
+          const T rpf = hop_pf_ratio(S, sm, a, b, fval, buf, mlp, 0);
           res = (double)rpf * (double)corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, s, sm.ele[a], b)) *
                 (S.n_hidden ? (double)exp_t<T>(mlp) : 1.0);
         }
@@ -1358,7 +1482,7 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
       const int i = sm.ele[a], j = sm.ele[b];
       if (i != j && sm.occ[Ns + i] < 0 && sm.occ[j] < 0) {
         T K[4], mlp;
-        res = (double)exchange_pf_ratio(S, sm, a, b - N, i, j, buf, K, mlp) *
+        res = (double)exchange_pf_ratio(S, sm, a, b - N, i, j, buf, K, mlp, 0) *
               (S.n_hidden ? (double)exp_t<T>(mlp) : 1.0);
       }
     }
@@ -1372,11 +1496,11 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers
 // ---------------------------------------------------------------------------
-size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int *acc_len) {
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len) {
   const int al = (Np <= VMC_ACC_MAX) ? Np : 0;
   if (acc_len) *acc_len = al;
-  return precision == 0 ? walker_layout<double>(N, Ns, al, H, nullptr, nullptr)
-                        : walker_layout<float>(N, Ns, al, H, nullptr, nullptr);
+  return precision == 0 ? walker_layout<double>(N, Ns, al, H, kd, nullptr, nullptr)
+                        : walker_layout<float>(N, Ns, al, H, kd, nullptr, nullptr);
 }
 
 size_t vmc_init_smem(int N, int Ns) {

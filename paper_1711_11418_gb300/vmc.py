@@ -76,7 +76,8 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_get_configs", "vmc_sample", "vmc_measure", "vmc_get_samples", "vmc_set_samples",
            "vmc_sr_step", "vmc_get_sr_matrices", "vmc_get_params", "vmc_set_params",
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
-           "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static"]
+           "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
+           "vmc_get_delay", "vmc_tune_delay"]
 
 
 def load(path: str = LIB_PATH):
@@ -115,6 +116,9 @@ def load(path: str = LIB_PATH):
     L.vmc_sr_force_static.argtypes = [P, C.c_int32, C.c_int32, C.c_int32, P, P, P, P, P]
     L.vmc_kernel_launches.argtypes = [P]
     L.vmc_kernel_launches.restype = C.c_int64
+    L.vmc_set_delay.argtypes = [P, C.c_int32]
+    L.vmc_get_delay.argtypes = [P]
+    L.vmc_tune_delay.argtypes = [P, C.c_int32, _I32P, C.c_int32, _I32P, _F64P]
     for name in EXPORTS:
         if name not in ("vmc_destroy", "vmc_strerror", "vmc_kernel_launches"):
             getattr(L, name).restype = C.c_int
@@ -299,6 +303,24 @@ class Context:
 
     def kernel_launches(self):
         return int(self._L.vmc_kernel_launches(self._h))
+
+    # -- delayed updates
+    def set_delay(self, k):
+        _check(self._L.vmc_set_delay(self._h, int(k)), "vmc_set_delay")
+
+    def get_delay(self):
+        return int(self._L.vmc_get_delay(self._h))
+
+    def tune_delay(self, sweeps=2, candidates=None):
+        """Time `sweeps` warm-up sweeps per candidate depth, keep the fastest.
+        Returns (chosen, {k: ms per sweep, or None where it does not fit})."""
+        cand = np.ascontiguousarray(candidates if candidates is not None else (1, 4, 8, 16, 32),
+                                    np.int32)
+        ms = np.zeros(cand.size)
+        chosen = np.zeros(1, np.int32)
+        _check(self._L.vmc_tune_delay(self._h, int(sweeps), _p(cand, _I32P), cand.size,
+                                      _p(chosen, _I32P), _p(ms, _F64P)), "vmc_tune_delay")
+        return int(chosen[0]), {int(k): (float(t) if t >= 0 else None) for k, t in zip(cand, ms)}
 
     def enable_timing(self, on=True):
         _check(self._L.vmc_enable_timing(self._h, 1 if on else 0), "vmc_enable_timing")
