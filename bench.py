@@ -237,11 +237,15 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
                       max_samples=S, recompute_every=args.recompute if precision == vmc.MIXED else -1,
                       stream=stream.cuda_stream)
     ctx.sample(args.equil, 0, 0)                        # equilibration (untimed)
-    sr = dict(dtau=0.05, shift_rel=1e-3, shift_abs=0.0, solver=vmc.CHOLESKY)
+    # plain form: FP64 Cholesky; mixed form: FP64 iterative refinement on an
+    # FP32 inverse (FP64 Cholesky if it does not reach the residual target)
+    sr = dict(dtau=0.05, shift_rel=1e-3, shift_abs=0.0,
+              solver=vmc.MIXED_IR if precision == vmc.MIXED else vmc.CHOLESKY, cg_eps=1e-12)
+    reps = []
 
     def step():
         ctx.sample(0, S, 1)
-        ctx.sr_step(**sr)
+        reps.append(ctx.sr_step(**sr))
 
     for _ in range(args.warmup):
         step()
@@ -270,8 +274,13 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
     kt = ctx.kernel_times()
     launches = ctx.kernel_launches() - l0
     d = delta(st0, st1)
+    timed = reps[-args.steps:]
+    solve = dict(solver="mixed_ir" if precision == vmc.MIXED else "cholesky_fp64",
+                 refinement_steps_max=max(r["cg_iters"] for r in timed),
+                 fallbacks=sum(r["fallback"] for r in timed),
+                 rel_residual_max=max(r["rel_residual"] for r in timed))
     return ctx, dict(ms=ms, stats=d, kt=kt, launches=launches, clocks=clk,
-                     energy=statistics.fmean(energies), last=st1)
+                     energy=statistics.fmean(energies), last=st1, solve=solve)
 
 
 def run_ours(args):
@@ -335,9 +344,11 @@ def run_ours(args):
         sweep_ms, sweep_n = r["kt"]["sweep"]
         return {"proposals_per_s": d["n_proposals"] * world / secs, "ms_per_step": r["ms"] / args.steps,
                 "sweep_kernel_ms_per_launch": sweep_ms / max(sweep_n, 1), "sweep_launches": sweep_n,
-                "init_ms": r["kt"]["init"][0], "sr_ms": r["kt"]["sr"][0],
+                "init_ms_per_step": r["kt"]["init"][0] / args.steps,
+                "sr_ms_per_step": r["kt"]["sr"][0] / args.steps,
                 "acceptance": d["n_accepted"] / max(d["n_proposals"], 1),
-                "energy_per_site": r["energy"] / prob.Ns, "recomputes": d["n_recomputes"]}
+                "energy_per_site": r["energy"] / prob.Ns, "recomputes": d["n_recomputes"],
+                "sr_solve": r["solve"]}
 
     peaks = measured_alu_peaks(torch)
     sm = summarize(mixed)
@@ -357,7 +368,7 @@ def run_ours(args):
                    "samples_per_walker_per_step": args.samples, "sweeps_between_samples": 1,
                    "proposals_per_sweep": prob.Ne, "p_exchange": prob.p_exchange, "Np": prob.Np,
                    "recompute_every_accepted": args.recompute,
-                   "sr": "dense S (FP64 SYRK plain / FP32 SYRK mixed), blocked Cholesky, shift_rel 1e-3, dtau 0.05",
+                   "sr": "dense S (FP64 SYRK plain / split-BF16 tensor cores mixed); FP64 Cholesky plain, FP64 iterative refinement on an FP32 inverse mixed; shift_rel 1e-3, dtau 0.05",
                    "l2": "no flush: walker state (4096 x 50.6 KB FP32 inverses) exceeds the 129 MB L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "mixed": sm,

@@ -62,8 +62,13 @@ enum {
 enum { VMC_FP64 = 0, VMC_MIXED = 1 };
 /* SR solvers: dense S~ + Cholesky; CG (Algorithm 1) with the SR-CG product
  * from the sample matrix (S never formed); CG with the dense S~ built by the
- * GEMM (tensor cores in the mixed form). */
-enum { VMC_SOLVE_CHOLESKY = 0, VMC_SOLVE_CG = 1, VMC_SOLVE_CG_DENSE = 2 };
+ * GEMM (tensor cores in the mixed form); dense S~ solved by iterative
+ * refinement in FP64 (residuals and solution) with an FP32 inverse of the
+ * Jacobi-scaled S~ as the correction operator, falling back to the FP64
+ * Cholesky when the residual target is not met (not in the paper: the
+ * O(Np^3) part in FP32, the result to FP64 residual). */
+enum { VMC_SOLVE_CHOLESKY = 0, VMC_SOLVE_CG = 1, VMC_SOLVE_CG_DENSE = 2,
+       VMC_SOLVE_MIXED_IR = 3 };
 
 typedef struct vmc_ctx vmc_ctx;
 
@@ -132,17 +137,20 @@ typedef struct {
   double dtau;                   /* Delta tau of Eq. SR_equation_system */
   double shift_rel;              /* S~_kk = S_kk (1 + shift_rel) + shift_abs */
   double shift_abs;
-  int32_t solver;                /* VMC_SOLVE_CHOLESKY, VMC_SOLVE_CG or VMC_SOLVE_CG_DENSE */
-  double cg_eps;                 /* Algorithm 1: stop when |r|^2 < eps^2 |b|^2 */
-  int32_t cg_kmax;               /* Algorithm 1: iteration limit */
+  int32_t solver;                /* VMC_SOLVE_* */
+  double cg_eps;                 /* Algorithm 1 / refinement: stop when |r| < eps |b| */
+  int32_t cg_kmax;               /* Algorithm 1: iteration limit; refinement:
+                                    min(cg_kmax, 16) steps */
 } vmc_sr_opts;
 
 typedef struct {
   double energy;                 /* <H> of the samples used */
   double norm_g;                 /* |g|_2 */
   double norm_dalpha;            /* |Delta alpha|_2 */
-  int32_t cg_iters;              /* iterations used (CG), 0 for Cholesky */
+  int32_t cg_iters;              /* iterations used (CG or refinement), 0 for Cholesky */
   int32_t n_params;
+  double rel_residual;           /* refinement: |g - S~ x| / |g| reached (else 0) */
+  int32_t fallback;              /* refinement: 1 if the FP64 Cholesky solved instead */
 } vmc_sr_report;
 
 /* Create a context for one system (Sec. 2.3-2.2 problem statement).
@@ -199,8 +207,9 @@ int vmc_set_samples(vmc_ctx *ctx, int32_t system, int32_t rows,
 
 /* One SR step on the stored samples of one system (Sec. 3.3.1-3.3.2):
  * S_km = <O_k O_m> - <O_k><O_m>, g_m = <E O_m> - <E><O_m>,
- * S~ = S with diagonal shift, solve S~ x = g by Cholesky (S~ = L L^T) or by
- * CG (Algorithm 1) with the SR-CG product or the dense S~, alpha += -dtau x.  Walker
+ * S~ = S with diagonal shift, solve S~ x = g by Cholesky (S~ = L L^T), by
+ * CG (Algorithm 1) with the SR-CG product or the dense S~, or by mixed-precision
+ * iterative refinement, alpha += -dtau x.  Walker
  * inverses are rebuilt on the next vmc_sample.  Errors: VMC_EINVAL,
  * VMC_ESTATE (no samples), VMC_ESINGULAR (S~ not positive definite),
  * VMC_ENUMERIC (CG breakdown), VMC_ECUDA. */

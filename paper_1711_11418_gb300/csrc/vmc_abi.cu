@@ -61,7 +61,10 @@ namespace {
 
 void ctx_free(vmc_ctx *c) {
   if (!c) return;
-  for (SysHost &s : c->sys) vmc_sr_release(s.sr);
+  for (SysHost &s : c->sys) {
+    vmc_sr_release(s.sr);
+    vmc_sr_ir_release(s.sr);
+  }
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
 }
@@ -283,7 +286,7 @@ int ensure_init(vmc_ctx *c, bool redraw_illcond = false) {
   return VMC_OK;
 }
 
-int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
+int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S, bool need_ir = false) {
   const int rows_cap = s.W * s.max_samples;
   if (!s.sr_alloc) {
     SrWork &w = s.sr;
@@ -325,6 +328,15 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S) {
   s.sr.precision = c->precision;
   s.sr.O = s.dev.O;
   s.sr.E = s.dev.E;
+  if (need_ir && !s.sr.S32) {
+    SrWork &w = s.sr;
+    CK(dalloc(c, &w.S32, sizeof(float) * (size_t)s.Np * s.Np));
+    CK(dalloc(c, &w.gjP, sizeof(float) * 32 * 32));
+    CK(dalloc(c, &w.gjC, sizeof(float) * (size_t)(s.Np + 64) * 32));
+    CK(dalloc(c, &w.rs32, sizeof(float) * s.Np));
+    CK(dalloc(c, &w.dsc, sizeof(double) * s.Np));
+    CK(dalloc(c, &w.irflag, sizeof(int) * 4));
+  }
   return VMC_OK;
 }
 
@@ -458,6 +470,30 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dupload(c, (int **)&d.v_idx, l.n_v ? l.v_idx : vneg.data(), n2))) return fail(rc);
     if ((rc = dupload(c, (int **)&d.f_idx, l.f_idx, n2))) return fail(rc);
     if ((rc = dupload(c, (signed char **)&d.f_sign, (const signed char *)l.f_sign, n2))) return fail(rc);
+    {
+      // measurement tables: packed pair-orbital class + sign, Jastrow pairs by class
+      std::vector<int> fc(n2);
+      for (size_t q = 0; q < n2; ++q) fc[q] = l.f_idx[q] >= 0 ? 2 * l.f_idx[q] + (l.f_sign[q] < 0) : -1;
+      if ((rc = dupload(c, (int **)&d.fcode, fc.data(), n2))) return fail(rc);
+      std::vector<int> vp(l.n_v + 1, 0);
+      std::vector<unsigned> pr;
+      if (l.n_v) {
+        for (size_t i = 0; i < Ns; ++i)
+          for (size_t j = i + 1; j < Ns; ++j)
+            if (l.v_idx[i * Ns + j] >= 0) vp[l.v_idx[i * Ns + j] + 1]++;
+        for (int k = 0; k < l.n_v; ++k) vp[k + 1] += vp[k];
+        pr.resize(vp[l.n_v]);
+        std::vector<int> fill(vp.begin(), vp.end() - 1);
+        for (size_t i = 0; i < Ns; ++i)
+          for (size_t j = i + 1; j < Ns; ++j) {
+            const int k = l.v_idx[i * Ns + j];
+            if (k >= 0) pr[fill[k]++] = (unsigned)i | ((unsigned)j << 16);
+          }
+      }
+      if ((rc = dupload(c, (int **)&d.vptr, vp.data(), vp.size()))) return fail(rc);
+      if ((rc = dupload(c, (unsigned **)&d.vpair, pr.empty() ? nullptr : pr.data(), pr.size())))
+        return fail(rc);
+    }
     if ((rc = dupload(c, (double **)&d.params, params[si], s.Np))) return fail(rc);
     if ((rc = dalloc(c, &d.f64, sizeof(double) * n2))) return fail(rc);
     if ((rc = dalloc(c, &d.fT64, sizeof(double) * n2))) return fail(rc);
@@ -813,19 +849,32 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
   if (!sys_ok(c, system) || !o) return VMC_EINVAL;
   if (!(o->dtau > 0.0) || o->shift_rel < 0.0 || o->shift_abs < 0.0) return VMC_EINVAL;
   if (o->solver != VMC_SOLVE_CHOLESKY && o->solver != VMC_SOLVE_CG &&
-      o->solver != VMC_SOLVE_CG_DENSE)
+      o->solver != VMC_SOLVE_CG_DENSE && o->solver != VMC_SOLVE_MIXED_IR)
     return VMC_EINVAL;
   SysHost &s = c->sys[system];
   if (!s.rows) return VMC_ESTATE;
   const bool chol = o->solver == VMC_SOLVE_CHOLESKY;
   const bool dense = o->solver == VMC_SOLVE_CG_DENSE;
-  CK(sr_alloc(c, s, chol || dense));
+  const bool ir = o->solver == VMC_SOLVE_MIXED_IR;
+  CK(sr_alloc(c, s, chol || dense || ir, ir));
   SrWork &w = s.sr;
   TimedRegion tr(c, 2);
   CKC(vmc_sr_means(w, c->st, &c->n_launch));
   CKC(vmc_sr_build_g(w, c->st, &c->n_launch));
-  int iters = 0;
-  if (chol) {
+  int iters = 0, fallback = 0;
+  double rel_res = 0.0;
+  if (ir) {
+    CK(build_S(c, s, o->shift_rel, o->shift_abs));
+    const double eps = o->cg_eps > 0.0 ? o->cg_eps : 1e-12;
+    const int kmax = o->cg_kmax > 0 ? std::min(o->cg_kmax, 16) : 8;
+    const int rc = vmc_sr_ir_solve(w, kmax, eps, &iters, &rel_res, c->st, &c->n_launch);
+    if (rc < 0) return rc;
+    if (rc == 1) {
+      fallback = 1;
+      const int rc2 = vmc_sr_cholesky_solve(w, c->st, &c->n_launch);
+      if (rc2) return rc2;
+    }
+  } else if (chol) {
     CK(build_S(c, s, o->shift_rel, o->shift_abs));
     const int rc = vmc_sr_cholesky_solve(w, c->st, &c->n_launch);
     if (rc) return rc;
@@ -854,6 +903,8 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
     rep->norm_dalpha = o->dtau * sqrt(xx);
     rep->cg_iters = iters;
     rep->n_params = s.Np;
+    rep->rel_residual = rel_res;
+    rep->fallback = fallback;
   }
   return VMC_OK;
 }

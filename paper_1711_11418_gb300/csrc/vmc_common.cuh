@@ -41,6 +41,9 @@ struct SysDev {
   const double *J_val;
   const int *g_idx, *v_idx, *f_idx;
   const signed char *f_sign;
+  const int *fcode;            // [Ns*Ns] 2 f_idx + (f_sign < 0), or -1 (no parameter)
+  const int *vptr;             // [n_v + 1] Jastrow class -> its site pairs (CSR)
+  const unsigned *vpair;       // i | j << 16, i < j, grouped by class
   const double *params;
   double *f64, *fT64;          // expanded f_ij and its transpose [Ns*Ns]
   float *f32, *fT32;
@@ -131,6 +134,15 @@ struct SrWork {
   double *dblk;                // [32*32] factored diagonal block in flight (Cholesky)
   double *part;                // column-reduction partials [vmc_colreduce_parts(rows, Np) * Np]
   void *chol_graph;            // cudaGraphExec_t of the Cholesky factor + solve (lazily built)
+  // mixed-precision iterative refinement (vmc_sr_mixed.cu)
+  float *S32;                  // [Np*Np] scaled S~, inverted in place
+  float *gjP, *gjC;            // [32*32] pivot-block inverse, [Np*32] column block
+  float *rs32;                 // [Np] scaled residual
+  double *dsc;                 // [Np] S~_kk^-1/2
+  int *irflag;                 // [4] converged, unusable, steps
+  void *ir_graph;
+  int ir_iter;
+  double ir_eps;
 };
 int vmc_colreduce_parts(int rows, int Np);
 cudaError_t vmc_sr_means(const SrWork &w, cudaStream_t st, long long *nl);
@@ -140,6 +152,9 @@ cudaError_t vmc_sr_build_g(const SrWork &w, cudaStream_t st, long long *nl);
 cudaError_t vmc_sr_diag(const SrWork &w, cudaStream_t st, long long *nl);
 int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl);
 void vmc_sr_release(SrWork &w);
+int vmc_sr_ir_solve(SrWork &w, int max_iter, double eps, int *iters, double *rel_res,
+                    cudaStream_t st, long long *nl);
+void vmc_sr_ir_release(SrWork &w);
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
                     int kmax, int *iters, cudaStream_t st, long long *nl, int dense);
 void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad);

@@ -788,6 +788,37 @@ __device__ T exchange_pf_ratio_warp(const SysDev &S, const WSmem<T> &sm, int n, 
 template <typename T>
 __device__ __forceinline__ void acc_add(T *p, T v) { atomicAdd(p, v); }
 
+// Sum of eight per-lane values over the warp by a transposed butterfly
+// (nine shuffles instead of eight separate reductions): on return lane l
+// holds the total of value k = 4 bit4(l) + 2 bit3(l) + bit2(l).
+template <typename T>
+__device__ __forceinline__ T reduce8_transposed(const T *p, int lane) {
+  T q[4], r[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T send = b4 ? p[k] : p[k + 4];
+    const T keep = b4 ? p[k + 4] : p[k];
+    q[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T send = b3 ? q[k] : q[k + 2];
+    const T keep = b3 ? q[k + 2] : q[k];
+    r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  T s = (b2 ? r[1] : r[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r[0] : r[1], 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+
+// a[r] for a warp-varying r < 4 without local-memory indexing
+template <typename V>
+__device__ __forceinline__ V sel4(const V *a, int r) {
+  return r == 0 ? a[0] : r == 1 ? a[1] : r == 2 ? a[2] : a[3];
+}
+
 template <typename T>
 __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int &buf,
                         MoveCounts &mc) {
@@ -815,15 +846,23 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
   }
   // --- hopping, one warp per target site i: the warp gathers the rows
   // f(i, r_m,dn) and f(r_n,up, i) once (lane-strided) and, one term per lane,
-  // the source sites j, t_ij and v_ji; then every electron on a neighbouring
-  // site j that can hop to i gives a Green-function ratio as a dot product
-  // with a column (row) of M^-1, times the correlation-factor ratio.
+  // the source sites j, t_ij and v_ji.  The Green-function ratios of up to
+  // four neighbouring sites (both spins: eight dot products with a column or
+  // row of M^-1) are formed together, reduced by one transposed butterfly
+  // (lane 4k ends with the sum for term k), and their correlation-factor
+  // ratios are evaluated by those eight lanes in parallel.
   T eo = (T)0;
   const T *TV = tvtab<T>(S);
   // Gathers for site i are issued one site ahead (software pipelining).
   T gu[4], gd[4], nu[4], nd[4];
   int jl = 0, njl = 0;
   T tl = (T)0, vl = (T)0, ntl = (T)0, nvl = (T)0;
+  // term ranges of the target sites, staged in shared memory (ilist is free
+  // until the O_v part): kb(i) = tp[i], ke(i) = tp[i + 1] or n_hop
+  int *tp = sm.ilist;
+  for (int i = tid; i < Ns; i += NT) tp[i] = S.tgt_ptr[i];
+  __syncthreads();
+  auto t_end = [&](int i) { return i + 1 < Ns ? tp[i + 1] : S.n_hop; };
   auto fetch = [&](int i, T *u4, T *d4, int &jj, T &tt, T &vv) {
     const bool uf = sm.occ[i] < 0, df = sm.occ[Ns + i] < 0;
 #pragma unroll
@@ -832,20 +871,21 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
       u4[u] = (uf && q < N) ? F[(size_t)i * Ns + sm.ele[N + q]] : (T)0;
       d4[u] = (df && q < N) ? FT[(size_t)i * Ns + sm.ele[q]] : (T)0;
     }
-    const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
+    const int kb = tp[i], ke = t_end(i);
     jj = 0;
     tt = vv = (T)0;
-    if (kb + lane < ke && lane < 32) {
+    if (kb + lane < ke) {
       jj = S.tgt_j[kb + lane];
       tt = (T)S.tgt_t[kb + lane];
       vv = TV[kb + lane];
     }
   };
+  const int tix = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
   if (warp < Ns) fetch(warp, gu, gd, jl, tl, vl);
   for (int i = warp; i < Ns; i += NWARP) {
     const int inext = i + NWARP;
     if (inext < Ns) fetch(inext, nu, nd, njl, ntl, nvl);
-    const int kb = S.tgt_ptr[i], ke = S.tgt_ptr[i + 1];
+    const int kb = tp[i], ke = t_end(i);
     const bool up_free = sm.occ[i] < 0, dn_free = sm.occ[Ns + i] < 0;
     if (kb < ke && (up_free || dn_free)) {
       for (int q0 = kb; q0 < ke; q0 += 32) {
@@ -861,43 +901,59 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
           }
         }
         const int nq = min(32, ke - q0);
-        for (int qq = 0; qq < nq; ++qq) {
-          const int j = __shfl_sync(0xffffffffu, jc, qq);
-          const T tij = __shfl_sync(0xffffffffu, tc, qq);
-          const T vji = __shfl_sync(0xffffffffu, vc, qq);
-          const int eu = sm.occ[j], ed = sm.occ[Ns + j];
-          if (up_free && eu >= 0) {
-            T part = (T)0;
+        for (int g0 = 0; g0 < nq; g0 += 4) {
+          // terms 2r (up electron on j_r -> i) and 2r+1 (down electron), r < 4
+          int jr[4], eur[4], edr[4];
+          T tr[4], vr[4];
+          bool any = false;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int q = lane + 32 * u;
-              if (q < N) part += gu[u] * sm.minv[q * ldm + eu];
-            }
-            part = warp_sum(part);
-            const T lm =
-                S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i, j, -1, -1, lane, 32)) : (T)0;
-            if (lane == 0) {
-              eo += -tij * part * corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, 0, j, i, vji)) *
-                    (S.n_hidden ? exp_t<T>(lm) : (T)1);
-              mc.meas_hop++;
-            }
+          for (int r = 0; r < 4; ++r) {
+            const bool ex = g0 + r < nq;
+            jr[r] = __shfl_sync(0xffffffffu, jc, (g0 + r) & 31);
+            tr[r] = __shfl_sync(0xffffffffu, tc, (g0 + r) & 31);
+            vr[r] = __shfl_sync(0xffffffffu, vc, (g0 + r) & 31);
+            eur[r] = (ex && up_free) ? sm.occ[jr[r]] : -1;
+            edr[r] = (ex && dn_free) ? sm.occ[Ns + jr[r]] : -1;
+            any |= eur[r] >= 0 || edr[r] >= 0;
           }
-          if (dn_free && ed >= 0) {
-            const T *row = sm.minv + (ed - N) * ldm;
-            T part = (T)0;
+          if (!any) continue;
+          // Branch-free: absent terms read column / row 0 and are masked, so
+          // all 32 shared loads can be in flight together (gu, gd are 0 for
+          // q >= N; q is clamped to a valid row).
+          T p[8];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int cu = max(eur[r], 0), rd = max(edr[r] - N, 0);
+            T su = (T)0, sd = (T)0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int q = lane + 32 * u;
-              if (q < N) part += gd[u] * row[q];
+              const int q = min(lane + 32 * u, N - 1);
+              su += gu[u] * sm.minv[q * ldm + cu];
+              sd += gd[u] * sm.minv[rd * ldm + q];
             }
-            part = warp_sum(part);
-            const T lm =
-                S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, i + Ns, j + Ns, -1, -1, lane, 32)) : (T)0;
-            if (lane == 0) {
-              eo += -tij * part * corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, 1, j, i, vji)) *
-                    (S.n_hidden ? exp_t<T>(lm) : (T)1);
-              mc.meas_hop++;
+            p[2 * r] = eur[r] >= 0 ? su : (T)0;
+            p[2 * r + 1] = edr[r] >= 0 ? sd : (T)0;
+          }
+          const T sum = reduce8_transposed(p, lane);
+          // this lane's term: r = tix >> 1, spin = tix & 1
+          const int r = tix >> 1, sp = tix & 1;
+          const int j = sel4(jr, r);
+          const int el = sp ? sel4(edr, r) : sel4(eur, r);
+          T lm = (T)0;
+          if (S.n_hidden) {
+            T mq[8];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) {
+              mq[2 * rr] = eur[rr] >= 0 ? mlp_log_ratio_part(S, sm, i, jr[rr], -1, -1, lane, 32) : (T)0;
+              mq[2 * rr + 1] =
+                  edr[rr] >= 0 ? mlp_log_ratio_part(S, sm, i + Ns, jr[rr] + Ns, -1, -1, lane, 32) : (T)0;
             }
+            lm = reduce8_transposed(mq, lane);
+          }
+          if ((lane & 3) == 0 && el >= 0) {
+            const T c = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, sp, j, i, sel4(vr, r)));
+            eo += -sel4(tr, r) * sum * c * (S.n_hidden ? exp_t<T>(lm) : (T)1);
+            mc.meas_hop++;
           }
         }
       }
@@ -953,62 +1009,52 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     for (int i = tid; i < Ns; i += NT)
       if (sm.occ[i] >= 0 && sm.occ[Ns + i] >= 0 && S.g_idx[i] >= 0) acc_add(acc + S.g_idx[i], (T)1);
   }
-  if (S.n_v > 0) {
-    for (int i = tid; i < Ns; i += NT) {
-      const int mi = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
-      if (mi != 0) sm.ilist[atomicAdd(&sm.misc[0], 1)] = i;
-    }
+  if (S.n_v > 0 && !S.local_spin) {
+    // O_v(class) = sum over the class's pairs i < j of m_i m_j, m = n - 1:
+    // one warp per class over its pair list, integer sums, no atomics.
+    // (Under the local-spin constraint every m_i = 0 and O_v = 0.)
+    int *mval = sm.ilist;
+    for (int i = tid; i < Ns; i += NT) mval[i] = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
     __syncthreads();
-    const int K = sm.misc[0];
-    const int npair = K * (K - 1) / 2;
-    constexpr int VB = 8;   // class gathers issued before the atomics of a batch
-    for (int p0 = tid; p0 < npair; p0 += VB * NT) {
-      int cls[VB], mm[VB];
-#pragma unroll
-      for (int u = 0; u < VB; ++u) {
-        const int p = p0 + u * NT;
-        cls[u] = -1;
-        if (p < npair) {
-          // unordered pair p -> (a, b), a < b, row-major over the strict upper triangle
-          int a = (int)((2.0f * K - 1.0f - sqrtf((2.0f * K - 1.0f) * (2.0f * K - 1.0f) - 8.0f * p)) * 0.5f);
-          if (a < 0) a = 0;
-          while (a > 0 && a * (2 * K - a - 1) / 2 > p) --a;
-          while ((a + 1) * (2 * K - a - 2) / 2 <= p) ++a;
-          const int b = p - a * (2 * K - a - 1) / 2 + a + 1;
-          const int i = sm.ilist[a], j = sm.ilist[b];
-          cls[u] = S.v_idx[(size_t)i * Ns + j];
-          const int mi = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
-          const int mj = (sm.occ[j] >= 0) + (sm.occ[Ns + j] >= 0) - 1;
-          mm[u] = mi * mj;
-        }
+    for (int c = warp; c < S.n_v; c += NWARP) {
+      int acc_i = 0;
+      const int pe = S.vptr[c + 1];
+#pragma unroll 4
+      for (int q = S.vptr[c] + lane; q < pe; q += 32) {
+        const unsigned pr = S.vpair[q];
+        acc_i += mval[pr & 0xFFFFu] * mval[pr >> 16];
       }
-#pragma unroll
-      for (int u = 0; u < VB; ++u)
-        if (cls[u] >= 0) acc_add(acc + S.n_g + cls[u], (T)mm[u]);
+      acc_i = warp_sum(acc_i);
+      if (lane == 0) acc[S.n_g + c] = (T)acc_i;
     }
   }
   // Pair orbital: d ln Pf / d f_ab = (M^-1)_{mn} for a = r_n,up, b = r_m,dn
   // (= -(X^-1)_{n, N+m}, Eq. DiffPf / Appendix C), times the class sign.
+  // One warp per up electron n (site a), lanes over the down electrons m;
+  // two rows in flight; the class and sign come from one packed table.
   const int base = S.n_g + S.n_v;
-  constexpr int OB = 16;  // gathers issued before the atomics of a batch
-  for (int p0 = tid; p0 < N * N; p0 += OB * NT) {
-    int cls[OB];
-    T val[OB];
+  for (int n0 = warp; n0 < N; n0 += 2 * NWARP) {
+    int code[2][4];
+    T val[2][4];
 #pragma unroll
-    for (int u = 0; u < OB; ++u) {
-      const int p = p0 + u * NT;
-      cls[u] = -1;
-      if (p < N * N) {
-        const int n = p / N, m = p - n * N;
-        const size_t ab = (size_t)sm.ele[n] * Ns + sm.ele[N + m];
-        cls[u] = S.f_idx[ab];
-        const T v = sm.minv[m * ldm + n];
-        val[u] = S.f_sign[ab] > 0 ? v : -v;
+    for (int h = 0; h < 2; ++h) {
+      const int n = n0 + h * NWARP;
+      const int *frow = S.fcode + (size_t)(n < N ? sm.ele[n] : 0) * Ns;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int m = lane + 32 * u;
+        const bool ok = n < N && m < N;
+        code[h][u] = ok ? frow[sm.ele[N + m]] : -1;
+        val[h][u] = ok ? sm.minv[m * ldm + n] : (T)0;
       }
     }
 #pragma unroll
-    for (int u = 0; u < OB; ++u)
-      if (cls[u] >= 0) acc_add(acc + base + cls[u], val[u]);
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int cd = code[h][u];
+        if (cd >= 0) acc_add(acc + base + (cd >> 1), (cd & 1) ? -val[h][u] : val[h][u]);
+      }
   }
   if (S.n_hidden) {
     // MLP factor: dW1_kc = w2_k (1 - t_k^2) n_c, db1_k = w2_k (1 - t_k^2),

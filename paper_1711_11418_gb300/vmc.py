@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libvmc.so")
 
 FP64, MIXED = 0, 1
 FORCE_STATIC_MAX_DOUBLES = 1 << 20
-CHOLESKY, CG, CG_DENSE = 0, 1, 2
+CHOLESKY, CG, CG_DENSE, MIXED_IR = 0, 1, 2, 3
 _I32P = C.POINTER(C.c_int32)
 _F64P = C.POINTER(C.c_double)
 _I8P = C.POINTER(C.c_int8)
@@ -61,7 +61,8 @@ class VmcSrOpts(C.Structure):
 
 class VmcSrReport(C.Structure):
     _fields_ = [("energy", C.c_double), ("norm_g", C.c_double), ("norm_dalpha", C.c_double),
-                ("cg_iters", C.c_int32), ("n_params", C.c_int32)]
+                ("cg_iters", C.c_int32), ("n_params", C.c_int32), ("rel_residual", C.c_double),
+                ("fallback", C.c_int32)]
 
 
 class VmcError(RuntimeError):
