@@ -30,16 +30,31 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-# FP32 lanes per SM and SM count of GB300 (sm_103); FP64 nominal rate.
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# FP32 lanes and FP64 FMA units per SM, SM count and maximum clock of GB300
+# (sm_103): the ALU peaks the sweep (FP32) and the from-scratch inverses
+# (FP64) are judged against.
+SMS, FP32_LANES, FP64_UNITS, SM_MAX_MHZ = 152, 128, 2, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+FP64_PEAK_TFLOPS = SMS * FP64_UNITS * 2 * SM_MAX_MHZ * 1e6 / 1e12
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels at 4096 walkers (profiles/k_sample_float_hubbard16x16_w4096.md,
+# profiles/k_init_float_hubbard16x16_w4096.md); proportional to walkers.
+TRAFFIC_SWEEP_4096 = 225.811712e6 + 181.474304e6
+TRAFFIC_INIT_4096 = 5.515264e6 + 159.806464e6
+
+
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=4096)
@@ -56,6 +71,22 @@ def parse():
 def workload():
     from paper_1711_11418_gb300 import inputs
     return inputs.square16_hubbard()
+
+
+METRIC = "Pfaffian hop-updates/s, 16x16 Hubbard (mixed/batched form; plain FP64 beside)"
+
+
+def workload_config(args, prob, world):
+    """The `config` object of both arms: the workload, with its sizes."""
+    return {"workload": "hubbard_16x16_U8_Ne224_apbc", "walkers": args.walkers,
+            "samples_per_walker_per_step": args.samples, "sweeps_between_samples": 1,
+            "proposals_per_sweep": prob.Ne, "p_exchange": prob.p_exchange, "Np": prob.Np,
+            "recompute_every_accepted": args.recompute,
+            "sr": "dense S (FP64 SYRK plain / split-BF16 tensor cores mixed); FP64 Cholesky "
+                  "plain, FP64 iterative refinement on an FP32 inverse mixed; shift_rel 1e-3, "
+                  "dtau 0.05",
+            "l2": "no flush: walker state (4096 x 50.6 KB FP32 inverses) exceeds the 129 MB L2",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def dist_info():
@@ -80,7 +111,7 @@ class Clocks:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -174,15 +205,16 @@ def run_reference(args):
             props.append(sum(r[0] for r in res))
     pool.close()
     value = sum(props) / sum(times)
-    line = {"impl": "reference", "metric": "Pfaffian hop-updates/s (16x16 Hubbard)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": value, "unit": "proposals/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "hubbard_16x16_U8_Ne224_apbc", "walkers_per_step": cores,
-                       "proposals_per_walker_per_step": per},
+            "config": workload_config(args, workload(), 1),
             "cpu_baseline": {"value": value, "unit": "proposals/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{cores} chains x {per} proposals per step"},
+                             "sample": f"each step: {cores} chains of the workload (one per core) "
+                                       f"x {per} proposals, ratios from two Parlett-Reid "
+                                       f"Pfaffians; measurement and SR not included"},
             "e2e": {"value": value, "unit": "proposals/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -218,8 +250,12 @@ def measured_alu_peaks(torch):
 
 
 def flops_of(d, N, precision):
-    """Algorithmic FLOPs of the sweep kernel from its counters:
-    returns (flops in the sweep's arithmetic type, FP64 recompute flops)."""
+    """Algorithmic FLOPs of the sweep kernel from its counters: a tested hop
+    2N (one dot product), a tested exchange 2N^2 + 6N (a row-vector times
+    M^-1 and the 2x2 entries), an accepted hop 4N^2 (that product and the
+    rank-1 update), an accepted exchange 6N^2 (rank-2 update), a measured hop
+    ratio 2N, a measured exchange ratio 2N^2 + 6N.  Returns (flops in the
+    sweep's arithmetic type, FP64 in-sweep recompute flops 2N^3 each)."""
     main = (2 * N * d["n_hop_tested"] + (2 * N * N + 6 * N) * d["n_exchange_tested"]
             + 4 * N * N * d["n_hop_accepted"] + 6 * N * N * d["n_exchange_accepted"]
             + 2 * N * d["n_measured_hops"] + (2 * N * N + 6 * N) * d["n_measured_exchanges"])
@@ -352,35 +388,52 @@ def run_ours(args):
 
     peaks = measured_alu_peaks(torch)
     sm = summarize(mixed)
-    # roofline of the dominant kernel (the sweep kernel): FP32 FLOPs per launch / launch time
+    # Rooflines of the two large kernels of the mixed step; the one with more
+    # device time in the timed region is reported as `roofline`.
+    #  sweep + measurement (k_sample<float>): FP32 FLOPs from its counters per
+    #    launch / launch time, against the FP32 ALU peak; its HBM fraction beside;
+    #  from-scratch inverses (k_init<float>): 2 N^3 FP64 FLOPs per inverse
+    #    (every walker after each SR step, plus in-sweep recomputes) / time,
+    #    against the FP64 peak.
+    hbm, hbm_src = hbm_peak_gbs()
+    scale = args.walkers / 4096.0
     f32, f64rec = flops_of(mixed["stats"], N, "mixed")
     sweep_ms, sweep_n = mixed["kt"]["sweep"]
     t_launch = sweep_ms * 1e-3 / max(sweep_n, 1)
     ach = f32 / max(sweep_n, 1) / t_launch / 1e12
-    ach64 = f64rec / max(sweep_n, 1) / t_launch / 1e12
+    sweep_gbs = TRAFFIC_SWEEP_4096 * scale / t_launch / 1e9
+    roof_sweep = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                  "frac": ach / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_SWEEP_4096 * scale,
+                  "kernel": "k_sample<float> (sweep + measurement)",
+                  "ms_in_timed_region": sweep_ms,
+                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                  "hbm": {"achieved_gbs": sweep_gbs, "peak_gbs": hbm, "frac": sweep_gbs / hbm,
+                          "peak_source": hbm_src}}
+    init_ms, _ = mixed["kt"]["init"]
+    n_inv = args.steps * args.walkers + mixed["stats"]["n_recomputes"]
+    ach_init = 2.0 * N ** 3 * n_inv / max(init_ms * 1e-3, 1e-12) / 1e12
+    roof_init = {"bound": "alu", "achieved": ach_init, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                 "frac": ach_init / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_INIT_4096 * scale,
+                 "kernel": "k_init<float> (FP64 from-scratch inverses)",
+                 "ms_in_timed_region": init_ms,
+                 "peak_source": "derived: 152 SMs x 2 FP64 FMA units x 2 x 2070 MHz "
+                                "(a DFMA throughput loop measured 1.198 TFLOP/s)"}
+    roof, roof2 = (roof_init, roof_sweep) if init_ms > sweep_ms else (roof_sweep, roof_init)
+    roof["measured_gemm_tflops"] = peaks
     line = {
-        "metric": "Pfaffian hop-updates/s, 16x16 Hubbard (mixed/batched form; plain FP64 beside)",
+        "metric": METRIC,
         "value": sm["proposals_per_s"], "unit": "proposals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sm["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "hubbard_16x16_U8_Ne224_apbc", "walkers": args.walkers,
-                   "samples_per_walker_per_step": args.samples, "sweeps_between_samples": 1,
-                   "proposals_per_sweep": prob.Ne, "p_exchange": prob.p_exchange, "Np": prob.Np,
-                   "recompute_every_accepted": args.recompute,
-                   "sr": "dense S (FP64 SYRK plain / split-BF16 tensor cores mixed); FP64 Cholesky plain, FP64 iterative refinement on an FP32 inverse mixed; shift_rel 1e-3, dtau 0.05",
-                   "l2": "no flush: walker state (4096 x 50.6 KB FP32 inverses) exceeds the 129 MB L2",
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": workload_config(args, prob, world),
         "mixed": sm,
         "plain_fp64": summarize(fp64) if fp64 else None,
         "speedup_mixed_over_fp64": (sm["proposals_per_s"] / summarize(fp64)["proposals_per_s"]) if fp64 else None,
         "energy_check": {"same_configs_dE_per_site_mean": dE, "same_configs_dE_per_site_max": dE_max,
                          "tolerance": 1e-4},
-        "roofline": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                     "kernel": "k_sample<float> (sweep + measurement)",
-                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                     "measured_gemm_tflops": peaks},
+        "roofline": roof,
+        "roofline_second": roof2,
         "clocks": mixed["clocks"],
         "gpu_launches": mixed["launches"],
         "e2e": e2e,

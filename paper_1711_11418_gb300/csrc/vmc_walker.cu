@@ -1096,6 +1096,8 @@ struct GJShared {
   double pmin, pmax;   // smallest / largest |pivot|
   double ipiv;
   double colk[VMC_MAX_N];   // pivot column of the current step (row k zeroed)
+  double apiv[VMC_MAX_N];   // |pivot| of every step
+  double pminw[NWARP];
 };
 
 __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, GJShared &g) {
@@ -1152,9 +1154,7 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
       g.colk[bi] = g.colk[k];
       g.colk[k] = 0.0;   // row k is scaled, not eliminated
       g.ipiv = 1.0 / piv;
-      g.logdet += log(fabs(piv));
-      g.pmin = fmin(g.pmin, fabs(piv));
-      g.pmax = fmax(g.pmax, fabs(piv));
+      g.apiv[k] = fabs(piv);   // log|det| is summed after the elimination
       if ((piv < 0.0) != (bi != k)) g.sign = -g.sign;
     }
     __syncthreads();
@@ -1188,16 +1188,49 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
     }
     __syncthreads();
   }
+  // log|det M| and the pivot range, off the elimination's serial path
+  {
+    double ls = 0.0, mn = 1e300, mx = 0.0;
+    for (int i = tid; i < N; i += NT) {
+      const double a = g.apiv[i];
+      ls += log(a);
+      mn = fmin(mn, a);
+      mx = fmax(mx, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ls += __shfl_xor_sync(0xffffffffu, ls, o);
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((tid & 31) == 0) {
+      g.val[tid >> 5] = ls;
+      g.pminw[tid >> 5] = mn;
+      g.amax[tid >> 5] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 1e300, c = 0.0;
+      for (int q = 0; q < NWARP; ++q) {
+        a += g.val[q];
+        b = fmin(b, g.pminw[q]);
+        c = fmax(c, g.amax[q]);
+      }
+      g.logdet = a;
+      g.pmin = b;
+      g.pmax = c;
+    }
+  }
   for (int k = N - 1; k >= 0; --k) {
     const int p = perm[k];
-    if (p != k)
-      for (int r = tid; r < N; r += NT) {
-        const double t0 = A[(size_t)r * lda + k];
-        A[(size_t)r * lda + k] = A[(size_t)r * lda + p];
-        A[(size_t)r * lda + p] = t0;
-      }
+    if (p == k) continue;   // uniform: perm is shared
+    for (int r = tid; r < N; r += NT) {
+      const double t0 = A[(size_t)r * lda + k];
+      A[(size_t)r * lda + k] = A[(size_t)r * lda + p];
+      A[(size_t)r * lda + p] = t0;
+    }
     __syncthreads();
   }
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
