@@ -1,0 +1,118 @@
+"""Parity at the benchmark's full size and launch configuration: the 16x16
+Hubbard lattice (U/t = 8, Ne = 224, APBC, Np = 1069), 4096 walkers, four
+samples per walker per call, in-sweep FP64 recompute every 256 accepted
+moves.
+
+The oracle computes sampled outputs one by one (a local energy at this size
+is about a thousand 224 x 224 Parlett-Reid Pfaffians):
+
+* mixed form: E_loc of sampled rows within 1e-4 t per site of the oracle,
+  O_k rows within 1e-3 of max(1, |O|) (FP32 inverse entries);
+* plain FP64 form: E_loc and O_k of sampled rows within 1e-10;
+* SR from the GPU's own 16384 sample rows: g within 1e-10 and the
+  split-BF16 tensor-core S~ within 2e-4 of max |S~| of the FP64 product of
+  the same rows; the mixed solve's update has FP64 backward error < 1e-3
+  against the FP64 S~ (the split-BF16 error of S~ bounds it).
+"""
+import numpy as np
+import pytest
+
+from oracle import fock
+from oracle.hamiltonian import local_energy
+from oracle.sr import sr_matrices, shifted
+from oracle.wavefunction import Wavefunction
+from paper_1711_11418_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+W, S = 4096, 4
+CHECK_WALKERS = (0, 2047, 4095)
+
+
+@pytest.fixture(scope="module")
+def vmc():
+    from paper_1711_11418_gb300 import build, vmc as V
+    build.build()
+    return V
+
+
+@pytest.fixture(scope="module")
+def problem():
+    return I.square16_hubbard()
+
+
+def oracle_rows(p, params, ele_rows):
+    wf = Wavefunction(p, params)
+    out = []
+    for ele in ele_rows:
+        n = fock.from_labels(ele, p.Ns)
+        out.append((local_energy(wf, n), wf.log_derivatives(n)))
+    return out
+
+
+def run(vmc, p, precision, warm):
+    with vmc.Context(p, W, seed=2024, precision=precision, max_samples=S,
+                     recompute_every=256 if precision == vmc.MIXED else -1) as ctx:
+        ctx.sample(warm, 0, 0)
+        ctx.sample(0, S, 1)
+        E, O = ctx.get_samples()
+        ele, _ = ctx.get_configs()
+        params = ctx.get_params()
+        st = ctx.measure()
+        St, g = ctx.get_sr_matrices(1e-3, 0.0)
+        p0 = params.copy()
+        rep = ctx.sr_step(0.05, 1e-3, 0.0, solver=vmc.MIXED_IR, cg_eps=1e-12)
+        x = -(ctx.get_params() - p0) / 0.05
+    return dict(E=E, O=O, ele=ele, params=params, st=st, St=St, g=g, x=x, rep=rep)
+
+
+@pytest.fixture(scope="module")
+def mixed(vmc, problem):
+    return run(vmc, problem, vmc.MIXED, 10)
+
+
+def test_fullsize_mixed_sampled_rows_match_oracle(problem, mixed):
+    p = problem
+    assert mixed["st"]["n_proposals"] == W * (10 + S) * p.Ne
+    # the measurement is the last step of the call: row w*S + S-1 is the stored configuration
+    rows = [w * S + S - 1 for w in CHECK_WALKERS]
+    ref = oracle_rows(p, mixed["params"], [mixed["ele"][w] for w in CHECK_WALKERS])
+    for r, (e_ref, o_ref) in zip(rows, ref):
+        assert abs(mixed["E"][r] - e_ref) / p.Ns < 1e-4, (r, mixed["E"][r], e_ref)
+        scale = max(1.0, np.max(np.abs(o_ref)))
+        assert np.max(np.abs(mixed["O"][r] - o_ref)) < 1e-3 * scale
+
+
+def test_fullsize_sr_from_own_samples(problem, mixed):
+    E, O = mixed["E"], mixed["O"].astype(np.float64)
+    S_ref, g_ref, _, _ = sr_matrices(E, O)
+    St_ref = shifted(S_ref, 1e-3, 0.0)
+    assert np.max(np.abs(mixed["g"] - g_ref)) <= 1e-10 * np.max(np.abs(g_ref))
+    assert np.max(np.abs(mixed["St"] - St_ref)) <= 2e-4 * np.max(np.abs(St_ref))
+    assert mixed["rep"]["fallback"] == 0
+    res = np.linalg.norm(g_ref - St_ref @ mixed["x"]) / np.linalg.norm(g_ref)
+    assert res < 1e-3, res
+
+
+def well_conditioned(p, params, ele_rows, limit=1e8):
+    """Walkers whose M has cond < limit (the 1e-10 comparisons exclude the
+    rest, as for the small systems)."""
+    wf = Wavefunction(p, params)
+    N = p.N
+    return [k for k, e in enumerate(ele_rows)
+            if np.linalg.cond(wf.f[np.ix_(e[:N], e[N:])]) < limit]
+
+
+def test_fullsize_fp64_sampled_rows_match_oracle(vmc, problem):
+    p = problem
+    r64 = run(vmc, p, vmc.FP64, 1)
+    cand = [w for w in range(0, W, 97)]
+    ok = well_conditioned(p, r64["params"], [r64["ele"][w] for w in cand])
+    walkers = [cand[k] for k in ok[:2]]
+    assert len(walkers) == 2
+    rows = [w * S + S - 1 for w in walkers]
+    ref = oracle_rows(p, r64["params"], [r64["ele"][w] for w in walkers])
+    for r, (e_ref, o_ref) in zip(rows, ref):
+        assert r64["E"][r] == pytest.approx(e_ref, rel=1e-10, abs=1e-10)
+        scale = max(1.0, np.max(np.abs(o_ref)))
+        assert np.max(np.abs(r64["O"][r] - o_ref)) <= 1e-10 * scale
