@@ -307,12 +307,20 @@ def test_mixed_precision_close_to_fp64(vmc):
     assert np.allclose(res[vmc.FP64][1], res[vmc.MIXED][1], rtol=1e-3, atol=1e-3)
 
 
-@pytest.mark.parametrize("rows,Np", [(1000, 19), (2049, 300), (4096, 1069)])
-def test_sr_overlap_tensor_cores_split_bf16(vmc, rows, Np):
+@pytest.mark.parametrize("kernel", ["tma", "tiles"])
+@pytest.mark.parametrize("rows,Np", [(1000, 19), (2049, 300), (4096, 1069), (8192, 4100)])
+def test_sr_overlap_tensor_cores_split_bf16(vmc, rows, Np, kernel, monkeypatch):
     """Mixed form: S built by the tcgen05 split-BF16 GEMM (FP32 accumulation)
-    against the oracle's FP64 S; tiles, chunks and ragged edges covered.
-    Tolerance: 2e-4 of max|S| (three BF16 products ~2^-16 relative each, FP32
-    sums over the samples)."""
+    against the oracle's FP64 S; tiles, chunks and ragged edges covered, for
+    both kernels (persistent TMA-fed kernel, and one CTA per tile with
+    cp.async staging).  Tolerance: 2e-4 of max|S| (three BF16 products ~2^-16
+    relative each, FP32 sums over the samples)."""
+    if kernel == "tiles":
+        monkeypatch.setenv("VMC_TC_KERNEL", "tiles")
+    else:
+        monkeypatch.delenv("VMC_TC_KERNEL", raising=False)
+    if kernel == "tiles" and Np > 2000:
+        pytest.skip("the one-CTA-per-tile kernel is covered at the smaller sizes")
     base = I.ring8_hubbard()
     n_f = Np - base.n_g - base.n_v
     if n_f == base.n_f:
