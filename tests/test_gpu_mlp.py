@@ -112,7 +112,11 @@ def test_mlp_mixed_form_close_to_fp64(vmc):
 def test_trained_mlp_gains_over_plain_state(vmc):
     """Same SR budget on the 6-site ring (U/t = 8): the exact energy of the
     trained Pfaffian x MLP state (by enumeration) lies below that of the
-    trained plain state, and both above the exact ground state."""
+    trained plain state, and both above the exact ground state.  The SR
+    solve is the dense FP64 Cholesky: with 300+ CG iterations per step the
+    training trajectory is far more sensitive to the rounding order of the
+    O_k sums (shared-memory atomics), so runs differ; the direct solve keeps
+    them reproducible to about 1e-8."""
     from oracle.hamiltonian import ground_state_energy
     plain = I.make_problem("r6", I.chain(6, -1), 6, U=8.0, sub=(2, 1), jastrow="chain",
                            noise=0.05, seed=5, p_exchange=0.5)
@@ -125,7 +129,7 @@ def test_trained_mlp_gains_over_plain_state(vmc):
             ctx.sample(10, 0, 0)
             for _ in range(60):
                 ctx.sample(0, 20, 1)
-                ctx.sr_step(0.05, 1e-3, 1e-4, solver=vmc.CG, cg_eps=1e-8, cg_kmax=500)
+                ctx.sr_step(0.05, 1e-3, 1e-4, solver=vmc.CHOLESKY)
             params = ctx.get_params()
         out[name] = enumerate_expectations(Wavefunction(p, params))["energy"]
     assert out["plain"] >= e_ed - 1e-9 and out["mlp"] >= e_ed - 1e-9
