@@ -7,15 +7,16 @@
 //
 // Pass 1 (k_split_T): O (rows x Np, FP32 or FP64, row-major) -> Hi, Lo
 //   (Np_pad x K_pad BF16, parameter-major = K-major for the GEMM, zero padded).
-// Pass 2 (k_syrk_tc): one CTA per 128x128 tile of the upper triangle.  The
-//   four operand tiles of a 64-sample chunk (A_hi, A_lo, B_hi, B_lo) are
-//   staged in shared memory in the canonical no-swizzle K-major layout (8x8
-//   core matrices of 128 contiguous bytes); one thread issues
-//   tcgen05.mma.kind::f16 (BF16 in, FP32 accumulate into TMEM, M = N = 128,
-//   K = 16), tcgen05.commit signals an mbarrier when the chunk's MMAs have
-//   read shared memory, and the epilogue reads TMEM with tcgen05.ld and writes
-//   the tile and its mirror image.  Two shared-memory stages: the producers
-//   fill one while the tensor cores consume the other.  Every wait is bounded.
+// Pass 2, default (k_syrk_tma): persistent and warp-specialised.  One thread
+//   issues TMA tensor copies (128-byte swizzle) of the four operand tiles of
+//   a 64-sample chunk (A_hi, A_lo, B_hi, B_lo) into a 3-stage ring; one
+//   thread issues tcgen05.mma.kind::f16 (BF16 in, FP32 accumulate into TMEM,
+//   M = N = 128, K = 16) into one of two accumulators; four warps read the
+//   other accumulator with tcgen05.ld and write the previous tile and its
+//   mirror image.  Every wait is bounded.
+// Pass 2, fallback (k_syrk_tc): one CTA per 128x128 tile, operands staged
+//   by cp.async in the canonical no-swizzle K-major layout (8x8 core
+//   matrices of 128 contiguous bytes), three stages.
 #include "vmc_common.cuh"
 
 #include <cuda.h>
