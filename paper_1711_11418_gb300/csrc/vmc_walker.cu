@@ -1096,6 +1096,7 @@ struct GJShared {
   double pmin, pmax;   // smallest / largest |pivot|
   double ipiv;
   double colk[VMC_MAX_N];   // pivot column of the current step (row k zeroed)
+  double rowk[VMC_MAX_N];   // scaled pivot row of the current step (column k zeroed)
   double apiv[VMC_MAX_N];   // |pivot| of every step
   double pminw[NWARP];
 };
@@ -1161,30 +1162,60 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
     if (g.bad) return;
     const int p = g.piv;
     const double ipiv = g.ipiv;
-    // (3) the new column k, one row per thread (from the copy, so no conflict
-    // with the elimination below); then each thread owns columns c != k: swap
-    // rows k and p, scale row k, eliminate every other row with the copy.
+    // (3a) the new column k, one row per thread (from the copy); for every
+    // column c != k: swap rows k and p, scale row k, keep it in rowk.
     for (int i = tid; i < N; i += NT) A[(size_t)i * lda + k] = (i == k) ? ipiv : -g.colk[i] * ipiv;
     for (int c = tid; c < N; c += NT) {
-      if (c == k) continue;
+      if (c == k) {
+        g.rowk[c] = 0.0;   // column k is final: the update below leaves it
+        continue;
+      }
       double rkc = A[(size_t)p * lda + c];
       if (p != k) A[(size_t)p * lda + c] = A[(size_t)k * lda + c];
       rkc *= ipiv;
       A[(size_t)k * lda + c] = rkc;
-      int i = 0;
-      for (; i + 4 <= N; i += 4) {
-        double a0 = A[(size_t)i * lda + c], a1 = A[(size_t)(i + 1) * lda + c];
-        double a2 = A[(size_t)(i + 2) * lda + c], a3 = A[(size_t)(i + 3) * lda + c];
-        a0 -= g.colk[i] * rkc;
-        a1 -= g.colk[i + 1] * rkc;
-        a2 -= g.colk[i + 2] * rkc;
-        a3 -= g.colk[i + 3] * rkc;
-        A[(size_t)i * lda + c] = a0;
-        A[(size_t)(i + 1) * lda + c] = a1;
-        A[(size_t)(i + 2) * lda + c] = a2;
-        A[(size_t)(i + 3) * lda + c] = a3;
+      g.rowk[c] = rkc;
+    }
+    __syncthreads();
+    // (3b) A_ic -= colk_i rowk_c over all N x N entries, spread flat over the
+    // threads (whole warps for any N; colk_k = 0 leaves row k), four entries
+    // in flight per thread.
+    {
+      const int qn = NT / N, rn = NT - (NT / N) * N;
+      auto adv = [&](int &ii, int &cc) {
+        ii += qn;
+        cc += rn;
+        if (cc >= N) {
+          cc -= N;
+          ++ii;
+        }
+      };
+      int i = tid / N, c = tid - (tid / N) * N;
+      while (i < N) {
+        int i1 = i, c1 = c;
+        adv(i1, c1);
+        int i2 = i1, c2 = c1;
+        adv(i2, c2);
+        int i3 = i2, c3 = c2;
+        adv(i3, c3);
+        const bool b1 = i1 < N, b2 = i2 < N, b3 = i3 < N;
+        double *q0 = A + (size_t)i * lda + c;
+        double *q1 = A + (size_t)(b1 ? i1 : i) * lda + (b1 ? c1 : c);
+        double *q2 = A + (size_t)(b2 ? i2 : i) * lda + (b2 ? c2 : c);
+        double *q3 = A + (size_t)(b3 ? i3 : i) * lda + (b3 ? c3 : c);
+        double a0 = *q0, a1 = *q1, a2 = *q2, a3 = *q3;
+        a0 -= g.colk[i] * g.rowk[c];
+        if (b1) a1 -= g.colk[i1] * g.rowk[c1];
+        if (b2) a2 -= g.colk[i2] * g.rowk[c2];
+        if (b3) a3 -= g.colk[i3] * g.rowk[c3];
+        *q0 = a0;
+        if (b1) *q1 = a1;
+        if (b2) *q2 = a2;
+        if (b3) *q3 = a3;
+        i = i3;
+        c = c3;
+        adv(i, c);
       }
-      for (; i < N; ++i) A[(size_t)i * lda + c] -= g.colk[i] * rkc;
     }
     __syncthreads();
   }
