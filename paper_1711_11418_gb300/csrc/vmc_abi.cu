@@ -303,6 +303,9 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S, bool need_ir = false) {
     CK(dalloc(c, &w.scal, sizeof(double) * 8));
     CK(dalloc(c, &w.info, sizeof(int) * 4));
     CK(dalloc(c, &w.dblk, sizeof(double) * 32 * 32));
+    CK(dalloc(c, &w.vf, sizeof(float) * Np));
+    CK(dalloc(c, &w.tf, sizeof(float) * rows_cap));
+    CK(dalloc(c, &w.dpart, sizeof(double) * 512));
     const size_t nparts = (size_t)vmc_colreduce_parts(rows_cap, Np);
     CK(dalloc(c, &w.part, sizeof(double) * nparts * Np));
     s.sr_alloc = true;

@@ -133,6 +133,8 @@ struct SrWork {
   int *info;                   // device status
   double *dblk;                // [32*32] factored diagonal block in flight (Cholesky)
   double *part;                // column-reduction partials [vmc_colreduce_parts(rows, Np) * Np]
+  float *vf, *tf;              // FP32 copies of the SR-CG vectors (mixed form) [Np], [rows]
+  double *dpart;               // dot-product partials [512]
   void *chol_graph;            // cudaGraphExec_t of the Cholesky factor + solve (lazily built)
   // mixed-precision iterative refinement (vmc_sr_mixed.cu)
   float *S32;                  // [Np*Np] scaled S~, inverted in place

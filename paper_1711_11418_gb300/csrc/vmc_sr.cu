@@ -472,20 +472,6 @@ __global__ void k_cg_finish(const double *u, const double *obar, const double *o
   w[k] = u[k] - obar[k] * odv[0] + (shift_rel * diagS[k] + shift_abs) * v[k];
 }
 
-__global__ void k_dot_dev(const double *a, const double *b, int n, double *out, const int *done) {
-  __shared__ double red[256];
-  if (done && *done) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) out[0] = red[0];
-}
-
 // x += alpha p, r -= alpha w with alpha = rho / (p.w)
 __global__ void k_cg_update_xr(double *x, double *r, const double *p, const double *w,
                                const double *rho, const double *pw, int n, int *flags) {
@@ -502,26 +488,6 @@ __global__ void k_cg_update_xr(double *x, double *r, const double *p, const doub
   if (k >= n) return;
   x[k] += alpha * p[k];
   r[k] -= alpha * w[k];
-}
-
-// rho' = r.r; done if rho' < threshold (one block)
-__global__ void k_cg_check(const double *r, int n, double *rho_new, const double *thr, int *flags) {
-  __shared__ double red[256];
-  if (flags[0]) return;
-  double s = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += r[i] * r[i];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    rho_new[0] = red[0];
-    flags[1] += 1;
-    if (!(red[0] >= thr[0])) flags[0] = 1;   // converged (or NaN: flagged below)
-    if (!isfinite(red[0])) flags[2] = 1;
-  }
 }
 
 // p = r + (rho'/rho) p
@@ -690,23 +656,145 @@ void vmc_sr_release(SrWork &w) {
   w.chol_graph = nullptr;
 }
 
+// Mixed form (FP32 O): the two passes of the SR-CG product with FP32
+// products summed in FP32 over 16 terms and the partial sums in FP64, so the
+// FP64 pipe (1/64 of the FP32 rate on this part) does one add per 16
+// products; relative error of each product sum about 1e-6 at most.  The
+// operand vectors enter as FP32 copies.
+constexpr int CH32 = 16;
+
+__global__ void k_to_float(const double *v, int n, float *vf, const int *done) {
+  if (done && *done) return;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) vf[k] = (float)v[k];
+}
+
+// t = O v, one warp per row; t in FP64 and as an FP32 copy
+__global__ void k_gemv_rows_f32(const float *O, int ldO, int rows, int Np, const float *vf,
+                                double *t, float *tf, const int *done) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= rows || *done) return;
+  const float *o = O + (size_t)warp * ldO;
+  double s = 0.0;
+  for (int k0 = lane; k0 < Np; k0 += 32 * CH32) {
+    float a = 0.0f;
+#pragma unroll
+    for (int u = 0; u < CH32; ++u) {
+      const int k = k0 + 32 * u;
+      if (k < Np) a = fmaf(o[k], vf[k], a);
+    }
+    s += (double)a;
+  }
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    t[warp] = s;
+    tf[warp] = (float)s;
+  }
+}
+
+// part[c][k] = sum over the rows of chunk c of O_rk t_r (thread per column)
+__global__ void __launch_bounds__(RB) k_colreduce_t32(const float *O, int ldO, int rows, int Np,
+                                                      const float *tf, int chunk, double *part,
+                                                      const int *done) {
+  const int k = blockIdx.x * RB + threadIdx.x;
+  const int c = blockIdx.y;
+  if (k >= Np || (done && *done)) return;
+  const int r1 = min(rows, c * chunk + chunk);
+  const float *col = O + k;
+  double s = 0.0;
+  for (int r = c * chunk; r < r1; r += CH32) {
+    float a = 0.0f;
+#pragma unroll
+    for (int u = 0; u < CH32; ++u)
+      if (r + u < r1) a = fmaf(col[(size_t)(r + u) * ldO], tf[r + u], a);
+    s += (double)a;
+  }
+  part[(size_t)c * Np + k] = s;
+}
+
+// Dot products over many CTAs, summed in a fixed order (deterministic):
+// dpart[b] = partial of CTA b; out = sum of the partials.
+constexpr int DOT_MAXB = 512;
+
+__global__ void k_dotp(const double *a, const double *b, int n, double *dpart, const int *done) {
+  __shared__ double red[256];
+  if (done && *done) return;
+  double s = 0.0;
+  for (int i = blockIdx.x * 256 + threadIdx.x; i < n; i += gridDim.x * 256) s += a[i] * b[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) dpart[blockIdx.x] = red[0];
+}
+
+__global__ void k_dotf(const double *dpart, int nb, double *out, const int *done) {
+  __shared__ double red[256];
+  if (done && *done) return;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 256) s += dpart[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+static int dot_blocks(int n) {
+  const int nb = (n + 4095) / 4096;
+  return nb < 1 ? 1 : (nb > DOT_MAXB ? DOT_MAXB : nb);
+}
+
+static void dot2(const double *a, const double *b, int n, double *out, double *dpart,
+                 const int *done, cudaStream_t st, long long *nl) {
+  const int nb = dot_blocks(n);
+  k_dotp<<<nb, 256, 0, st>>>(a, b, n, dpart, done);
+  k_dotf<<<1, 256, 0, st>>>(dpart, nb, out, done);
+  *nl += 2;
+}
+
+// convergence test on rho' = r.r (computed by dot2): done if rho' < threshold
+__global__ void k_cg_check2(const double *rho_new, const double *thr, int *flags) {
+  if (flags[0]) return;
+  const double v = rho_new[0];
+  flags[1] += 1;
+  if (!(v >= thr[0])) flags[0] = 1;   // converged (or NaN: flagged below)
+  if (!isfinite(v)) flags[2] = 1;
+}
+
 // One SR-CG product out = S~ v (Sec. 3.3.2): t = O v, u = O^T t / rows,
 // out = u - o (o . v) + shift terms.  2 (rows + 1) Np products for the S part.
 static cudaError_t srcg_matvec(const SrWork &w, const double *v, double *out, double shift_rel,
                                double shift_abs, const int *done, cudaStream_t st, long long *nl) {
   const int threads = 256;
   const int blocks = (int)(((size_t)w.rows * 32 + threads - 1) / threads);
-  if (w.precision == 0)
+  if (w.precision == 0) {
     k_gemv_rows<double><<<blocks, threads, 0, st>>>((const double *)w.O, w.ldO, w.rows, w.Np, v, w.t, done);
-  else
-    k_gemv_rows<float><<<blocks, threads, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, v, w.t, done);
-  ++*nl;
-  cudaError_t e = colreduce_any(w, 3, w.t, 0.0, 1.0 / w.rows, w.r + w.Np, st, nl, done);
-  if (e) return e;
-  k_dot_dev<<<1, 256, 0, st>>>(w.obar, v, w.Np, w.scal + 3, done);
+    ++*nl;
+    cudaError_t e = colreduce_any(w, 3, w.t, 0.0, 1.0 / w.rows, w.r + w.Np, st, nl, done);
+    if (e) return e;
+  } else {
+    k_to_float<<<(w.Np + 255) / 256, 256, 0, st>>>(v, w.Np, w.vf, done);
+    k_gemv_rows_f32<<<blocks, threads, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, w.vf,
+                                                w.t, w.tf, done);
+    const int nparts = vmc_colreduce_parts(w.rows, w.Np);
+    const int chunk = (w.rows + nparts - 1) / nparts;
+    dim3 grid((w.Np + RB - 1) / RB, nparts);
+    k_colreduce_t32<<<grid, RB, 0, st>>>((const float *)w.O, w.ldO, w.rows, w.Np, w.tf, chunk,
+                                         w.part, done);
+    k_sum_parts<<<(w.Np + 255) / 256, 256, 0, st>>>(w.part, nparts, w.Np, 1.0 / w.rows,
+                                                    w.r + w.Np, done);
+    *nl += 4;
+  }
+  dot2(w.obar, v, w.Np, w.scal + 3, w.dpart, done, st, nl);
   k_cg_finish<<<(w.Np + 255) / 256, 256, 0, st>>>(w.r + w.Np, w.obar, w.scal + 3, w.diagS, v,
                                                    shift_rel, shift_abs, w.Np, out, done);
-  *nl += 2;
+  *nl += 1;
   return cudaGetLastError();
 }
 
@@ -733,9 +821,9 @@ int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double 
   cudaMemsetAsync(w.x, 0, sizeof(double) * n, st);
   cudaMemcpyAsync(w.r, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
   cudaMemcpyAsync(w.p, w.g, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
-  k_dot_dev<<<1, 256, 0, st>>>(w.r, w.r, n, cg + 0, nullptr);
+  dot2(w.r, w.r, n, cg + 0, w.dpart, nullptr, st, nl);
   k_cg_init<<<1, 1, 0, st>>>(cg, flags, eps);
-  *nl += 2;
+  *nl += 1;
   const int batch = 16;
   int h[3] = {0, 0, 0};
   for (int k = 1; k <= kmax; ++k) {
@@ -746,11 +834,12 @@ int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double 
     } else if (srcg_matvec(w, w.p, w.w, shift_rel, shift_abs, flags, st, nl) != cudaSuccess) {
       return -3;
     }
-    k_dot_dev<<<1, 256, 0, st>>>(w.p, w.w, n, cg + 2, flags);
+    dot2(w.p, w.w, n, cg + 2, w.dpart, flags, st, nl);
     k_cg_update_xr<<<g, 256, 0, st>>>(w.x, w.r, w.p, w.w, rho, cg + 2, n, flags);
-    k_cg_check<<<1, 256, 0, st>>>(w.r, n, rho_new, cg + 4, flags);
+    dot2(w.r, w.r, n, rho_new, w.dpart, flags, st, nl);
+    k_cg_check2<<<1, 1, 0, st>>>(rho_new, cg + 4, flags);
     k_cg_update_p<<<g, 256, 0, st>>>(w.p, w.r, rho_new, rho, n, flags);
-    *nl += 4;
+    *nl += 3;
     if (k % batch == 0 || k == kmax) {
       if (cudaMemcpyAsync(h, flags, sizeof(int) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
       if (cudaStreamSynchronize(st) != cudaSuccess) return -3;

@@ -104,3 +104,28 @@ def test_mixed_ir_on_sampled_overlap_matrix(vmc):
         x = -(ctx.get_params() - p0) / 0.05
     res = np.linalg.norm(g - St @ x) / np.linalg.norm(g)
     assert res < (1e-11 if rep["fallback"] == 0 else 1e-8), (res, rep)
+
+
+def test_mixed_form_srcg_matches_oracle(vmc):
+    """Mixed form, CG with the SR-CG product (S never formed), whose two
+    passes over the FP32 samples sum FP32 products in FP32 over 16 terms and
+    in FP64 beyond: the update equals the oracle's Cholesky solution of the
+    same (FP32-rounded) samples within 1e-5, for 300 parameters and 2049
+    rows (ragged against the 16-term chunks)."""
+    base = I.ring8_hubbard()
+    Np = 300
+    n_f = Np - base.n_g - base.n_v
+    p = base.copy_with(n_f=n_f, f_idx=np.arange(64, dtype=np.int32), f_sign=np.ones(64, np.int8),
+                       params=np.concatenate([base.params[:3],
+                                              np.random.default_rng(0).uniform(-1, 1, n_f)]))
+    rows, W = 2049, 16
+    E, O = I.random_samples(rows, Np, seed=31)
+    O[:, : Np // 3] += 0.5
+    with vmc.Context(p, W, seed=1, precision=vmc.MIXED, max_samples=(rows + W - 1) // W) as ctx:
+        ctx.set_samples(E, O)
+        p0 = ctx.get_params()
+        rep = ctx.sr_step(0.05, 1e-3, 1e-4, solver=vmc.CG, cg_eps=1e-9, cg_kmax=1000)
+        d_gpu = ctx.get_params() - p0
+    d_ref, _ = sr_step(E, O.astype(np.float32).astype(np.float64), 0.05, 1e-3, 1e-4, "cholesky")
+    assert rep["cg_iters"] > 0
+    assert rel_close(d_gpu, d_ref, rtol=1e-5)
