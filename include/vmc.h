@@ -216,6 +216,18 @@ int vmc_set_samples(vmc_ctx *ctx, int32_t system, int32_t rows,
 int vmc_sr_step(vmc_ctx *ctx, int32_t system, const vmc_sr_opts *opts,
                 vmc_sr_report *report);
 
+/* One SR step for every system of the context with the same options
+ * (Sec. 3.3.1-3.3.2, as vmc_sr_step), for batches of independent systems:
+ * the work of all systems is enqueued before the host waits, so a batch of
+ * small systems costs two synchronisations instead of several per system.
+ * reports: NULL or n_sys entries (index = system).  With VMC_SOLVE_CHOLESKY
+ * and VMC_SOLVE_MIXED_IR the systems are solved together; with the CG
+ * solvers (their loop reads a convergence flag on the host) the call is
+ * vmc_sr_step for each system in turn.  Every system with samples is stepped
+ * even if another fails; the return value is the first error (VMC_ESTATE if
+ * a system has no samples, before any work).  Results equal vmc_sr_step's. */
+int vmc_sr_step_all(vmc_ctx *ctx, const vmc_sr_opts *opts, vmc_sr_report *reports);
+
 /* S~ (Np x Np, row-major, FP64) and g (Np) of the stored samples, as built
  * by vmc_sr_step's dense path (for checks).  Either pointer may be NULL. */
 int vmc_get_sr_matrices(vmc_ctx *ctx, int32_t system, double shift_rel,

@@ -49,6 +49,11 @@ struct vmc_ctx {
   double *d_scalar = nullptr;
   int recompute_every = 0;
   int delay_k = 0;            // as set by the caller (0/1 = immediate)
+  unsigned char *pin = nullptr;   // pinned staging for vmc_sr_step_all's results (per system)
+  // vmc_sr_step_all: systems run on a small pool of streams forked from st
+  static constexpr int NPOOL = 8;
+  cudaStream_t pool[NPOOL] = {};
+  cudaEvent_t fork_ev = nullptr, join_ev[NPOOL] = {};
   size_t smem_cap = 0;        // dynamic shared-memory limit set on the sweep kernels
   // timing (CUDA events on st): 0 sweep, 1 init, 2 SR step, 3 S GEMM
   bool timing = false;
@@ -65,6 +70,16 @@ void ctx_free(vmc_ctx *c) {
     vmc_sr_release(s.sr);
     vmc_sr_ir_release(s.sr);
   }
+  if (c->pin) cudaFreeHost(c->pin);
+  c->pin = nullptr;
+  for (int k = 0; k < vmc_ctx::NPOOL; ++k) {
+    if (c->pool[k]) cudaStreamDestroy(c->pool[k]);
+    if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+    c->pool[k] = nullptr;
+    c->join_ev[k] = nullptr;
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  c->fork_ev = nullptr;
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
 }
@@ -344,6 +359,18 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S, bool need_ir = false) {
 }
 
 // Dense S~: FP64 SIMT GEMM (plain form) or split-BF16 tensor-core GEMM (mixed).
+// Enqueue the S~ build (no host synchronisation; the tensor-core path's
+// status stays on the device).
+int build_S_launch(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs, cudaStream_t st) {
+  if (c->precision == VMC_MIXED) {
+    CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, s.tc_tiles,
+                          st, &c->n_launch));
+  } else {
+    CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, st, &c->n_launch));
+  }
+  return VMC_OK;
+}
+
 int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
   TimedRegion tr(c, 3);
   if (c->precision == VMC_MIXED) {
@@ -910,6 +937,155 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
     rep->fallback = fallback;
   }
   return VMC_OK;
+}
+
+// Results of one system's SR step copied to pinned host memory, read after
+// the single synchronisation of vmc_sr_step_all.
+struct SrStage {
+  int irflag[4];
+  int info[4];
+  int tcstat[4];
+  double irsc[3];
+  double ebar, gg, xx;
+};
+
+int vmc_sr_step_all(vmc_ctx *c, const vmc_sr_opts *o, vmc_sr_report *reps) {
+  if (!c || !o) return VMC_EINVAL;
+  if (!(o->dtau > 0.0) || o->shift_rel < 0.0 || o->shift_abs < 0.0) return VMC_EINVAL;
+  if (o->solver == VMC_SOLVE_CG || o->solver == VMC_SOLVE_CG_DENSE) {
+    // the CG loop reads its convergence flag on the host: system by system
+    for (int si = 0; si < c->n_sys; ++si) CK(vmc_sr_step(c, si, o, reps ? reps + si : nullptr));
+    return VMC_OK;
+  }
+  if (o->solver != VMC_SOLVE_CHOLESKY && o->solver != VMC_SOLVE_MIXED_IR) return VMC_EINVAL;
+  for (auto &s : c->sys)
+    if (!s.rows) return VMC_ESTATE;
+  const bool ir = o->solver == VMC_SOLVE_MIXED_IR;
+  if (!c->pin) {
+    if (cudaHostAlloc((void **)&c->pin, sizeof(SrStage) * (size_t)c->n_sys, cudaHostAllocDefault) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      c->pin = nullptr;
+      return VMC_ENOMEM;
+    }
+  }
+  SrStage *stg = (SrStage *)c->pin;
+  if (!c->fork_ev) {
+    bool okp = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; okp && k < vmc_ctx::NPOOL; ++k)
+      okp = cudaStreamCreateWithFlags(&c->pool[k], cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!okp) {
+      cudaGetLastError();
+      return VMC_ECUDA;
+    }
+  }
+  for (auto &s : c->sys) CK(sr_alloc(c, s, true, ir));
+  const double eps = o->cg_eps > 0.0 ? o->cg_eps : 1e-12;
+  const int kmax = o->cg_kmax > 0 ? std::min(o->cg_kmax, 16) : 8;
+  const int np = std::min(c->n_sys, (int)vmc_ctx::NPOOL);
+  // fork: the pool streams wait for everything queued on st so far; join:
+  // st waits for the pool.  System si runs on pool[si % np].
+  auto fork = [&]() -> int {
+    CKC(cudaEventRecord(c->fork_ev, c->st));
+    for (int k = 0; k < np; ++k) CKC(cudaStreamWaitEvent(c->pool[k], c->fork_ev, 0));
+    return VMC_OK;
+  };
+  auto join = [&]() -> int {
+    for (int k = 0; k < np; ++k) {
+      CKC(cudaEventRecord(c->join_ev[k], c->pool[k]));
+      CKC(cudaStreamWaitEvent(c->st, c->join_ev[k], 0));
+    }
+    return VMC_OK;
+  };
+  TimedRegion tr(c, 2);
+  // (1) every system's means, force, S~ and solve, enqueued without a wait
+  CK(fork());
+  for (int si = 0; si < c->n_sys; ++si) {
+    SysHost &s = c->sys[si];
+    SrWork &w = s.sr;
+    cudaStream_t st = c->pool[si % np];
+    CKC(vmc_sr_means(w, st, &c->n_launch));
+    CKC(vmc_sr_build_g(w, st, &c->n_launch));
+    CK(build_S_launch(c, s, o->shift_rel, o->shift_abs, st));
+    if (c->precision == VMC_MIXED)
+      CKC(cudaMemcpyAsync(stg[si].tcstat, s.tc_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    else
+      stg[si].tcstat[0] = 0;
+    if (ir) {
+      if (vmc_sr_ir_launch(w, kmax, eps, st, &c->n_launch)) return VMC_ECUDA;
+      if (vmc_sr_ir_fetch(w, stg[si].irflag, stg[si].irsc, st)) return VMC_ECUDA;
+    } else {
+      if (vmc_sr_cholesky_launch(w, st, &c->n_launch)) return VMC_ECUDA;
+      CKC(cudaMemcpyAsync(stg[si].info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
+    }
+  }
+  CK(join());
+  CKC(cudaStreamSynchronize(c->st));
+  // (2) systems whose refinement did not converge: FP64 Cholesky (rare)
+  int rc = VMC_OK;
+  std::vector<int> iters(c->n_sys, 0), fallback(c->n_sys, 0), ok(c->n_sys, 1);
+  std::vector<double> relres(c->n_sys, 0.0);
+  for (int si = 0; si < c->n_sys; ++si) {
+    SysHost &s = c->sys[si];
+    if (stg[si].tcstat[0]) {
+      ok[si] = 0;
+      if (rc == VMC_OK) rc = VMC_ETIMEOUT;
+      continue;
+    }
+    if (ir) {
+      if (vmc_sr_ir_eval(stg[si].irflag, stg[si].irsc, &iters[si], &relres[si]) == 1) {
+        fallback[si] = 1;
+        const int r2 = vmc_sr_cholesky_solve(s.sr, c->st, &c->n_launch);
+        if (r2) {
+          ok[si] = 0;
+          if (rc == VMC_OK) rc = r2;
+        }
+      }
+    } else if (stg[si].info[0]) {
+      ok[si] = 0;
+      if (rc == VMC_OK) rc = VMC_ESINGULAR;
+    }
+  }
+  // (3) norms for the reports, then the updates of the systems that solved
+  CK(fork());
+  for (int si = 0; si < c->n_sys; ++si) {
+    if (!ok[si]) continue;
+    SrWork &w = c->sys[si].sr;
+    cudaStream_t st = c->pool[si % np];
+    CKC(vmc_dot_dev(w.g, w.g, w.Np, w.scal + 5, w.dpart, st, &c->n_launch));
+    CKC(vmc_dot_dev(w.x, w.x, w.Np, w.scal + 6, w.dpart, st, &c->n_launch));
+    CKC(cudaMemcpyAsync(&stg[si].gg, w.scal + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CKC(cudaMemcpyAsync(&stg[si].ebar, w.ebar, sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  CK(join());
+  CKC(cudaStreamSynchronize(c->st));
+  CK(fork());
+  for (int si = 0; si < c->n_sys; ++si) {
+    SysHost &s = c->sys[si];
+    if (!ok[si]) continue;
+    if (!isfinite(stg[si].xx)) {
+      if (rc == VMC_OK) rc = VMC_ENUMERIC;
+      continue;
+    }
+    cudaStream_t st = c->pool[si % np];
+    CKC(vmc_sr_update_params((double *)s.dev.params, s.sr.x, o->dtau, s.Np, st, &c->n_launch));
+    CKC(vmc_launch_expand(&s.dev, st, &c->n_launch));
+    s.dirty = true;
+    if (reps) {
+      vmc_sr_report &r = reps[si];
+      r.energy = stg[si].ebar;
+      r.norm_g = sqrt(stg[si].gg);
+      r.norm_dalpha = o->dtau * sqrt(stg[si].xx);
+      r.cg_iters = iters[si];
+      r.n_params = s.Np;
+      r.rel_residual = relres[si];
+      r.fallback = fallback[si];
+    }
+  }
+  CK(join());
+  CKC(cudaStreamSynchronize(c->st));
+  return rc;
 }
 
 int vmc_get_params(vmc_ctx *c, int32_t system, double *params) {

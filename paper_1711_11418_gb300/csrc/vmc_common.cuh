@@ -156,6 +156,12 @@ int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl);
 void vmc_sr_release(SrWork &w);
 int vmc_sr_ir_solve(SrWork &w, int max_iter, double eps, int *iters, double *rel_res,
                     cudaStream_t st, long long *nl);
+int vmc_sr_ir_launch(SrWork &w, int max_iter, double eps, cudaStream_t st, long long *nl);
+int vmc_sr_ir_fetch(const SrWork &w, int *flags4, double *scal3, cudaStream_t st);
+int vmc_sr_ir_eval(const int *fl, const double *sc, int *iters, double *rel_res);
+int vmc_sr_cholesky_launch(SrWork &w, cudaStream_t st, long long *nl);
+cudaError_t vmc_dot_dev(const double *a, const double *b, int n, double *out_dev, double *dpart,
+                        cudaStream_t st, long long *nl);
 void vmc_sr_ir_release(SrWork &w);
 int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double eps,
                     int kmax, int *iters, cudaStream_t st, long long *nl, int dense);

@@ -45,14 +45,16 @@ __device__ __forceinline__ double ld(const TO *p) { return (double)*p; }
 template <typename TO>
 __global__ void __launch_bounds__(RB) k_colreduce(const TO *O, int ldO, int rows, int Np,
                                                   const double *obar, const double *wvec,
-                                                  double wshift, int mode, int chunk,
-                                                  double *part, const int *done) {
+                                                  double wshift_h, const double *wshift_d,
+                                                  int mode, int chunk, double *part,
+                                                  const int *done) {
   const int k = blockIdx.x * RB + threadIdx.x;
   const int c = blockIdx.y;
   if (k >= Np || (done && *done)) return;
   const int r0 = c * chunk;
   const int r1 = min(rows, r0 + chunk);
   const double ok = (mode == 1 || mode == 2) ? obar[k] : 0.0;
+  const double wshift = wshift_d ? *wshift_d : wshift_h;
   const TO *col = O + k;
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   int r = r0;
@@ -515,12 +517,12 @@ __global__ void k_update_params(double *p, const double *x, double dtau, int n) 
 template <typename TO>
 cudaError_t colreduce(const SrWork &w, const TO *O, int mode, const double *wvec, double wshift,
                       double scale, double *out, cudaStream_t st, long long *nl,
-                      const int *done = nullptr) {
+                      const int *done = nullptr, const double *wshift_d = nullptr) {
   const int nparts = vmc_colreduce_parts(w.rows, w.Np);
   const int chunk = (w.rows + nparts - 1) / nparts;
   dim3 grid((w.Np + RB - 1) / RB, nparts);
-  k_colreduce<TO><<<grid, RB, 0, st>>>(O, w.ldO, w.rows, w.Np, w.obar, wvec, wshift, mode, chunk,
-                                       w.part, done);
+  k_colreduce<TO><<<grid, RB, 0, st>>>(O, w.ldO, w.rows, w.Np, w.obar, wvec, wshift, wshift_d, mode,
+                                       chunk, w.part, done);
   k_sum_parts<<<(w.Np + 255) / 256, 256, 0, st>>>(w.part, nparts, w.Np, scale, out, done);
   *nl += 2;
   return cudaGetLastError();
@@ -528,10 +530,12 @@ cudaError_t colreduce(const SrWork &w, const TO *O, int mode, const double *wvec
 
 cudaError_t colreduce_any(const SrWork &w, int mode, const double *wvec, double wshift,
                           double scale, double *out, cudaStream_t st, long long *nl,
-                          const int *done = nullptr) {
+                          const int *done = nullptr, const double *wshift_d = nullptr) {
   if (w.precision == 0)
-    return colreduce<double>(w, (const double *)w.O, mode, wvec, wshift, scale, out, st, nl, done);
-  return colreduce<float>(w, (const float *)w.O, mode, wvec, wshift, scale, out, st, nl, done);
+    return colreduce<double>(w, (const double *)w.O, mode, wvec, wshift, scale, out, st, nl, done,
+                             wshift_d);
+  return colreduce<float>(w, (const float *)w.O, mode, wvec, wshift, scale, out, st, nl, done,
+                          wshift_d);
 }
 
 }  // namespace
@@ -543,12 +547,8 @@ cudaError_t vmc_sr_means(const SrWork &w, cudaStream_t st, long long *nl) {
 }
 
 cudaError_t vmc_sr_build_g(const SrWork &w, cudaStream_t st, long long *nl) {
-  // wshift must be a host value: read ebar back (small, once per SR step)
-  double ebar = 0.0;
-  cudaError_t e = cudaMemcpyAsync(&ebar, w.ebar, sizeof(double), cudaMemcpyDeviceToHost, st);
-  if (e) return e;
-  if ((e = cudaStreamSynchronize(st))) return e;
-  return colreduce_any(w, 1, w.E, ebar, 1.0 / w.rows, w.g, st, nl);
+  // E - ebar with ebar read by the kernel from device memory (no host round trip)
+  return colreduce_any(w, 1, w.E, 0.0, 1.0 / w.rows, w.g, st, nl, nullptr, w.ebar);
 }
 
 cudaError_t vmc_sr_diag(const SrWork &w, cudaStream_t st, long long *nl) {
@@ -620,7 +620,7 @@ static long long chol_launches(int n) {
   return c;
 }
 
-int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl) {
+int vmc_sr_cholesky_launch(SrWork &w, cudaStream_t st, long long *nl) {
   if (!w.chol_graph) {
     // Capture on a private stream (the caller's may be the legacy stream,
     // which cannot be captured).
@@ -644,6 +644,12 @@ int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl) {
   }
   if (cudaGraphLaunch((cudaGraphExec_t)w.chol_graph, st) != cudaSuccess) return -3;
   *nl += chol_launches(w.Np);
+  return 0;
+}
+
+// Factor and solve; returns 0, -4 (S~ not positive definite) or -3.
+int vmc_sr_cholesky_solve(SrWork &w, cudaStream_t st, long long *nl) {
+  if (vmc_sr_cholesky_launch(w, st, nl)) return -3;
   int info = 0;
   if (cudaMemcpyAsync(&info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return -3;
@@ -857,6 +863,12 @@ cudaError_t vmc_sr_update_params(double *params, const double *x, double dtau, i
                                  cudaStream_t st, long long *nl) {
   k_update_params<<<(Np + 255) / 256, 256, 0, st>>>(params, x, dtau, Np);
   ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_dot_dev(const double *a, const double *b, int n, double *out_dev, double *dpart,
+                        cudaStream_t st, long long *nl) {
+  dot2(a, b, n, out_dev, dpart, nullptr, st, nl);
   return cudaGetLastError();
 }
 

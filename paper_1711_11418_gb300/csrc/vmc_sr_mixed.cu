@@ -262,10 +262,9 @@ long long vmc_sr_ir_launches(int n, int max_iter) {
   return 3 + 2LL * ((n + GB - 1) / GB) + 3LL * max_iter;
 }
 
-// Returns 0 (converged; *iters = refinement steps), 1 (not converged or S~
-// unusable: the caller solves by FP64 Cholesky), or -3 on a CUDA error.
-int vmc_sr_ir_solve(SrWork &w, int max_iter, double eps, int *iters, double *rel_res,
-                    cudaStream_t st, long long *nl) {
+// Launch the refinement (the captured graph, made on first use).  Returns 0
+// or -3 on a CUDA error.
+int vmc_sr_ir_launch(SrWork &w, int max_iter, double eps, cudaStream_t st, long long *nl) {
   if (!w.ir_graph || w.ir_iter != max_iter || w.ir_eps != eps) {
     if (w.ir_graph) cudaGraphExecDestroy((cudaGraphExec_t)w.ir_graph);
     w.ir_graph = nullptr;
@@ -291,14 +290,37 @@ int vmc_sr_ir_solve(SrWork &w, int max_iter, double eps, int *iters, double *rel
   }
   if (cudaGraphLaunch((cudaGraphExec_t)w.ir_graph, st) != cudaSuccess) return -3;
   *nl += vmc_sr_ir_launches(w.Np, max_iter);
-  int fl[4] = {0, 0, 0, 0};
-  double sc[3] = {0, 0, 0};
-  if (cudaMemcpyAsync(fl, w.irflag, sizeof(fl), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
-  if (cudaMemcpyAsync(sc, w.scal, sizeof(sc), cudaMemcpyDeviceToHost, st) != cudaSuccess) return -3;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+  return 0;
+}
+
+// Enqueue the copies of the refinement's flags (4 ints) and scalars (3
+// doubles) to host memory; evaluate them after the stream has synchronised.
+int vmc_sr_ir_fetch(const SrWork &w, int *flags4, double *scal3, cudaStream_t st) {
+  if (cudaMemcpyAsync(flags4, w.irflag, sizeof(int) * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -3;
+  if (cudaMemcpyAsync(scal3, w.scal, sizeof(double) * 3, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return -3;
+  return 0;
+}
+
+// 0: converged (*iters refinement steps, *rel_res = |r| / |g|); 1: not
+// converged or S~ unusable (the caller solves by FP64 Cholesky).
+int vmc_sr_ir_eval(const int *fl, const double *sc, int *iters, double *rel_res) {
   *iters = fl[2];
   *rel_res = sc[1] > 0.0 ? sqrt(sc[2] / sc[1]) : 0.0;
   return (fl[0] && !fl[1]) ? 0 : 1;
+}
+
+// Returns 0 (converged; *iters = refinement steps), 1 (not converged or S~
+// unusable: the caller solves by FP64 Cholesky), or -3 on a CUDA error.
+int vmc_sr_ir_solve(SrWork &w, int max_iter, double eps, int *iters, double *rel_res,
+                    cudaStream_t st, long long *nl) {
+  if (vmc_sr_ir_launch(w, max_iter, eps, st, nl)) return -3;
+  int fl[4] = {0, 0, 0, 0};
+  double sc[3] = {0, 0, 0};
+  if (vmc_sr_ir_fetch(w, fl, sc, st)) return -3;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return -3;
+  return vmc_sr_ir_eval(fl, sc, iters, rel_res);
 }
 
 void vmc_sr_ir_release(SrWork &w) {

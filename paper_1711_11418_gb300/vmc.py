@@ -78,7 +78,7 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_sr_step", "vmc_get_sr_matrices", "vmc_get_params", "vmc_set_params",
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
            "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
-           "vmc_get_delay", "vmc_tune_delay"]
+           "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all"]
 
 
 def load(path: str = LIB_PATH):
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
     L.vmc_get_samples.argtypes = [P, C.c_int32, _F64P, _F64P]
     L.vmc_set_samples.argtypes = [P, C.c_int32, C.c_int32, _F64P, _F64P]
     L.vmc_sr_step.argtypes = [P, C.c_int32, C.POINTER(VmcSrOpts), C.POINTER(VmcSrReport)]
+    L.vmc_sr_step_all.argtypes = [P, C.POINTER(VmcSrOpts), C.POINTER(VmcSrReport)]
     L.vmc_get_sr_matrices.argtypes = [P, C.c_int32, C.c_double, C.c_double, _F64P, _F64P]
     L.vmc_get_params.argtypes = [P, C.c_int32, _F64P]
     L.vmc_set_params.argtypes = [P, C.c_int32, _F64P]
@@ -266,6 +267,14 @@ class Context:
         r = VmcSrReport()
         _check(self._L.vmc_sr_step(self._h, system, C.byref(o), C.byref(r)), "vmc_sr_step")
         return {k: getattr(r, k) for k, _ in VmcSrReport._fields_}
+
+    def sr_step_all(self, dtau, shift_rel=0.0, shift_abs=0.0, solver=CHOLESKY, cg_eps=1e-10,
+                    cg_kmax=1000):
+        """One SR step for every system (vmc_sr_step_all); a report per system."""
+        o = VmcSrOpts(dtau, shift_rel, shift_abs, solver, cg_eps, cg_kmax)
+        reps = (VmcSrReport * len(self.problems))()
+        _check(self._L.vmc_sr_step_all(self._h, C.byref(o), reps), "vmc_sr_step_all")
+        return [{k: getattr(r, k) for k, _ in VmcSrReport._fields_} for r in reps]
 
     def get_sr_matrices(self, shift_rel=0.0, shift_abs=0.0, system=0, with_S=True):
         Np = self.num_params(system)
