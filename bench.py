@@ -94,6 +94,19 @@ def dist_info():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def reduce_over_ranks(torch, value, op):
+    """`value` reduced over all ranks ("max" or "sum"); the value itself when
+    no process group is running.  Replicas are timed by the slowest rank and
+    credited with the work of all."""
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # Clock sampling during the timed region
 # ---------------------------------------------------------------------------
@@ -305,18 +318,20 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
+    ms = reduce_over_ranks(torch, e0.elapsed_time(e1), "max")
     st1 = ctx.measure()
     kt = ctx.kernel_times()
     launches = ctx.kernel_launches() - l0
     d = delta(st0, st1)
+    props_all = reduce_over_ranks(torch, d["n_proposals"], "sum")
     timed = reps[-args.steps:]
     solve = dict(solver="mixed_ir" if precision == vmc.MIXED else "cholesky_fp64",
                  refinement_steps_max=max(r["cg_iters"] for r in timed),
                  fallbacks=sum(r["fallback"] for r in timed),
                  rel_residual_max=max(r["rel_residual"] for r in timed))
     return ctx, dict(ms=ms, stats=d, kt=kt, launches=launches, clocks=clk,
-                     energy=statistics.fmean(energies), last=st1, solve=solve)
+                     energy=statistics.fmean(energies), last=st1, solve=solve,
+                     props_all=props_all, sr=sr)
 
 
 def run_ours(args):
@@ -363,13 +378,13 @@ def run_ours(args):
             for _ in range(args.steps):
                 ctx.set_params(hp)
                 ctx.sample(0, args.samples, 1)
-                ctx.sr_step(dtau=0.05, shift_rel=1e-3, solver=vmc.CHOLESKY)
+                ctx.sr_step(**mixed["sr"])
                 hp[:] = ctx.get_params()
                 _ = ctx.measure()["energy"]
             torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            props = ctx.measure()["n_proposals"] - p0
-            e2e = {"value": props * world / dt, "unit": "proposals/s",
+            dt = reduce_over_ranks(torch, time.perf_counter() - t0, "max")
+            props = reduce_over_ranks(torch, ctx.measure()["n_proposals"] - p0, "sum")
+            e2e = {"value": props / dt, "unit": "proposals/s",
                    "h2d_bytes_per_step": 8 * prob.Np,
                    "d2h_bytes_per_step": 8 * prob.Np + 8 * args.walkers * args.samples + 64}
         ctx.close()
@@ -378,7 +393,7 @@ def run_ours(args):
         d = r["stats"]
         secs = r["ms"] * 1e-3
         sweep_ms, sweep_n = r["kt"]["sweep"]
-        return {"proposals_per_s": d["n_proposals"] * world / secs, "ms_per_step": r["ms"] / args.steps,
+        return {"proposals_per_s": r["props_all"] / secs, "ms_per_step": r["ms"] / args.steps,
                 "sweep_kernel_ms_per_launch": sweep_ms / max(sweep_n, 1), "sweep_launches": sweep_n,
                 "init_ms_per_step": r["kt"]["init"][0] / args.steps,
                 "sr_ms_per_step": r["kt"]["sr"][0] / args.steps,
