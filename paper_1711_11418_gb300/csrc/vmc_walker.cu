@@ -650,6 +650,14 @@ __device__ void delayed_hop_update(const SysDev &S, const WSmem<T> &sm, int e, i
 // One Metropolis proposal (Sec. 3.1.2).  Every thread runs it; decisions are
 // uniform across the block.
 // ---------------------------------------------------------------------------
+// An accepted move with |det M'/det M| below SMALL_RATIO amplifies the
+// rounding already in the updated inverse by more than 1/SMALL_RATIO: the
+// walker is then marked due for the next from-scratch rebuild whatever its
+// count of accepted moves (the count is set to RECOMPUTE_NOW, above any
+// recompute interval).
+constexpr double SMALL_RATIO = 1e-3;
+constexpr int RECOMPUTE_NOW = 1 << 30;
+
 struct MoveCounts {
   long long hop_t = 0, ex_t = 0, hop_a = 0, ex_a = 0;
   long long meas_hop = 0, meas_ex = 0, samples = 0;
@@ -695,7 +703,7 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
       }
       __syncthreads();
       mc.ex_a++;
-      acc_since++;
+      acc_since = (fabs((double)rpf) < SMALL_RATIO) ? RECOMPUTE_NOW : acc_since + 1;
     }
     return;
   }
@@ -744,7 +752,7 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   }
   __syncthreads();
   mc.hop_a++;
-  acc_since++;
+  acc_since = (fabs((double)rpf) < SMALL_RATIO) ? RECOMPUTE_NOW : acc_since + 1;
 }
 
 // ---------------------------------------------------------------------------
