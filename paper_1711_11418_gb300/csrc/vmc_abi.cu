@@ -999,9 +999,9 @@ int vmc_sr_step_all(vmc_ctx *c, const vmc_sr_opts *o, vmc_sr_report *reps) {
     return VMC_OK;
   };
   TimedRegion tr(c, 2);
-  // (1) every system's means, force, S~ and solve, enqueued without a wait
-  CK(fork());
-  for (int si = 0; si < c->n_sys; ++si) {
+  // (1) every system's means, force, S~ and solve, enqueued without a wait.
+  // An error stops the enqueueing; the pool is joined back in every case.
+  auto enqueue = [&](int si) -> int {
     SysHost &s = c->sys[si];
     SrWork &w = s.sr;
     cudaStream_t st = c->pool[si % np];
@@ -1019,9 +1019,14 @@ int vmc_sr_step_all(vmc_ctx *c, const vmc_sr_opts *o, vmc_sr_report *reps) {
       if (vmc_sr_cholesky_launch(w, st, &c->n_launch)) return VMC_ECUDA;
       CKC(cudaMemcpyAsync(stg[si].info, w.info, sizeof(int), cudaMemcpyDeviceToHost, st));
     }
-  }
+    return VMC_OK;
+  };
+  CK(fork());
+  int rq = VMC_OK;
+  for (int si = 0; si < c->n_sys && rq == VMC_OK; ++si) rq = enqueue(si);
   CK(join());
   CKC(cudaStreamSynchronize(c->st));
+  if (rq != VMC_OK) return rq;
   // (2) systems whose refinement did not converge: FP64 Cholesky (rare)
   int rc = VMC_OK;
   std::vector<int> iters(c->n_sys, 0), fallback(c->n_sys, 0), ok(c->n_sys, 1);
@@ -1048,29 +1053,37 @@ int vmc_sr_step_all(vmc_ctx *c, const vmc_sr_opts *o, vmc_sr_report *reps) {
     }
   }
   // (3) norms for the reports, then the updates of the systems that solved
-  CK(fork());
-  for (int si = 0; si < c->n_sys; ++si) {
-    if (!ok[si]) continue;
+  auto norms = [&](int si) -> int {
     SrWork &w = c->sys[si].sr;
     cudaStream_t st = c->pool[si % np];
     CKC(vmc_dot_dev(w.g, w.g, w.Np, w.scal + 5, w.dpart, st, &c->n_launch));
     CKC(vmc_dot_dev(w.x, w.x, w.Np, w.scal + 6, w.dpart, st, &c->n_launch));
     CKC(cudaMemcpyAsync(&stg[si].gg, w.scal + 5, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CKC(cudaMemcpyAsync(&stg[si].ebar, w.ebar, sizeof(double), cudaMemcpyDeviceToHost, st));
-  }
+    return VMC_OK;
+  };
+  CK(fork());
+  for (int si = 0; si < c->n_sys && rq == VMC_OK; ++si)
+    if (ok[si]) rq = norms(si);
   CK(join());
   CKC(cudaStreamSynchronize(c->st));
+  if (rq != VMC_OK) return rq;
+  auto update = [&](int si) -> int {
+    SysHost &s = c->sys[si];
+    cudaStream_t st = c->pool[si % np];
+    CKC(vmc_sr_update_params((double *)s.dev.params, s.sr.x, o->dtau, s.Np, st, &c->n_launch));
+    CKC(vmc_launch_expand(&s.dev, st, &c->n_launch));
+    return VMC_OK;
+  };
   CK(fork());
-  for (int si = 0; si < c->n_sys; ++si) {
+  for (int si = 0; si < c->n_sys && rq == VMC_OK; ++si) {
     SysHost &s = c->sys[si];
     if (!ok[si]) continue;
     if (!isfinite(stg[si].xx)) {
       if (rc == VMC_OK) rc = VMC_ENUMERIC;
       continue;
     }
-    cudaStream_t st = c->pool[si % np];
-    CKC(vmc_sr_update_params((double *)s.dev.params, s.sr.x, o->dtau, s.Np, st, &c->n_launch));
-    CKC(vmc_launch_expand(&s.dev, st, &c->n_launch));
+    if ((rq = update(si)) != VMC_OK) break;
     s.dirty = true;
     if (reps) {
       vmc_sr_report &r = reps[si];
@@ -1085,7 +1098,7 @@ int vmc_sr_step_all(vmc_ctx *c, const vmc_sr_opts *o, vmc_sr_report *reps) {
   }
   CK(join());
   CKC(cudaStreamSynchronize(c->st));
-  return rc;
+  return rq != VMC_OK ? rq : rc;
 }
 
 int vmc_get_params(vmc_ctx *c, int32_t system, double *params) {
