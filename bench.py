@@ -286,6 +286,12 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
                       max_samples=S, recompute_every=args.recompute if precision == vmc.MIXED else -1,
                       stream=stream.cuda_stream)
     ctx.sample(args.equil, 0, 0)                        # equilibration (untimed)
+    delay = None
+    if precision == vmc.MIXED:
+        # delayed-update depth by the autotuner, timed on the step's launch
+        # shape (one sweep and one measurement; these are warm-up sweeps)
+        delay, delay_ms = ctx.tune_delay(sweeps=1, candidates=(1, 2, 4, 8))
+        delay = {"chosen": delay, "ms_per_sweep": delay_ms}
     # plain form: FP64 Cholesky; mixed form: FP64 iterative refinement on an
     # FP32 inverse (FP64 Cholesky if it does not reach the residual target)
     sr = dict(dtau=0.05, shift_rel=1e-3, shift_abs=0.0,
@@ -331,7 +337,7 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
                  rel_residual_max=max(r["rel_residual"] for r in timed))
     return ctx, dict(ms=ms, stats=d, kt=kt, launches=launches, clocks=clk,
                      energy=statistics.fmean(energies), last=st1, solve=solve,
-                     props_all=props_all, sr=sr)
+                     props_all=props_all, sr=sr, delay=delay)
 
 
 def run_ours(args):
@@ -402,7 +408,7 @@ def run_ours(args):
                 "sr_ms_per_step": r["kt"]["sr"][0] / args.steps,
                 "acceptance": d["n_accepted"] / max(d["n_proposals"], 1),
                 "energy_per_site": r["energy"] / prob.Ns, "recomputes": d["n_recomputes"],
-                "sr_solve": r["solve"]}
+                "sr_solve": r["solve"], "delay_tuner": r["delay"]}
 
     peaks = measured_alu_peaks(torch)
     sm = summarize(mixed)

@@ -281,13 +281,14 @@ int vmc_set_delay(vmc_ctx *ctx, int32_t k);
 int32_t vmc_get_delay(vmc_ctx *ctx);
 
 /* Autotuner for the delay depth (no counterpart in the paper).  For each
- * candidate depth cand[0..n_cand) (NULL: 1, 4, 8, 16, 32) runs `sweeps`
- * Metropolis sweeps per walker as vmc_sample(ctx, sweeps, 0, 0) does -- they
- * advance the chains and count as warm-up -- timed with CUDA events on the
- * context's stream, then keeps the fastest depth.  In-sweep FP64 recomputes
- * are held off while timing; walkers that fall due meanwhile are rebuilt by
- * the next vmc_sample.  *chosen receives
- * it; ms (optional, n_cand entries) the milliseconds per sweep of each
+ * candidate depth cand[0..n_cand) (NULL: 1, 4, 8, 16, 32) runs
+ * vmc_sample(ctx, 0, 1, sweeps) -- `sweeps` Metropolis sweeps per walker and
+ * one measurement, the shape of a sampling step; the sweeps advance the
+ * chains and the measurement replaces the stored samples -- timed with CUDA
+ * events on the context's stream, then keeps the fastest depth.  In-sweep
+ * FP64 recomputes are held off while timing; walkers that fall due meanwhile
+ * are rebuilt by the next vmc_sample.  *chosen receives it; ms (optional,
+ * n_cand entries) the milliseconds per sweep (measurement included) of each
  * candidate (negative where the depth does not fit). */
 int vmc_tune_delay(vmc_ctx *ctx, int32_t sweeps, const int32_t *cand, int32_t n_cand,
                    int32_t *chosen, double *ms);

@@ -1213,7 +1213,7 @@ int vmc_tune_delay(vmc_ctx *c, int32_t sweeps, const int32_t *cand, int32_t n_ca
     if (ms) ms[q] = -1.0;
     if (set_delay_impl(c, cand[q]) != VMC_OK) continue;
     cudaEventRecord(e0, c->st);
-    rc = vmc_sample(c, sweeps, 0, 0);
+    rc = vmc_sample(c, 0, 1, sweeps);
     cudaEventRecord(e1, c->st);
     if (rc != VMC_OK) break;
     if (cudaEventSynchronize(e1) != cudaSuccess) {

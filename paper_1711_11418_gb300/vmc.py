@@ -322,8 +322,9 @@ class Context:
         return int(self._L.vmc_get_delay(self._h))
 
     def tune_delay(self, sweeps=2, candidates=None):
-        """Time `sweeps` warm-up sweeps per candidate depth, keep the fastest.
-        Returns (chosen, {k: ms per sweep, or None where it does not fit})."""
+        """Time vmc_sample(0, 1, sweeps) (sweeps + one measurement) per
+        candidate depth, keep the fastest.  Returns (chosen, {k: ms per sweep,
+        or None where it does not fit})."""
         cand = np.ascontiguousarray(candidates if candidates is not None else (1, 4, 8, 16, 32),
                                     np.int32)
         ms = np.zeros(cand.size)
