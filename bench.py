@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = SMS * FP64_UNITS * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels at 4096 walkers (profiles/k_sample_float_hubbard16x16_w4096.md,
 # profiles/k_init_float_hubbard16x16_w4096.md); proportional to walkers.
-TRAFFIC_SWEEP_4096 = 225.811712e6 + 181.474304e6
+TRAFFIC_SWEEP_4096 = 225.731328e6 + 181.081344e6
 TRAFFIC_INIT_4096 = 6.181120e6 + 160.923392e6
 
 
