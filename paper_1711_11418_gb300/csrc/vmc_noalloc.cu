@@ -17,7 +17,7 @@
 
 namespace {
 
-constexpr int RCHUNK = 2048;   // rows per partial sum (same chunking as the context path)
+constexpr int RCHUNK = 2048;   // rows per partial sum (fixed, so the scratch bound is simple)
 constexpr int RTHREADS = 256;
 constexpr int MAX_DEVICES = 64;
 
