@@ -116,3 +116,34 @@ def test_fullsize_fp64_sampled_rows_match_oracle(vmc, problem):
         assert r64["E"][r] == pytest.approx(e_ref, rel=1e-10, abs=1e-10)
         scale = max(1.0, np.max(np.abs(o_ref)))
         assert np.max(np.abs(r64["O"][r] - o_ref)) <= 1e-10 * scale
+
+
+# --- learned part at full lattice size: 16x16 Hubbard x MLP (512 -> 1024 -> 1)
+
+def _mlp_run(vmc, p, precision):
+    with vmc.Context(p, 64, seed=77, precision=precision, max_samples=1) as ctx:
+        ctx.sample(1, 1, 1)
+        E, O = ctx.get_samples()
+        ele, _ = ctx.get_configs()
+        params = ctx.get_params()
+    return E, O, ele, params
+
+
+def test_fullsize_mlp_sampled_rows_match_oracle(vmc):
+    """FP64 form with the MLP factor (Np = 527,406): E_loc and the whole O_k
+    row (Gutzwiller, Jastrow, pair orbitals and the MLP gradients) of sampled
+    rows within 1e-10 of the oracle; mixed form (BF16 W1) E_loc within
+    5e-3 t per site (the BF16 rounding of W1 moves the log-amplitude)."""
+    p = I.square16_hubbard_mlp()
+    E, O, ele, params = _mlp_run(vmc, p, vmc.FP64)
+    ok = well_conditioned(p, params, [ele[w] for w in range(0, 64, 7)])
+    walkers = [range(0, 64, 7)[k] for k in ok[:2]]
+    assert len(walkers) == 2
+    ref = oracle_rows(p, params, [ele[w] for w in walkers])
+    for w, (e_ref, o_ref) in zip(walkers, ref):
+        assert E[w] == pytest.approx(e_ref, rel=1e-10, abs=1e-10)
+        assert np.max(np.abs(O[w] - o_ref)) <= 1e-10 * max(1.0, np.max(np.abs(o_ref)))
+    E32, _, ele32, params32 = _mlp_run(vmc, p, vmc.MIXED)
+    ref32 = oracle_rows(p, params32, [ele32[w] for w in walkers])
+    for w, (e_ref, _) in zip(walkers, ref32):
+        assert abs(E32[w] - e_ref) / p.Ns < 5e-3
