@@ -177,3 +177,50 @@ def test_fullsize_j1j2_sampled_rows_match_oracle(vmc):
     ref32 = oracle_rows(p, params32, [ele32[w] for w in walkers])
     for w, (e_ref, _) in zip(walkers, ref32):
         assert abs(E32[w] - e_ref) / p.Ns < 1e-4
+
+
+# --- 8x8 FP64 workload (1024 walkers) and the 64-system uneven batch
+
+def test_fullsize_square8_fp64_sampled_rows_match_oracle(vmc):
+    """8x8 Hubbard (P x AP, Ne = 64, U/t = 4), 1024 walkers, FP64 everywhere:
+    sampled E_loc and O_k rows within 1e-10 of the oracle."""
+    p = I.square8_hubbard()
+    with vmc.Context(p, 1024, seed=8, precision=vmc.FP64, max_samples=2) as ctx:
+        ctx.sample(2, 2, 1)
+        E, O = ctx.get_samples()
+        ele, _ = ctx.get_configs()
+        params = ctx.get_params()
+    cand = [0, 511, 1023, 300]
+    ok = well_conditioned(p, params, [ele[w] for w in cand])
+    walkers = [cand[k] for k in ok[:3]]
+    assert len(walkers) >= 2
+    ref = oracle_rows(p, params, [ele[w] for w in walkers])
+    for w, (e_ref, o_ref) in zip(walkers, ref):
+        r = w * 2 + 1
+        assert E[r] == pytest.approx(e_ref, rel=1e-10, abs=1e-10)
+        assert np.max(np.abs(O[r] - o_ref)) <= 1e-10 * max(1.0, np.max(np.abs(o_ref)))
+
+
+def test_fullsize_batch64_mixed_sampled_rows_match_oracle(vmc):
+    """64 uneven Hubbard systems in one context (L in {4..16}, n = 0.875,
+    U/t in [2, 8]), mixed form with the in-sweep FP64 recompute every 64
+    accepted moves: for one system of each size, sampled E_loc within 1e-4 t
+    per site of the oracle."""
+    probs = I.batched_hubbard(64, seed=0)
+    with vmc.Context(probs, 64, seed=11, precision=vmc.MIXED, max_samples=2,
+                     recompute_every=64) as ctx:
+        ctx.sample(4, 2, 1)
+        got = {}
+        for s, p in enumerate(probs):
+            if p.Ns in got:
+                continue
+            E, _ = ctx.get_samples(s)
+            ele, _ = ctx.get_configs(s)
+            got[p.Ns] = (s, E, ele, ctx.get_params(s))
+    assert len(got) == 7
+    for Ns, (s, E, ele, params) in got.items():
+        p = probs[s]
+        ok = well_conditioned(p, params, [ele[w] for w in range(4)])
+        w = ok[0]
+        (e_ref, _), = oracle_rows(p, params, [ele[w]])
+        assert abs(E[w * 2 + 1] - e_ref) / Ns < 1e-4, (Ns, E[w * 2 + 1], e_ref)
