@@ -18,6 +18,8 @@ sampler       Metropolis chains with hop / exchange updates (Sec. 3.1.2).
 sr            SR matrices S, g and the solve: Cholesky or CG (Sec. 3.3.1-2,
               Algorithm 1).
 exact         Exact enumeration over all configurations (tiny systems).
+physics       Pair correlations by Eq. MC (measurement mode, Sec. 2.2.3) and the
+              structure factors of Sec. 2.4.2.
 
 Every function cites the passage it follows.  Pins against values the paper
 or mathematics fix live in ``tests/test_oracle_*.py``.

@@ -1,0 +1,143 @@
+"""Physical quantities of a fixed wave function (the measurement mode of
+Sec. 2.2.3, NVMCCalMode = 1): equal-time pair correlations estimated by
+Eq. MC, and the structure factors of Sec. 2.4.2 built from them.
+
+Test infrastructure, like the rest of ``oracle``: tests, the smoke check and
+the CPU-baseline leg of the benchmark may call it; the product library never
+does.
+
+For a configuration |x> and an operator A, the local estimator of Eq. MC is
+    A_loc(x) = <psi|A|x> / <psi|x> = sum_x' <x'|A|x> psi(x') / psi(x)
+(real psi): A acts on the ket |x>, each resulting |x'> is weighted by its
+amplitude, recomputed from scratch.  <A> is the mean of A_loc over
+configurations drawn from rho(x) = |psi(x)|^2 / <psi|psi> (Sec. 3.1.1).
+
+Pair correlations, one Ns x Ns matrix per kind (kind index, operator at
+site pair (i, j)):
+    0  c^dag_{i up} c_{j up}
+    1  c^dag_{i dn} c_{j dn}
+    2  n_i n_j,                 n_i = n_{i up} + n_{i dn}
+    3  S^z_i S^z_j,             S^z_i = (n_{i up} - n_{i dn}) / 2
+    4  S^+_i S^-_j,             S^+_i = c^dag_{i up} c_{i dn}, S^-_i its adjoint
+    5  S_i . S_j = S^z_i S^z_j + (S^+_i S^-_j + S^-_i S^+_j) / 2
+The off-diagonal kinds (0, 1, 4 and the transverse part of 5) are applied as
+operator strings in the canonical Fock basis with their Jordan-Wigner signs;
+the diagonal kinds (2, 3) are read off the occupations.
+
+Structure factors (Sec. 2.4.2): X(k) = (1/N_cell) sum_{i,j} exp(-i k.(R_i - R_j))
+<X_i^dag X_j>; from the kinds above, n_sigma(k) from 0 / 1, N(k) from 2,
+S^z(k) from 3, S(k) from 5.  The quantities of the comparison with exact
+diagonalisation (Sec. 4.1.1): the doublon
+density D = (1/Ns) sum_i <n_i,up n_i,dn>, the nearest-neighbour spin
+correlation S_nn = (1/(4 Ns)) sum_{i, mu} <S_{r_i} . S_{r_i + e_mu}> and
+S~(k) = S(k) / (3 Ns).
+"""
+import math
+
+import numpy as np
+
+from .fock import apply_string
+from .hamiltonian import basis
+
+KINDS = ("cdag_c_up", "cdag_c_dn", "n_n", "sz_sz", "sp_sm", "s_s")
+
+
+def _strings(Ns, i, j):
+    """Operator strings (left to right as written) of kinds 0, 1, 4 and of
+    S^-_i S^+_j, for the pair (i, j)."""
+    up_i, up_j, dn_i, dn_j = i, j, Ns + i, Ns + j
+    return {
+        0: [("+", up_i), ("-", up_j)],
+        1: [("+", dn_i), ("-", dn_j)],
+        4: [("+", up_i), ("-", dn_i), ("+", dn_j), ("-", up_j)],
+        "sm_sp": [("+", dn_i), ("-", up_i), ("+", up_j), ("-", dn_j)],
+    }
+
+
+def local_correlations(wf, n):
+    """[6, Ns, Ns] array of A_loc(x) for every kind and site pair (Eq. MC)."""
+    Ns = wf.Ns
+    s0, l0 = wf.amplitude_slog(n)
+    if s0 == 0.0:
+        raise ZeroDivisionError("psi(x) = 0")
+    cache = {}
+
+    def ratio(n2):
+        if n2 == n:
+            return 1.0
+        if n2 not in cache:
+            s1, l1 = wf.amplitude_slog(n2)
+            cache[n2] = 0.0 if s1 == 0.0 else s1 * s0 * math.exp(l1 - l0)
+        return cache[n2]
+
+    def loc(ops):
+        r = apply_string(ops, (1.0, n))
+        return 0.0 if r is None else r[0] * ratio(r[1])
+
+    up = np.array([(n >> i) & 1 for i in range(Ns)], np.float64)
+    dn = np.array([(n >> (Ns + i)) & 1 for i in range(Ns)], np.float64)
+    occ = up + dn
+    sz = 0.5 * (up - dn)
+    out = np.zeros((6, Ns, Ns))
+    out[2] = np.outer(occ, occ)
+    out[3] = np.outer(sz, sz)
+    for i in range(Ns):
+        for j in range(Ns):
+            st = _strings(Ns, i, j)
+            out[0, i, j] = loc(st[0])
+            out[1, i, j] = loc(st[1])
+            out[4, i, j] = loc(st[4])
+            out[5, i, j] = out[3, i, j] + 0.5 * (out[4, i, j] + loc(st["sm_sp"]))
+    return out
+
+
+def mean_correlations(wf, configs):
+    """Mean of local_correlations over configurations (bitmasks) drawn from
+    rho(x): the estimate of Eq. MC."""
+    acc = None
+    for n in configs:
+        v = local_correlations(wf, n)
+        acc = v if acc is None else acc + v
+    return acc / len(configs)
+
+
+def exact_correlations(wf):
+    """<psi|A|psi>/<psi|psi> for every kind and pair by enumeration of all
+    S^z = 0 configurations, weighted by rho(x) (tiny systems only)."""
+    N = wf.Ne // 2
+    states = basis(wf.Ns, N, N, wf.local_spin)
+    amps = np.array([wf.amplitude(n) for n in states])
+    w = amps ** 2
+    keep = np.nonzero(w > 0)[0]
+    w = w[keep] / w[keep].sum()
+    acc = np.zeros((6, wf.Ns, wf.Ns))
+    for k, wk in zip(keep, w):
+        acc += wk * local_correlations(wf, states[k])
+    return acc
+
+
+def doublon_density(corr):
+    """D = (1/Ns) sum_i <n_i,up n_i,dn>, from n_i^2 = n_i + 2 n_i,up n_i,dn
+    and n_i = <c^dag_{i up} c_{i up}> + <c^dag_{i dn} c_{i dn}>."""
+    Ns = corr.shape[-1]
+    d = np.diagonal(corr[2]) - np.diagonal(corr[0]) - np.diagonal(corr[1])
+    return float(0.5 * d.sum() / Ns)
+
+
+def nn_spin_correlation(corr, bond_i, bond_j):
+    """S_nn = (1/(4 Ns)) sum over the 2 d nearest-neighbour vectors e_mu of
+    every site; with the bond list holding each undirected nearest-neighbour
+    bond once, every bond occurs twice in that sum (i -> j and j -> i)."""
+    Ns = corr.shape[-1]
+    ss = corr[5]
+    tot = sum(ss[i, j] + ss[j, i] for i, j in zip(bond_i, bond_j))
+    return float(tot / (4.0 * Ns))
+
+
+def structure_factor(mat, R, k, n_cell=None):
+    """(1/N_cell) sum_{i,j} exp(-i k.(R_i - R_j)) mat[i, j] for one k
+    (real part; R: [Ns, d] site positions, k: [d])."""
+    Ns = mat.shape[0]
+    n_cell = Ns if n_cell is None else n_cell
+    ph = np.exp(-1j * (np.asarray(R, np.float64) @ np.asarray(k, np.float64)))
+    return float(np.real(ph @ mat @ np.conj(ph)) / n_cell)
