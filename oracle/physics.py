@@ -54,40 +54,59 @@ def _strings(Ns, i, j):
     }
 
 
+class _Local:
+    """Local estimators of one configuration n, with the amplitudes of the
+    configurations reached from it cached."""
+
+    def __init__(self, wf, n):
+        self.wf, self.n, self.Ns = wf, n, wf.Ns
+        self.s0, self.l0 = wf.amplitude_slog(n)
+        if self.s0 == 0.0:
+            raise ZeroDivisionError("psi(x) = 0")
+        self.cache = {}
+        Ns = wf.Ns
+        self.up = np.array([(n >> i) & 1 for i in range(Ns)], np.float64)
+        self.dn = np.array([(n >> (Ns + i)) & 1 for i in range(Ns)], np.float64)
+
+    def ratio(self, n2):
+        if n2 == self.n:
+            return 1.0
+        if n2 not in self.cache:
+            s1, l1 = self.wf.amplitude_slog(n2)
+            self.cache[n2] = 0.0 if s1 == 0.0 else s1 * self.s0 * math.exp(l1 - self.l0)
+        return self.cache[n2]
+
+    def loc(self, ops):
+        r = apply_string(ops, (1.0, self.n))
+        return 0.0 if r is None else r[0] * self.ratio(r[1])
+
+    def entry(self, kind, i, j):
+        up, dn = self.up, self.dn
+        if kind == 2:
+            return (up[i] + dn[i]) * (up[j] + dn[j])
+        szsz = 0.25 * (up[i] - dn[i]) * (up[j] - dn[j])
+        if kind == 3:
+            return szsz
+        st = _strings(self.Ns, i, j)
+        if kind in (0, 1, 4):
+            return self.loc(st[kind])
+        return szsz + 0.5 * (self.loc(st[4]) + self.loc(st["sm_sp"]))
+
+
+def local_correlation(wf, n, kind, i, j):
+    """One entry A_loc(x) of local_correlations (for large lattices)."""
+    return _Local(wf, n).entry(kind, i, j)
+
+
 def local_correlations(wf, n):
     """[6, Ns, Ns] array of A_loc(x) for every kind and site pair (Eq. MC)."""
+    L = _Local(wf, n)
     Ns = wf.Ns
-    s0, l0 = wf.amplitude_slog(n)
-    if s0 == 0.0:
-        raise ZeroDivisionError("psi(x) = 0")
-    cache = {}
-
-    def ratio(n2):
-        if n2 == n:
-            return 1.0
-        if n2 not in cache:
-            s1, l1 = wf.amplitude_slog(n2)
-            cache[n2] = 0.0 if s1 == 0.0 else s1 * s0 * math.exp(l1 - l0)
-        return cache[n2]
-
-    def loc(ops):
-        r = apply_string(ops, (1.0, n))
-        return 0.0 if r is None else r[0] * ratio(r[1])
-
-    up = np.array([(n >> i) & 1 for i in range(Ns)], np.float64)
-    dn = np.array([(n >> (Ns + i)) & 1 for i in range(Ns)], np.float64)
-    occ = up + dn
-    sz = 0.5 * (up - dn)
     out = np.zeros((6, Ns, Ns))
-    out[2] = np.outer(occ, occ)
-    out[3] = np.outer(sz, sz)
-    for i in range(Ns):
-        for j in range(Ns):
-            st = _strings(Ns, i, j)
-            out[0, i, j] = loc(st[0])
-            out[1, i, j] = loc(st[1])
-            out[4, i, j] = loc(st[4])
-            out[5, i, j] = out[3, i, j] + 0.5 * (out[4, i, j] + loc(st["sm_sp"]))
+    for kind in range(6):
+        for i in range(Ns):
+            for j in range(Ns):
+                out[kind, i, j] = L.entry(kind, i, j)
     return out
 
 

@@ -9,8 +9,9 @@ import pytest
 
 from oracle import fock
 from oracle.hamiltonian import local_energy
-from oracle.physics import (doublon_density, exact_correlations, local_correlations,
-                            mean_correlations, nn_spin_correlation, structure_factor)
+from oracle.physics import (doublon_density, exact_correlations, local_correlation,
+                            local_correlations, mean_correlations, nn_spin_correlation,
+                            structure_factor)
 from oracle.wavefunction import Wavefunction
 from paper_1711_11418_gb300 import inputs as I
 
@@ -191,3 +192,14 @@ def test_mean_over_configurations_is_the_average_of_local_values():
     m = mean_correlations(wf, cfgs)
     ref = sum(local_correlations(wf, n) for n in cfgs) / 3
     np.testing.assert_allclose(m, ref, rtol=0, atol=1e-15)
+
+
+def test_single_entry_matches_dense():
+    p = I.make_problem("c6t2", I.chain(6, -1), 6, t2=0.4, U=3.0, f_full=True, jastrow="chain",
+                       noise=0.3, seed=2)
+    wf = Wavefunction(p)
+    n = fock.from_labels(I.initial_configs(p.Ns, p.Ne, 1, False, 3)[0], p.Ns)
+    dense = local_correlations(wf, n)
+    for kind in range(6):
+        for i, j in ((0, 3), (2, 2), (5, 1)):
+            assert local_correlation(wf, n, kind, i, j) == dense[kind, i, j]
