@@ -11,7 +11,9 @@ pair orbitals (Np = 1069), 4096 walkers, synthetic seeded inputs.
 The headline `value` is the mixed form (FP32 sweep, FP64 from-scratch
 inverses, FP64 energies and solve); the plain FP64 form runs the same steps
 and is reported beside it, with the energy difference of the two forms on
-identical configurations.
+identical configurations.  After the timed steps, the pair correlations of
+the measurement mode (vmc_measure_corr) are timed on the mixed context's
+configurations and reported in their own object.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -64,6 +66,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-corr", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -396,6 +399,16 @@ def run_ours(args):
             e2e = {"value": props / dt, "unit": "proposals/s",
                    "h2d_bytes_per_step": 8 * prob.Np,
                    "d2h_bytes_per_step": 8 * prob.Np + 8 * args.walkers * args.samples + 64}
+        # Pair correlations of the walkers' configurations (measurement mode;
+        # not part of the optimisation step timed above): device time of the
+        # whole measurement and of its ratio kernel, CUDA events on the stream.
+        corr = None
+        if not args.no_corr:
+            ctx.measure_corr()                      # scratch allocation
+            runs = [ctx.measure_corr(timing=True)[1] for _ in range(5)]
+            k_ms = statistics.median(r[0] for r in runs)
+            all_ms = statistics.median(r[1] for r in runs)
+            corr = {"k_ms": k_ms, "all_ms": all_ms}
         ctx.close()
 
     def summarize(r):
@@ -444,6 +457,22 @@ def run_ours(args):
                                 "(a DFMA throughput loop measured 1.198 TFLOP/s)"}
     roof, roof2 = (roof_init, roof_sweep) if init_ms > sweep_ms else (roof_sweep, roof_init)
     roof["measured_gemm_tflops"] = peaks
+    pair_corr = None
+    if corr is not None:
+        # k_corr<float>: per configuration G_up (Ns N^2 FMA) and, for each of
+        # the N sites holding a down electron, G_dn and T (2 N Ns FMA each)
+        fl = 2.0 * 3 * prob.Ns * N * N * args.walkers
+        ach_c = fl / (corr["k_ms"] * 1e-3) / 1e12
+        pair_corr = {
+            "what": "all 6 x Ns^2 pair correlations (c+c up/dn, n n, SzSz, S+S-, S.S) of the "
+                    f"{args.walkers} walkers' current configurations, mixed form",
+            "ms_per_measurement": corr["all_ms"],
+            "configurations_per_s": args.walkers / (corr["all_ms"] * 1e-3),
+            "roofline": {"bound": "alu", "achieved": ach_c, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach_c / FP32_PEAK_TFLOPS, "traffic": None,
+                         "kernel": "k_corr<float>", "ms_per_launch": corr["k_ms"],
+                         "flops_per_launch": fl,
+                         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}}
     line = {
         "metric": METRIC,
         "value": sm["proposals_per_s"], "unit": "proposals/s", "n_gpus": world,
@@ -461,6 +490,7 @@ def run_ours(args):
                          "tolerance_applies_to": "the energy estimate (walker mean)"},
         "roofline": roof,
         "roofline_second": roof2,
+        "pair_correlations": pair_corr,
         "clocks": mixed["clocks"],
         "gpu_launches": mixed["launches"],
         "e2e": e2e,

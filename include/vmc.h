@@ -195,6 +195,31 @@ int vmc_sample(vmc_ctx *ctx, int32_t n_warmup, int32_t n_samples,
 /* Statistics of the stored samples of one system (Eq. MC) and counters. */
 int vmc_measure(vmc_ctx *ctx, int32_t system, vmc_stats *out);
 
+/* Equal-time pair correlations of the walkers' CURRENT configurations (the
+ * physical-quantity mode of Sec. 2.2.3, NVMCCalMode = 1): for every kind and
+ * site pair (i, j), the mean over the system's walkers of the local
+ * estimator of Eq. MC, A_loc(x) = <psi|A|x> / <psi|x> (A acting on the ket),
+ *   kind 0  c^dag_{i up} c_{j up}         kind 3  S^z_i S^z_j
+ *   kind 1  c^dag_{i dn} c_{j dn}         kind 4  S^+_i S^-_j
+ *   kind 2  n_i n_j                       kind 5  S_i . S_j
+ * with n_i = n_i,up + n_i,dn, S^z_i = (n_i,up - n_i,dn)/2,
+ * S^+_i = c^dag_{i up} c_{i dn}.  Averaging the results of calls between
+ * vmc_sample calls gives the Monte Carlo estimate of <A>; the structure
+ * factors of Sec. 2.4.2 (n_sigma(k), N(k), S^z(k), S(k)) and the doublon
+ * density and nearest-neighbour spin correlation of Sec. 4.1.1 follow from
+ * these matrices.  Hops and spin swaps are evaluated from the walker's
+ * M^-1 in the context's precision (FP64, or FP32 in the mixed form), the
+ * diagonal kinds are exact; the walker means are FP64.
+ * corr: host [6 * Ns * Ns], layout [kind][i][j] row-major.  ms: NULL or
+ * host [2]: the device milliseconds of the ratio kernel and of the whole
+ * measurement (CUDA events on the context's stream).  Rebuilds walker
+ * inverses first if parameters or configurations changed.  Device scratch
+ * (at most 512 MiB of per-CTA partial sums plus 56 Ns^2 bytes) is kept by
+ * the context.  Errors: VMC_EINVAL (bad system, NULL corr, or a context
+ * with the MLP factor, which this measurement does not evaluate),
+ * VMC_ESINGULAR, VMC_ENOMEM, VMC_ECUDA. */
+int vmc_measure_corr(vmc_ctx *ctx, int32_t system, double *corr, double *ms);
+
 /* Copy the stored samples of one system to host buffers: E [rows],
  * O [rows * Np] row-major, row = walker * n_samples + sample.  Either
  * pointer may be NULL. */

@@ -55,6 +55,8 @@ struct vmc_ctx {
   cudaStream_t pool[NPOOL] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[NPOOL] = {};
   size_t smem_cap = 0;        // dynamic shared-memory limit set on the sweep kernels
+  void *corr_buf = nullptr;   // vmc_measure_corr scratch (grown on demand)
+  size_t corr_bytes = 0;
   // timing (CUDA events on st): 0 sweep, 1 init, 2 SR step, 3 S GEMM
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
@@ -80,6 +82,9 @@ void ctx_free(vmc_ctx *c) {
   }
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   c->fork_ev = nullptr;
+  if (c->corr_buf) cudaFree(c->corr_buf);
+  c->corr_buf = nullptr;
+  c->corr_bytes = 0;
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
 }
@@ -1175,6 +1180,64 @@ int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, do
   if (logabsdet) *logabsdet = ld;
   if (sign) *sign = sg;
   return VMC_OK;
+}
+
+int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
+  if (!sys_ok(c, system) || !corr) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (s.dev.n_hidden) return VMC_EINVAL;
+  CK(ensure_init(c));
+  CK(upload_sysdesc(c));
+  const int prec = c->precision == VMC_FP64 ? 0 : 1;
+  const int grid = vmc_corr_grid(prec, c->smem_sample, s.W, s.Ns);
+  const size_t ns2 = (size_t)s.Ns * s.Ns;
+  const size_t part_b = (size_t)grid * 3 * ns2 * sizeof(double);
+  const size_t cnt_b = (4 * ns2 * sizeof(int) + 255) / 256 * 256;
+  const size_t out_b = 6 * ns2 * sizeof(double);
+  const size_t need = part_b + cnt_b + out_b;
+  if (c->corr_bytes < need) {
+    if (c->corr_buf) cudaFree(c->corr_buf);
+    c->corr_buf = nullptr;
+    c->corr_bytes = 0;
+    if (cudaMalloc(&c->corr_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      c->corr_buf = nullptr;
+      return VMC_ENOMEM;
+    }
+    c->corr_bytes = need;
+  }
+  double *part = (double *)c->corr_buf;
+  int *cnt = (int *)((unsigned char *)c->corr_buf + part_b);
+  double *out = (double *)((unsigned char *)c->corr_buf + part_b + cnt_b);
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (ms)
+    for (auto &e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        for (auto &f : ev)
+          if (f) cudaEventDestroy(f);
+        return VMC_ECUDA;
+      }
+  int rc = VMC_OK;
+  if ((ms && cudaEventRecord(ev[0], c->st)) || cudaMemsetAsync(part, 0, part_b, c->st) ||
+      vmc_launch_corr_occ(c->d_sys, system, s.Ns, cnt, c->st, &c->n_launch) ||
+      (ms && cudaEventRecord(ev[1], c->st)) ||
+      vmc_launch_corr(c->d_sys, system, prec, grid, part, c->smem_sample, c->st, &c->n_launch) ||
+      (ms && cudaEventRecord(ev[2], c->st)) ||
+      vmc_launch_corr_reduce(part, grid, cnt, s.Ns, s.W, out, c->st, &c->n_launch) ||
+      (ms && cudaEventRecord(ev[3], c->st)) ||
+      cudaMemcpyAsync(corr, out, out_b, cudaMemcpyDeviceToHost, c->st) ||
+      cudaStreamSynchronize(c->st))
+    rc = VMC_ECUDA;
+  if (ms && rc == VMC_OK) {
+    float t1 = 0.f, t2 = 0.f;
+    cudaEventElapsedTime(&t1, ev[1], ev[2]);
+    cudaEventElapsedTime(&t2, ev[0], ev[3]);
+    ms[0] = t1;
+    ms[1] = t2;
+  }
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
 }
 
 int64_t vmc_kernel_launches(vmc_ctx *c) { return c ? c->n_launch : -1; }

@@ -111,6 +111,18 @@ cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker,
                                    int precision, int n_moves, const int *d_moves,
                                    double *d_out, size_t smem, cudaStream_t st,
                                    long long *n_launch);
+// Pair correlations (measurement mode): CTA count of k_corr (occupancy x SMs,
+// at most W, and at most VMC_CORR_PART_BYTES of per-CTA FP64 planes
+// [grid][3][Ns][Ns]), the ratio kernel, the occupation-count kernel
+// (int [4][Ns][Ns]) and the reduction into double [6][Ns][Ns].
+#define VMC_CORR_PART_BYTES ((size_t)512 << 20)
+int vmc_corr_grid(int precision, size_t smem, int W, int Ns);
+cudaError_t vmc_launch_corr(const SysDev *d_sys, int sys, int precision, int grid,
+                            double *part, size_t smem, cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_corr_occ(const SysDev *d_sys, int sys, int Ns, int *cnt,
+                                cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_corr_reduce(const double *part, int n_part, const int *cnt, int Ns,
+                                   int W, double *out, cudaStream_t st, long long *n_launch);
 size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len);
 size_t vmc_init_smem(int N, int Ns);
 int vmc_sample_occupancy(int precision, size_t smem);

@@ -1,6 +1,7 @@
 // Walker kernels: parameter expansion, from-scratch inverse (FP64 Gauss-Jordan),
-// the Metropolis sweep with fast Pfaffian-ratio updates, and the per-sample
-// measurement of E_loc and the O_k row.
+// the Metropolis sweep with fast Pfaffian-ratio updates, the per-sample
+// measurement of E_loc and the O_k row, and the pair correlations of the
+// measurement mode.
 //
 // Wave function (mVMC paper, Sec. 3.2): psi(x) = P_G P_J <x|phi_AP-Pf>.  For
 // S^z = 0 and the anti-parallel form (Eq. AP-Pf) the Ne x Ne skew matrix X of
@@ -1609,6 +1610,162 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pair correlations of the current configurations (measurement mode,
+// Sec. 2.2.3; local estimators of Eq. MC, A acting on the ket |x>).
+//
+// Off-diagonal kinds, per walker, from Green-function ratios of its M^-1 = B:
+//   G_up[b, k] = sum_l f(b, r_l,dn) B_lk      (up electron k hops to b)
+//   G_dn[a, m] = sum_k f(r_k,up, a) B_mk      (down electron m hops to a)
+//   T[b, a]    = sum_k G_up[b, k] f(r_k,up, a)
+// and, for the spin swap of up electron n on a with down electron m on b
+// (both sites singly occupied; det of M with row n and column m replaced),
+//   det M'/det M = G_up[b, n] G_dn[a, m] - B_mn (T[b, a] - f(b, a)).
+// One pass over the sites b: G_up[b, :] (N^2), then for the down electron on
+// b (if any) G_dn[:, m] and T[b, :] together (2 N Ns): Ns N^2 + 2 N_dn N Ns
+// per configuration for all Ns^2 pairs.
+//   kind 0 (c^dag_{b up} c_{j up}): up electron on j hops to b,
+//          G_up[b, k] x P_G P_J ratio;
+//   kind 1 (c^dag_{a dn} c_{b dn}): down electron on b hops to a,
+//          G_dn[a, m] x P_G P_J ratio;
+//   kind 4 (S^+_b S^-_a): the swap above, with the fermion sign -1 of
+//          S^+S^- in the labelled basis (P_G, P_J unchanged).
+// Each CTA takes walkers blockIdx.x, blockIdx.x + gridDim.x, ... in turn and
+// adds their values (FP64) to its own plane triple part[blockIdx.x][3][Ns][Ns]
+// (diagonal entries stay 0), so the walker sums are in a fixed order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, double *part) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ SysDev S;
+  load_sys(&S, systems + sys);
+  const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
+  WSmem<T> sm;
+  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, smem_raw, &sm);
+  T *fb = sm.vec;                    // f(b, r_l,dn), l < N
+  T *gu = sm.vec + VMC_MAX_N;        // G_up[b, k], k < N
+  const T *F = ftab<T>(S);
+  const size_t ns2 = (size_t)Ns * Ns;
+  double *P0 = part + (size_t)blockIdx.x * 3 * ns2;
+  double *P1 = P0 + ns2;
+  double *P4 = P1 + ns2;
+  const size_t nb = minv_bytes(N, ldm, sizeof(T));
+  for (int w = blockIdx.x; w < S.W; w += gridDim.x) {
+    const T *src = (const T *)((const unsigned char *)S.minv + (size_t)w * nb);
+    for (int k = tid; k < N * ldm; k += NT) sm.minv[k] = src[k];
+    for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
+    for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
+    for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
+    __syncthreads();
+    for (int b = 0; b < Ns; ++b) {
+      if (tid < N) fb[tid] = F[(size_t)b * Ns + sm.ele[N + tid]];
+      __syncthreads();
+      if (tid < N) {
+        T s = (T)0;
+        for (int l = 0; l < N; ++l) s += fb[l] * sm.minv[l * ldm + tid];
+        gu[tid] = s;
+      }
+      __syncthreads();
+      const bool b_up = sm.occ[b] >= 0, b_dn = sm.occ[Ns + b] >= 0;
+      // kind 0 at (b, r_k,up)
+      if (tid < N && !b_up && !(S.local_spin && b_dn)) {
+        const int j = sm.ele[tid];
+        const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 0, j, b));
+        P0[(size_t)b * Ns + j] += (double)(gu[tid] * c);
+      }
+      if (b_dn) {
+        const int m = sm.occ[Ns + b] - N;
+        const T *Bm = sm.minv + (size_t)m * ldm;
+        for (int a = tid; a < Ns; a += NT) {
+          T accD = (T)0, accT = (T)0;
+#pragma unroll 4
+          for (int k = 0; k < N; ++k) {
+            const T fk = F[(size_t)sm.ele[k] * Ns + a];
+            accD += Bm[k] * fk;
+            accT += gu[k] * fk;
+          }
+          if (a == b) continue;
+          const bool a_up = sm.occ[a] >= 0, a_dn = sm.occ[Ns + a] >= 0;
+          // kind 1 at (a, b)
+          if (!a_dn && !(S.local_spin && a_up)) {
+            const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, b, a));
+            P1[(size_t)a * Ns + b] += (double)(accD * c);
+          }
+          // kind 4 at (b, a)
+          if (a_up && !a_dn && !b_up) {
+            const int n = sm.occ[a];
+            const T r = gu[n] * accD - Bm[n] * (accT - F[(size_t)b * Ns + a]);
+            P4[(size_t)b * Ns + a] -= (double)r;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Occupation products summed over the walkers of one system, exactly in
+// integers: cnt[c][i][j] = sum_w x_i y_j with (x, y) = (n_up, n_up),
+// (n_up, n_dn), (n_dn, n_up), (n_dn, n_dn) for c = 0..3.  These give every
+// diagonal estimator (n_i n_j, S^z_i S^z_j and the i = j terms of kinds 0, 1,
+// 4, 5).  One thread per (i, j) of a 16 x 16 tile.
+__global__ void k_corr_occ(const SysDev *systems, int sys, int *cnt) {
+  const SysDev &S = systems[sys];
+  const int Ns = S.Ns;
+  const int i = blockIdx.y * 16 + threadIdx.y, j = blockIdx.x * 16 + threadIdx.x;
+  if (i >= Ns || j >= Ns) return;
+  int uu = 0, ud = 0, du = 0, dd = 0;
+  for (int w = 0; w < S.W; ++w) {
+    const int *o = S.occ + (size_t)w * 2 * Ns;
+    const int ui = o[i] >= 0, di = o[Ns + i] >= 0, uj = o[j] >= 0, dj = o[Ns + j] >= 0;
+    uu += ui & uj;
+    ud += ui & dj;
+    du += di & uj;
+    dd += di & dj;
+  }
+  const size_t ns2 = (size_t)Ns * Ns, q = (size_t)i * Ns + j;
+  cnt[q] = uu;
+  cnt[ns2 + q] = ud;
+  cnt[2 * ns2 + q] = du;
+  cnt[3 * ns2 + q] = dd;
+}
+
+// out[kind][i][j] = walker mean of the local estimators (kinds 0..5 of the
+// header): the CTA planes summed in CTA order, the integer counts scaled.
+__global__ void k_corr_reduce(const double *part, int n_part, const int *cnt, int Ns, int W,
+                              double *out) {
+  const size_t ns2 = (size_t)Ns * Ns;
+  const double inv = 1.0 / (double)W;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns2;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(q / Ns), j = (int)(q % Ns);
+    const size_t qt = (size_t)j * Ns + i;
+    double g0 = 0.0, g1 = 0.0, s4 = 0.0, s4t = 0.0;
+    for (int b = 0; b < n_part; ++b) {
+      const double *P = part + (size_t)b * 3 * ns2;
+      g0 += P[q];
+      g1 += P[ns2 + q];
+      s4 += P[2 * ns2 + q];
+      s4t += P[2 * ns2 + qt];
+    }
+    const double uu = cnt[q], ud = cnt[ns2 + q], du = cnt[2 * ns2 + q], dd = cnt[3 * ns2 + q];
+    const double szsz = 0.25 * (uu - ud - du + dd);
+    double d0 = 0.0, d1 = 0.0, d4 = 0.0, d5 = 0.0;
+    if (i == j) {   // n_up, n_dn, n_up (1 - n_dn), (n_up + n_dn - 2 n_up n_dn) / 2
+      d0 = uu;
+      d1 = dd;
+      d4 = uu - ud;
+      d5 = 0.5 * (uu - ud + dd - du);
+    }
+    out[q] = (g0 + d0) * inv;
+    out[ns2 + q] = (g1 + d1) * inv;
+    out[2 * ns2 + q] = (uu + ud + du + dd) * inv;
+    out[3 * ns2 + q] = szsz * inv;
+    out[4 * ns2 + q] = (s4 + d4) * inv;
+    out[5 * ns2 + q] = (szsz + 0.5 * (s4 + s4t) + d5) * inv;
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1641,6 +1798,8 @@ cudaError_t vmc_walker_set_smem_limits(size_t s64, size_t s32, size_t sinit) {
   if ((e = cudaFuncSetAttribute(k_eval_ratios<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
   if ((e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
   if ((e = cudaFuncSetAttribute(k_eval_ratios<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+  if ((e = cudaFuncSetAttribute(k_corr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
+  if ((e = cudaFuncSetAttribute(k_corr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
   if ((e = cudaFuncSetAttribute(k_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sinit))) return e;
   if ((e = cudaFuncSetAttribute(k_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sinit))) return e;
   return cudaSuccess;
@@ -1711,6 +1870,52 @@ cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker, int
     k_eval_ratios<double><<<1, NT, smem, st>>>(d_sys, sys, walker, n_moves, d_moves, d_out);
   else
     k_eval_ratios<float><<<1, NT, smem, st>>>(d_sys, sys, walker, n_moves, d_moves, d_out);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+int vmc_corr_grid(int precision, size_t smem, int W, int Ns) {
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (precision == 0)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_corr<double>, NT, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_corr<float>, NT, smem);
+  if (per < 1) per = 1;
+  long long grid = (long long)nsm * per;
+  const size_t planes = (size_t)3 * Ns * Ns * sizeof(double);
+  const long long cap = (long long)(VMC_CORR_PART_BYTES / planes);
+  if (grid > cap) grid = cap;
+  if (grid > W) grid = W;
+  if (grid < 1) grid = 1;
+  return (int)grid;
+}
+
+cudaError_t vmc_launch_corr(const SysDev *d_sys, int sys, int precision, int grid, double *part,
+                            size_t smem, cudaStream_t st, long long *nl) {
+  if (precision == 0)
+    k_corr<double><<<grid, NT, smem, st>>>(d_sys, sys, part);
+  else
+    k_corr<float><<<grid, NT, smem, st>>>(d_sys, sys, part);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_launch_corr_occ(const SysDev *d_sys, int sys, int Ns, int *cnt, cudaStream_t st,
+                                long long *nl) {
+  const dim3 blk(16, 16), grd((Ns + 15) / 16, (Ns + 15) / 16);
+  k_corr_occ<<<grd, blk, 0, st>>>(d_sys, sys, cnt);
+  ++*nl;
+  return cudaGetLastError();
+}
+
+cudaError_t vmc_launch_corr_reduce(const double *part, int n_part, const int *cnt, int Ns, int W,
+                                   double *out, cudaStream_t st, long long *nl) {
+  const size_t ns2 = (size_t)Ns * Ns;
+  const size_t blocks = (ns2 + 255) / 256;
+  const int grid = (int)(blocks < 4096 ? blocks : 4096);
+  k_corr_reduce<<<grid, 256, 0, st>>>(part, n_part, cnt, Ns, W, out);
   ++*nl;
   return cudaGetLastError();
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libvmc.so")
 FP64, MIXED = 0, 1
 FORCE_STATIC_MAX_DOUBLES = 1 << 20
 CHOLESKY, CG, CG_DENSE, MIXED_IR = 0, 1, 2, 3
+CORR_KINDS = ("cdag_c_up", "cdag_c_dn", "n_n", "sz_sz", "sp_sm", "s_s")
 _I32P = C.POINTER(C.c_int32)
 _F64P = C.POINTER(C.c_double)
 _I8P = C.POINTER(C.c_int8)
@@ -78,7 +79,7 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_sr_step", "vmc_get_sr_matrices", "vmc_get_params", "vmc_set_params",
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
            "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
-           "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all"]
+           "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all", "vmc_measure_corr"]
 
 
 def load(path: str = LIB_PATH):
@@ -103,6 +104,7 @@ def load(path: str = LIB_PATH):
     L.vmc_get_configs.argtypes = [P, C.c_int32, _I32P, _U64P]
     L.vmc_sample.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     L.vmc_measure.argtypes = [P, C.c_int32, C.POINTER(VmcStats)]
+    L.vmc_measure_corr.argtypes = [P, C.c_int32, _F64P, _F64P]
     L.vmc_get_samples.argtypes = [P, C.c_int32, _F64P, _F64P]
     L.vmc_set_samples.argtypes = [P, C.c_int32, C.c_int32, _F64P, _F64P]
     L.vmc_sr_step.argtypes = [P, C.c_int32, C.POINTER(VmcSrOpts), C.POINTER(VmcSrReport)]
@@ -237,6 +239,18 @@ class Context:
         s = VmcStats()
         _check(self._L.vmc_measure(self._h, system, C.byref(s)), "vmc_measure")
         return {k: getattr(s, k) for k, _ in VmcStats._fields_}
+
+    def measure_corr(self, system=0, timing=False):
+        """Pair correlations of the walkers' current configurations
+        (vmc_measure_corr): array [6, Ns, Ns] indexed [kind, i, j] (kinds
+        CORR_KINDS).  With timing=True also returns (ratio-kernel ms,
+        whole-measurement ms)."""
+        Ns = self.problems[system].Ns
+        out = np.zeros((6, Ns, Ns))
+        ms = np.zeros(2)
+        _check(self._L.vmc_measure_corr(self._h, system, _p(out, _F64P),
+                                        _p(ms, _F64P) if timing else None), "vmc_measure_corr")
+        return (out, (float(ms[0]), float(ms[1]))) if timing else out
 
     def num_params(self, system=0):
         n = self._L.vmc_num_params(self._h, system)
