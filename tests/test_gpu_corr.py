@@ -132,8 +132,9 @@ def test_corr_rejects_mlp_context(vmc):
         with pytest.raises(vmc.VmcError) as e:
             ctx.measure_corr()
         assert e.value.code == -1
-        with pytest.raises(vmc.VmcError):
-            ctx.measure_corr(system=1)
+        # a system index the context does not have, at the C boundary
+        buf = np.zeros(6 * p.Ns * p.Ns)
+        assert ctx._L.vmc_measure_corr(ctx._h, 1, vmc._p(buf, vmc._F64P), None) == -1
 
 
 def _sampled_entries(cfg_pair, Ns, rng):
