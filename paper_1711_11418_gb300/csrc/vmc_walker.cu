@@ -1621,9 +1621,11 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
 // and, for the spin swap of up electron n on a with down electron m on b
 // (both sites singly occupied; det of M with row n and column m replaced),
 //   det M'/det M = G_up[b, n] G_dn[a, m] - B_mn (T[b, a] - f(b, a)).
-// One pass over the sites b: G_up[b, :] (N^2), then for the down electron on
-// b (if any) G_dn[:, m] and T[b, :] together (2 N Ns): Ns N^2 + 2 N_dn N Ns
-// per configuration for all Ns^2 pairs.
+// One pass over the sites b: G_up[b, :] (N^2); the down-occupied sites are
+// collected in groups of CORR_G, and for a group G_dn[:, m] and T[b, :] of
+// all its sites are formed together (2 N Ns each), so every gathered
+// f(r_k,up, a) serves 2 CORR_G products: Ns N^2 + 2 N_dn N Ns per
+// configuration for all Ns^2 pairs.
 //   kind 0 (c^dag_{b up} c_{j up}): up electron on j hops to b,
 //          G_up[b, k] x P_G P_J ratio;
 //   kind 1 (c^dag_{a dn} c_{b dn}): down electron on b hops to a,
@@ -1634,6 +1636,10 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
 // adds their values (FP64) to its own plane triple part[blockIdx.x][3][Ns][Ns]
 // (diagonal entries stay 0), so the walker sums are in a fixed order.
 // ---------------------------------------------------------------------------
+// Down-occupied sites whose second product is formed together (their G_up
+// rows wait in vector slots 1..CORR_G of shared memory).
+constexpr int CORR_G = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, double *part) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1642,8 +1648,7 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
   WSmem<T> sm;
   walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, smem_raw, &sm);
-  T *fb = sm.vec;                    // f(b, r_l,dn), l < N
-  T *gu = sm.vec + VMC_MAX_N;        // G_up[b, k], k < N
+  T *fb = sm.vec;                    // slot 0: f(b, r_l,dn), l < N
   const T *F = ftab<T>(S);
   const size_t ns2 = (size_t)Ns * Ns;
   double *P0 = part + (size_t)blockIdx.x * 3 * ns2;
@@ -1657,7 +1662,13 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
     for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
     for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
     __syncthreads();
+    // pending group: sites gb[q] with down electron gm[q], G_up row in slot 1 + q
+    int ng = 0;
+    int gb[CORR_G], gm[CORR_G];
+#pragma unroll
+    for (int q = 0; q < CORR_G; ++q) gb[q] = gm[q] = 0;
     for (int b = 0; b < Ns; ++b) {
+      T *gu = sm.vec + (size_t)(1 + ng) * VMC_MAX_N;   // G_up[b, k], k < N
       if (tid < N) fb[tid] = F[(size_t)b * Ns + sm.ele[N + tid]];
       __syncthreads();
       if (tid < N) {
@@ -1674,30 +1685,66 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
         P0[(size_t)b * Ns + j] += (double)(gu[tid] * c);
       }
       if (b_dn) {
-        const int m = sm.occ[Ns + b] - N;
-        const T *Bm = sm.minv + (size_t)m * ldm;
-        for (int a = tid; a < Ns; a += NT) {
-          T accD = (T)0, accT = (T)0;
-#pragma unroll 4
+#pragma unroll
+        for (int q = 0; q < CORR_G; ++q)
+          if (q == ng) {
+            gb[q] = b;
+            gm[q] = sm.occ[Ns + b] - N;
+          }
+        ++ng;
+      }
+      if (ng == CORR_G || (b == Ns - 1 && ng > 0)) {
+        // G_dn[a, m] and T[b, a] of the group's sites, two sites a per
+        // thread: each f(r_k,up, a) feeds 2 x CORR_G pairs of products.
+        const T *Bq[CORR_G], *Gq[CORR_G];
+#pragma unroll
+        for (int q = 0; q < CORR_G; ++q) {
+          Bq[q] = sm.minv + (size_t)gm[q] * ldm;       // unused slots: a valid row
+          Gq[q] = sm.vec + (size_t)(1 + q) * VMC_MAX_N;
+        }
+        for (int a0 = tid; a0 < Ns; a0 += 2 * NT) {
+          const int a1 = a0 + NT < Ns ? a0 + NT : a0;
+          T d0[CORR_G], t0[CORR_G], d1[CORR_G], t1[CORR_G];
+#pragma unroll
+          for (int q = 0; q < CORR_G; ++q) d0[q] = t0[q] = d1[q] = t1[q] = (T)0;
           for (int k = 0; k < N; ++k) {
-            const T fk = F[(size_t)sm.ele[k] * Ns + a];
-            accD += Bm[k] * fk;
-            accT += gu[k] * fk;
+            const T *Fk = F + (size_t)sm.ele[k] * Ns;
+            const T f0 = Fk[a0], f1 = Fk[a1];
+#pragma unroll
+            for (int q = 0; q < CORR_G; ++q) {
+              const T bk = Bq[q][k], gk = Gq[q][k];
+              d0[q] += bk * f0;
+              t0[q] += gk * f0;
+              d1[q] += bk * f1;
+              t1[q] += gk * f1;
+            }
           }
-          if (a == b) continue;
-          const bool a_up = sm.occ[a] >= 0, a_dn = sm.occ[Ns + a] >= 0;
-          // kind 1 at (a, b)
-          if (!a_dn && !(S.local_spin && a_up)) {
-            const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, b, a));
-            P1[(size_t)a * Ns + b] += (double)(accD * c);
-          }
-          // kind 4 at (b, a)
-          if (a_up && !a_dn && !b_up) {
-            const int n = sm.occ[a];
-            const T r = gu[n] * accD - Bm[n] * (accT - F[(size_t)b * Ns + a]);
-            P4[(size_t)b * Ns + a] -= (double)r;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int a = h ? a1 : a0;
+            if (h && a1 == a0) break;
+            const bool a_up = sm.occ[a] >= 0, a_dn = sm.occ[Ns + a] >= 0;
+#pragma unroll
+            for (int q = 0; q < CORR_G; ++q) {
+              if (q >= ng) break;
+              const int bq = gb[q];
+              if (a == bq) continue;
+              const T accD = h ? d1[q] : d0[q], accT = h ? t1[q] : t0[q];
+              // kind 1 at (a, bq): down electron gm[q] hops bq -> a
+              if (!a_dn && !(S.local_spin && a_up)) {
+                const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, bq, a));
+                P1[(size_t)a * Ns + bq] += (double)(accD * c);
+              }
+              // kind 4 at (bq, a): spin swap with up electron n on a
+              if (a_up && !a_dn && sm.occ[bq] < 0) {
+                const int n = sm.occ[a];
+                const T r = Gq[q][n] * accD - Bq[q][n] * (accT - F[(size_t)bq * Ns + a]);
+                P4[(size_t)bq * Ns + a] -= (double)r;
+              }
+            }
           }
         }
+        ng = 0;
       }
       __syncthreads();
     }
