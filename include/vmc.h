@@ -209,13 +209,13 @@ int vmc_measure(vmc_ctx *ctx, int32_t system, vmc_stats *out);
  * density and nearest-neighbour spin correlation of Sec. 4.1.1 follow from
  * these matrices.  Hops and spin swaps are evaluated from the walker's
  * M^-1 in the context's precision (FP64, or FP32 in the mixed form), the
- * diagonal kinds are exact; the walker means are FP64.
+ * diagonal kinds are exact; the walker means are FP64 (summed by atomic
+ * adds, so their last bit may differ between calls).
  * corr: host [6 * Ns * Ns], layout [kind][i][j] row-major.  ms: NULL or
  * host [2]: the device milliseconds of the ratio kernel and of the whole
  * measurement (CUDA events on the context's stream).  Rebuilds walker
  * inverses first if parameters or configurations changed.  Device scratch
- * (at most 512 MiB of per-CTA partial sums plus 56 Ns^2 bytes) is kept by
- * the context.  Errors: VMC_EINVAL (bad system, NULL corr, or a context
+ * (88 Ns^2 bytes) is kept by the context.  Errors: VMC_EINVAL (bad system, NULL corr, or a context
  * with the MLP factor, which this measurement does not evaluate),
  * VMC_ESINGULAR, VMC_ENOMEM, VMC_ECUDA. */
 int vmc_measure_corr(vmc_ctx *ctx, int32_t system, double *corr, double *ms);

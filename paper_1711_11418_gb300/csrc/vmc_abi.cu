@@ -1191,7 +1191,7 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
   const int prec = c->precision == VMC_FP64 ? 0 : 1;
   const int grid = vmc_corr_grid(prec, c->smem_sample, s.W, s.Ns);
   const size_t ns2 = (size_t)s.Ns * s.Ns;
-  const size_t part_b = (size_t)grid * 3 * ns2 * sizeof(double);
+  const size_t part_b = 3 * ns2 * sizeof(double);
   const size_t cnt_b = (4 * ns2 * sizeof(int) + 255) / 256 * 256;
   const size_t out_b = 6 * ns2 * sizeof(double);
   const size_t need = part_b + cnt_b + out_b;
@@ -1223,7 +1223,7 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
       (ms && cudaEventRecord(ev[1], c->st)) ||
       vmc_launch_corr(c->d_sys, system, prec, grid, part, c->smem_sample, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[2], c->st)) ||
-      vmc_launch_corr_reduce(part, grid, cnt, s.Ns, s.W, out, c->st, &c->n_launch) ||
+      vmc_launch_corr_reduce(part, 1, cnt, s.Ns, s.W, out, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[3], c->st)) ||
       cudaMemcpyAsync(corr, out, out_b, cudaMemcpyDeviceToHost, c->st) ||
       cudaStreamSynchronize(c->st))

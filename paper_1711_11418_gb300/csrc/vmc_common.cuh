@@ -112,10 +112,9 @@ cudaError_t vmc_launch_eval_ratios(const SysDev *d_sys, int sys, int walker,
                                    double *d_out, size_t smem, cudaStream_t st,
                                    long long *n_launch);
 // Pair correlations (measurement mode): CTA count of k_corr (occupancy x SMs,
-// at most W, and at most VMC_CORR_PART_BYTES of per-CTA FP64 planes
-// [grid][3][Ns][Ns]), the ratio kernel, the occupation-count kernel
-// (int [4][Ns][Ns]) and the reduction into double [6][Ns][Ns].
-#define VMC_CORR_PART_BYTES ((size_t)512 << 20)
+// at most W), the ratio kernel (adds into FP64 planes [3][Ns][Ns]), the
+// occupation-count kernel (int [4][Ns][Ns]) and the reduction into
+// double [6][Ns][Ns].
 int vmc_corr_grid(int precision, size_t smem, int W, int Ns);
 cudaError_t vmc_launch_corr(const SysDev *d_sys, int sys, int precision, int grid,
                             double *part, size_t smem, cudaStream_t st, long long *n_launch);

@@ -1633,8 +1633,10 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
 //   kind 4 (S^+_b S^-_a): the swap above, with the fermion sign -1 of
 //          S^+S^- in the labelled basis (P_G, P_J unchanged).
 // Each CTA takes walkers blockIdx.x, blockIdx.x + gridDim.x, ... in turn and
-// adds their values (FP64) to its own plane triple part[blockIdx.x][3][Ns][Ns]
-// (diagonal entries stay 0), so the walker sums are in a fixed order.
+// adds their values to one FP64 plane triple part[3][Ns][Ns] (diagonal
+// entries stay 0) by atomic adds without return, so the 24 Ns^2 bytes stay
+// in L2 and no thread waits on them; the order of the additions, and so the
+// last bit of a sum, varies between runs.
 // ---------------------------------------------------------------------------
 // Down-occupied sites whose second product is formed together (their G_up
 // rows wait in vector slots 1..CORR_G of shared memory).
@@ -1651,7 +1653,7 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
   T *fb = sm.vec;                    // slot 0: f(b, r_l,dn), l < N
   const T *F = ftab<T>(S);
   const size_t ns2 = (size_t)Ns * Ns;
-  double *P0 = part + (size_t)blockIdx.x * 3 * ns2;
+  double *P0 = part;
   double *P1 = P0 + ns2;
   double *P4 = P1 + ns2;
   const size_t nb = minv_bytes(N, ldm, sizeof(T));
@@ -1682,7 +1684,7 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
       if (tid < N && !b_up && !(S.local_spin && b_dn)) {
         const int j = sm.ele[tid];
         const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 0, j, b));
-        P0[(size_t)b * Ns + j] += (double)(gu[tid] * c);
+        atomicAdd(&P0[(size_t)b * Ns + j], (double)(gu[tid] * c));
       }
       if (b_dn) {
 #pragma unroll
@@ -1733,13 +1735,13 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
               // kind 1 at (a, bq): down electron gm[q] hops bq -> a
               if (!a_dn && !(S.local_spin && a_up)) {
                 const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, bq, a));
-                P1[(size_t)a * Ns + bq] += (double)(accD * c);
+                atomicAdd(&P1[(size_t)a * Ns + bq], (double)(accD * c));
               }
               // kind 4 at (bq, a): spin swap with up electron n on a
               if (a_up && !a_dn && sm.occ[bq] < 0) {
                 const int n = sm.occ[a];
                 const T r = Gq[q][n] * accD - Bq[q][n] * (accT - F[(size_t)bq * Ns + a]);
-                P4[(size_t)bq * Ns + a] -= (double)r;
+                atomicAdd(&P4[(size_t)bq * Ns + a], -(double)r);
               }
             }
           }
@@ -1778,7 +1780,8 @@ __global__ void k_corr_occ(const SysDev *systems, int sys, int *cnt) {
 }
 
 // out[kind][i][j] = walker mean of the local estimators (kinds 0..5 of the
-// header): the CTA planes summed in CTA order, the integer counts scaled.
+// header): the ratio planes (n_part sets, summed in order) and the integer
+// counts, scaled.
 __global__ void k_corr_reduce(const double *part, int n_part, const int *cnt, int Ns, int W,
                               double *out) {
   const size_t ns2 = (size_t)Ns * Ns;
@@ -1931,9 +1934,6 @@ int vmc_corr_grid(int precision, size_t smem, int W, int Ns) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_corr<float>, NT, smem);
   if (per < 1) per = 1;
   long long grid = (long long)nsm * per;
-  const size_t planes = (size_t)3 * Ns * Ns * sizeof(double);
-  const long long cap = (long long)(VMC_CORR_PART_BYTES / planes);
-  if (grid > cap) grid = cap;
   if (grid > W) grid = W;
   if (grid < 1) grid = 1;
   return (int)grid;
