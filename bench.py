@@ -43,6 +43,9 @@ FP64_PEAK_TFLOPS = SMS * FP64_UNITS * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # profiles/k_init_float_hubbard16x16_w4096.md); proportional to walkers.
 TRAFFIC_SWEEP_4096 = 225.731328e6 + 181.081344e6
 TRAFFIC_INIT_4096 = 6.181120e6 + 160.923392e6
+# k_corr<float> (pair correlations), DRAM read + write per launch at 4096
+# walkers (profiles/k_corr_float_hubbard16x16_w4096.md).
+TRAFFIC_CORR_4096 = 229.7047e6
 
 
 def hbm_peak_gbs():
@@ -469,7 +472,8 @@ def run_ours(args):
             "ms_per_measurement": corr["all_ms"],
             "configurations_per_s": args.walkers / (corr["all_ms"] * 1e-3),
             "roofline": {"bound": "alu", "achieved": ach_c, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": ach_c / FP32_PEAK_TFLOPS, "traffic": None,
+                         "unit": "TFLOP/s", "frac": ach_c / FP32_PEAK_TFLOPS,
+                         "traffic": TRAFFIC_CORR_4096 * scale,
                          "kernel": "k_corr<float>", "ms_per_launch": corr["k_ms"],
                          "flops_per_launch": fl,
                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}}
