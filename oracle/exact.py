@@ -9,7 +9,7 @@ from .hamiltonian import basis, local_energy
 
 def enumerate_expectations(wf):
     N = wf.Ne // 2
-    states = basis(wf.Ns, N, N, wf.local_spin)
+    states = basis(wf.Ns, N, N, wf.local_spin, wf.local_sites)
     amps = np.array([wf.amplitude(n) for n in states])
     w = amps ** 2
     keep = w > 0

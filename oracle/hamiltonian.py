@@ -69,8 +69,11 @@ def local_energy(wf, n):
     return float(e)
 
 
-def basis(Ns, N_up, N_dn, local_spin=False):
-    """All S^z-fixed configurations as bitmasks (no doublons if local_spin)."""
+def basis(Ns, N_up, N_dn, local_spin=False, local_sites=None):
+    """All S^z-fixed configurations as bitmasks (no doublons if local_spin;
+    exactly one electron on each site of the local_sites mask)."""
+    if local_sites is not None:
+        return _basis_local_sites(Ns, N_up, N_dn, np.asarray(local_sites, bool))
     out = []
     for ups in combinations(range(Ns), N_up):
         mu = sum(1 << i for i in ups)
@@ -81,6 +84,24 @@ def basis(Ns, N_up, N_dn, local_spin=False):
             if local_spin and set(ups) & set(dns):
                 continue
             out.append(mu | sum(1 << (Ns + i) for i in dns))
+    return out
+
+
+def _basis_local_sites(Ns, N_up, N_dn, mask):
+    loc = [i for i in range(Ns) if mask[i]]
+    itin = [i for i in range(Ns) if not mask[i]]
+    out = []
+    for k in range(len(loc) + 1):            # up spins among the local sites
+        cu, cd = N_up - k, N_dn - (len(loc) - k)
+        if not (0 <= cu <= len(itin) and 0 <= cd <= len(itin)):
+            continue
+        for lu in combinations(loc, k):
+            up_loc = set(lu)
+            base = sum(1 << i for i in lu) | sum(1 << (Ns + i) for i in loc if i not in up_loc)
+            for ups in combinations(itin, cu):
+                m1 = base | sum(1 << i for i in ups)
+                for dns in combinations(itin, cd):
+                    out.append(m1 | sum(1 << (Ns + i) for i in dns))
     return out
 
 
@@ -158,11 +179,11 @@ def hamiltonian_matrix_vec(prob, states):
                          shape=(nS, nS))
 
 
-def ground_state_energy(prob):
-    """Exact diagonalisation in the S^z = 0 sector (dense below 3000 states,
-    else Lanczos via scipy eigsh)."""
-    N = prob.Ne // 2
-    states = basis(prob.lat.Ns, N, N, prob.local_spin)
+def ground_state_energy(prob, two_sz=0):
+    """Exact diagonalisation in the sector 2 S^z = two_sz (dense below 3000
+    states, else Lanczos via scipy eigsh)."""
+    states = basis(prob.lat.Ns, (prob.Ne + two_sz) // 2, (prob.Ne - two_sz) // 2,
+                   prob.local_spin, getattr(prob, "local_sites", None))
     H = hamiltonian_matrix_vec(prob, states)
     if len(states) <= 3000:
         return float(np.linalg.eigvalsh(H.toarray())[0])

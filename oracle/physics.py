@@ -27,17 +27,18 @@ the diagonal kinds (2, 3) are read off the occupations.
 Structure factors (Sec. 2.4.2): X(k) = (1/N_cell) sum_{i,j} exp(-i k.(R_i - R_j))
 <X_i^dag X_j>; from the kinds above, n_sigma(k) from 0 / 1, N(k) from 2,
 S^z(k) from 3, S(k) from 5.  The quantities of the comparison with exact
-diagonalisation (Sec. 4.1.1): the doublon
-density D = (1/Ns) sum_i <n_i,up n_i,dn>, the nearest-neighbour spin
-correlation S_nn = (1/(4 Ns)) sum_{i, mu} <S_{r_i} . S_{r_i + e_mu}> and
-S~(k) = S(k) / (3 Ns).
+diagonalisation (Sec. 4.1.1, Sec. 4.2): the doublon density
+D = (1/Ns) sum_i <n_i,up n_i,dn>, the nearest-neighbour spin correlation
+S_nn (read as the mean of <S_i . S_j> over nearest-neighbour bonds: the
+printed (1/(4 Ns)) sum_{i, mu} on the square lattice, and what reproduces
+the printed exact value of the Kondo chain) and S~(k) = S(k) / (3 N_cell).
 """
 import math
 
 import numpy as np
 
 from .fock import apply_string
-from .hamiltonian import basis
+from .hamiltonian import _apply_string_vec, basis
 
 KINDS = ("cdag_c_up", "cdag_c_dn", "n_n", "sz_sz", "sp_sm", "s_s")
 
@@ -124,7 +125,7 @@ def exact_correlations(wf):
     """<psi|A|psi>/<psi|psi> for every kind and pair by enumeration of all
     S^z = 0 configurations, weighted by rho(x) (tiny systems only)."""
     N = wf.Ne // 2
-    states = basis(wf.Ns, N, N, wf.local_spin)
+    states = basis(wf.Ns, N, N, wf.local_spin, wf.local_sites)
     amps = np.array([wf.amplitude(n) for n in states])
     w = amps ** 2
     keep = np.nonzero(w > 0)[0]
@@ -143,14 +144,45 @@ def doublon_density(corr):
     return float(0.5 * d.sum() / Ns)
 
 
-def nn_spin_correlation(corr, bond_i, bond_j):
-    """S_nn = (1/(4 Ns)) sum over the 2 d nearest-neighbour vectors e_mu of
-    every site; with the bond list holding each undirected nearest-neighbour
-    bond once, every bond occurs twice in that sum (i -> j and j -> i)."""
-    Ns = corr.shape[-1]
-    ss = corr[5]
-    tot = sum(ss[i, j] + ss[j, i] for i, j in zip(bond_i, bond_j))
-    return float(tot / (4.0 * Ns))
+def nn_spin_correlation(ss, bond_i, bond_j):
+    """S_nn: the mean over the nearest-neighbour bonds (each undirected bond
+    listed once) of (<S_i . S_j> + <S_j . S_i>) / 2; ss is the [Ns, Ns]
+    matrix of <S_a . S_b> (kind 5)."""
+    tot = sum(0.5 * (ss[i, j] + ss[j, i]) for i, j in zip(bond_i, bond_j))
+    return float(tot / len(bond_i))
+
+
+def state_spin_matrix(Ns, states, vec):
+    """[Ns, Ns] matrix of <v| S_a . S_b |v> for a normalised state vector v
+    over the basis `states` (any order; exact diagonalisation checks):
+    S^z_a S^z_b from the occupations, (S^+_a S^-_b + S^-_a S^+_b)/2 by
+    applying the operator strings to every basis state; S_a . S_a =
+    3/4 (n_a - 2 n_a,up n_a,dn)."""
+    st = np.asarray(states, np.int64)
+    order = np.argsort(st)
+    sst = st[order]
+    p = np.abs(vec) ** 2
+    up = np.stack([(st >> i) & 1 for i in range(Ns)], axis=1).astype(np.float64)
+    dn = np.stack([(st >> (Ns + i)) & 1 for i in range(Ns)], axis=1).astype(np.float64)
+    sz = 0.5 * (up - dn)
+    ss = (sz * p[:, None]).T @ sz
+    single = p @ (up + dn - 2 * up * dn)
+
+    def overlap(ops):
+        new, sign, ok = _apply_string_vec(ops, st)
+        k = np.searchsorted(sst, new[ok])
+        kc = np.minimum(k, len(sst) - 1)
+        hit = sst[kc] == new[ok]
+        return float(np.sum(vec[order[kc[hit]]] * sign[ok][hit] * vec[ok][hit]))
+
+    for a in range(Ns):
+        ss[a, a] = 0.75 * single[a]
+        for b in range(a + 1, Ns):
+            t = 0.5 * (overlap([("+", a), ("-", Ns + a), ("+", Ns + b), ("-", b)]) +
+                       overlap([("+", Ns + a), ("-", a), ("+", b), ("-", Ns + b)]))
+            ss[a, b] += t
+            ss[b, a] += t
+    return ss
 
 
 def structure_factor(mat, R, k, n_cell=None):

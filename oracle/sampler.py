@@ -12,7 +12,9 @@ reading used throughout the project):
 * exchange iff r0 < floor(p_ex * 2^32); hop otherwise;
 * hop: electron e = mulhi(r1, Ne), target site = mulhi(r2, Ns); invalid
   (rejected, still counted) if the target already holds that spin, or any
-  electron under the local-spin constraint;
+  electron under the local-spin constraint, or if the electron leaves or
+  enters a site of the per-site constraint (Kondo local spins, Sec. 4.2:
+  they change only by exchange);
 * exchange: up electron n = mulhi(r1, N), down electron N + mulhi(r2, N);
   invalid unless the two sites differ, the up site holds no down electron
   and the down site no up electron;
@@ -93,6 +95,9 @@ class Chain:
             if self.occ[s][t] >= 0:
                 return False
             if self.wf.local_spin and self.occ[1 - s][t] >= 0:
+                return False
+            if self.wf.local_sites is not None and (self.wf.local_sites[t] or
+                                                    self.wf.local_sites[self.ele[e]]):
                 return False
             moves = [(e, t)]
         n_new = self._try(moves)

@@ -7,7 +7,9 @@ log-derivatives O_k(x) = d ln<x|psi> / d alpha_k.
 * Correlation factors (Sec. 3.2.3): P_G = exp(sum_i g_i n_i,up n_i,dn),
   P_J = exp(1/2 sum_{i != j} v_ij (n_i - 1)(n_j - 1)).  Under the
   local-spin constraint (g -> -infinity, Sec. 3.2.3) a doubly occupied site
-  gives psi = 0.
+  gives psi = 0.  With a per-site constraint (local spins of the Kondo
+  lattice, Sec. 4.2: double occupancy excluded on those sites) psi = 0
+  unless each marked site holds exactly one electron.
 * O_k (Sec. 3.3.1): Gutzwiller O = D_k(x); Jastrow O = sum over the class
   of (n_i - 1)(n_j - 1) for i < j; pair orbital dPf/dF_AB = -Pf(X) (X^-1)_AB
   (Eq. DiffPf and Appendix C), summed over the class with the class sign.
@@ -34,6 +36,8 @@ class Wavefunction:
         self.Ne = int(prob.Ne)
         self.n_g, self.n_v, self.n_f = int(prob.n_g), int(prob.n_v), int(prob.n_f)
         self.local_spin = bool(prob.local_spin)
+        ls = getattr(prob, "local_sites", None)
+        self.local_sites = None if ls is None else np.asarray(ls, bool).reshape(Ns)
         gi = np.asarray(prob.g_idx).reshape(Ns)
         self.g_site = np.where(gi >= 0, p[np.maximum(gi, 0)], 0.0) if self.n_g else np.zeros(Ns)
         vi = np.asarray(prob.v_idx).reshape(Ns, Ns)
@@ -88,6 +92,8 @@ class Wavefunction:
         """(sign, log|<x|psi>|) including the (Ne/2)! factor."""
         up, dn = self.occ(n)
         if self.local_spin and np.any(up * dn):
+            return 0.0, -math.inf
+        if self.local_sites is not None and np.any((up + dn)[self.local_sites] != 1):
             return 0.0, -math.inf
         X, _ = self.X(n)
         s, l = pfaffian_slog(X)

@@ -309,6 +309,9 @@ class Problem:
     V_j: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
     V_val: np.ndarray = field(default_factory=lambda: np.zeros(0))
     meta: dict = field(default_factory=dict)
+    # per-site local-spin constraint (exactly one electron on each marked
+    # site); None = none, or all sites when local_spin is set
+    local_sites: np.ndarray | None = None
 
     @property
     def Ns(self) -> int:
@@ -437,6 +440,35 @@ def heisenberg_square(L=4, noise=0.05, seed=0, sub=(2, 2)):
     return make_problem(f"heis_{L}x{L}", square(L, L, 1, -1), L * L, t=0.0,
                         J1=1.0, local_spin=True, sub=sub, gutzwiller=False,
                         noise=noise, seed=seed)
+
+
+def kondo_chain(L=8, t=1.0, J=1.0, bc=1, noise=0.3, seed=0):
+    """One-dimensional Kondo lattice: L conduction sites 0..L-1 on a ring
+    (hopping t, boundary sign bc on the wrap-around bond) and L local spins
+    L..2L-1, local spin L+i coupled to conduction site i by J S.s; Ne = 2L
+    (half-filled conduction band).  Local sites carry the per-site
+    local-spin constraint; full f with seeded U(-noise, noise) entries,
+    Gutzwiller factor on the conduction sites, no Jastrow factor."""
+    Ns = 2 * L
+    hop_i, hop_j, hop_t = [], [], []
+    for i in range(L):
+        j = (i + 1) % L
+        tij = t * (bc if j < i else 1.0)
+        hop_i += [i, j]
+        hop_j += [j, i]
+        hop_t += [tij, tij]
+    f_idx, f_sign, n_f = full_f_layout(Ns)
+    g_idx = np.where(np.arange(Ns) < L, 0, -1).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    params = np.concatenate([[0.0], rng.uniform(-noise, noise, n_f) + 0.5 * np.eye(Ns).reshape(-1)])
+    return Problem(name=f"kondo_{L}", lat=Lattice(Ns, 1), Ne=Ns,
+                   hop_i=np.array(hop_i, np.int32), hop_j=np.array(hop_j, np.int32),
+                   hop_t=np.array(hop_t, np.float64), U=np.zeros(Ns),
+                   ex_i=np.arange(L, dtype=np.int32), ex_j=np.arange(L, Ns, dtype=np.int32),
+                   ex_J=np.full(L, float(J)), local_spin=False, g_idx=g_idx, n_g=1,
+                   v_idx=np.full(Ns * Ns, -1, np.int32), n_v=0, f_idx=f_idx, f_sign=f_sign,
+                   n_f=n_f, params=params, p_exchange=0.5,
+                   local_sites=np.arange(Ns) >= L)
 
 
 def batched_hubbard(n_systems=64, seed=0, sizes=(4, 6, 8, 10, 12, 14, 16)):

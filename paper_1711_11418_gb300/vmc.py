@@ -170,6 +170,10 @@ class Context:
                  delay_k=0, recompute_every=0, stream=None):
         L = load()
         probs = problems if isinstance(problems, (list, tuple)) else [problems]
+        for pr in probs:
+            if getattr(pr, "local_sites", None) is not None and not pr.local_spin:
+                raise VmcError(-1, "vmc_create: per-site local-spin constraint (Kondo "
+                                   "lattice) is not supported by the library")
         self.problems = list(probs)
         self.n_walkers = int(n_walkers)
         self.precision = precision

@@ -34,3 +34,12 @@ def test_strerror_is_host_only():
     L = vmc.load(build.build())
     assert L.vmc_strerror(0) == b"ok"
     assert b"invalid" in L.vmc_strerror(-1)
+
+
+def test_context_rejects_per_site_local_spin():
+    """The CUDA path has no per-site local-spin constraint: a Kondo-lattice
+    problem is refused before any CUDA call."""
+    from paper_1711_11418_gb300 import build, inputs, vmc
+    vmc.load(build.build())
+    with pytest.raises(vmc.VmcError):
+        vmc.Context(inputs.kondo_chain(2), 2)

@@ -170,8 +170,7 @@ def test_local_estimators_act_on_the_ket_and_conserve_particles():
 
 def test_structure_factor_sum_rules():
     """k = 0: N(0) = Ne^2 / Ns for fixed particle number, S(0) = 0 for a
-    singlet; S_nn of the two-site singlet (one bond, Ns = 2) is
-    (2 x -3/4) / (4 x 2)."""
+    singlet; S_nn of the two-site singlet (one bond) is -3/4."""
     p = _correlated_chain(True)
     c = exact_correlations(Wavefunction(p))
     R = np.arange(p.Ns, dtype=np.float64)[:, None]
@@ -182,7 +181,7 @@ def test_structure_factor_sum_rules():
     tot = sum(structure_factor(c[5], R, [k]) for k in ks)
     assert tot == pytest.approx(float(np.trace(c[5])), abs=1e-11)
     c2 = exact_correlations(Wavefunction(_two_site(0.7, 0.7)))
-    assert nn_spin_correlation(c2, [0], [1]) == pytest.approx(2 * -0.75 / 8, abs=1e-14)
+    assert nn_spin_correlation(c2[5], [0], [1]) == pytest.approx(-0.75, abs=1e-14)
 
 
 def test_mean_over_configurations_is_the_average_of_local_values():
