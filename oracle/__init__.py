@@ -20,6 +20,8 @@ sr            SR matrices S, g and the solve: Cholesky or CG (Sec. 3.3.1-2,
 exact         Exact enumeration over all configurations (tiny systems).
 physics       Pair correlations by Eq. MC (measurement mode, Sec. 2.2.3) and the
               structure factors of Sec. 2.4.2.
+projection    Momentum and point-group projection of the pair-product part
+              (Sec. 3.2.2, Eqs. momP and pointP).
 
 Every function cites the passage it follows.  Pins against values the paper
 or mathematics fix live in ``tests/test_oracle_*.py``.
