@@ -22,6 +22,7 @@ physics       Pair correlations by Eq. MC (measurement mode, Sec. 2.2.3) and the
               structure factors of Sec. 2.4.2.
 projection    Momentum and point-group projection of the pair-product part
               (Sec. 3.2.2, Eqs. momP and pointP).
+lanczos       First-step power-Lanczos moments and alpha_1 (Sec. 3.4).
 
 Every function cites the passage it follows.  Pins against values the paper
 or mathematics fix live in ``tests/test_oracle_*.py``.
