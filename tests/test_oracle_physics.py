@@ -202,3 +202,37 @@ def test_single_entry_matches_dense():
     for kind in range(6):
         for i, j in ((0, 3), (2, 2), (5, 1)):
             assert local_correlation(wf, n, kind, i, j) == dense[kind, i, j]
+
+
+def test_spin_swap_closed_form():
+    """The identity the pair-correlation kernel uses for a spin swap (up
+    electron n on site a, down electron m on site b): with B = M^-1,
+    det M'/det M = G_up[b, n] G_dn[a, m] - B_mn (T[b, a] - f(b, a)), where
+    G_up[b, :] = f(b, r_dn) B, G_dn[a, m] = B[m, :] f(r_up, a) and
+    T[b, a] = G_up[b, :] f(r_up, a); against direct determinants."""
+    rng = np.random.default_rng(0)
+    Ns, N = 10, 4
+    f = rng.standard_normal((Ns, Ns))
+    checked = 0
+    for _ in range(300):
+        up = list(rng.permutation(Ns)[:N])
+        dn = list(rng.permutation(Ns)[:N])
+        M = f[np.ix_(up, dn)]
+        if abs(np.linalg.det(M)) < 1e-6:
+            continue
+        B = np.linalg.inv(M)
+        ns = [k for k in range(N) if up[k] not in dn]
+        ms = [k for k in range(N) if dn[k] not in up]
+        if not ns or not ms:
+            continue
+        n, m = ns[0], ms[0]
+        a, b = up[n], dn[m]
+        up2, dn2 = list(up), list(dn)
+        up2[n], dn2[m] = b, a
+        direct = np.linalg.det(f[np.ix_(up2, dn2)]) / np.linalg.det(M)
+        gu = f[b, dn] @ B
+        gd = B[m, :] @ f[up, a]
+        T = gu @ f[up, a]
+        assert gu[n] * gd - B[m, n] * (T - f[b, a]) == pytest.approx(direct, rel=1e-9, abs=1e-9)
+        checked += 1
+    assert checked > 100
