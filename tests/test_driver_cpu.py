@@ -82,3 +82,18 @@ def test_measure_physics_single_measurement_has_no_error():
     assert np.all(np.isnan(err))
     with pytest.raises(ValueError):
         driver.measure_physics(FakeContext(), 0)
+
+
+def test_stand_in_matches_the_binding():
+    """The driver calls Context methods by these names and keywords; the
+    stand-in above must accept what the real binding accepts."""
+    import inspect
+    from paper_1711_11418_gb300 import vmc
+    for name in ("sample", "measure", "sr_step", "measure_corr"):
+        real = inspect.signature(getattr(vmc.Context, name)).parameters
+        fake = inspect.signature(getattr(FakeContext, name)).parameters
+        for p in fake:
+            assert p in real, (name, p)
+        for p, spec in real.items():
+            if spec.default is inspect.Parameter.empty:
+                assert p in fake, (name, p)
