@@ -110,3 +110,23 @@ def test_kondo_local_sites_keep_one_electron():
     E = np.asarray(ref["E"])
     err = E.std() / math.sqrt(len(E) / 20.0)     # 20-sample blocks as a conservative error
     assert abs(E.mean() - ex["energy"]) < 4 * err + 1e-9
+
+
+def test_kondo_pair_correlations_respect_the_constraint():
+    """Exact pair correlations of a 2-cell Kondo chain (oracle.physics on
+    the constrained space): one electron on every local site, no hop into
+    or out of one, and the couplings of H contracted with the correlations
+    give the exact energy."""
+    from oracle.physics import exact_correlations
+    p = I.kondo_chain(2, noise=0.4, seed=5)
+    wf = Wavefunction(p)
+    c = exact_correlations(wf)
+    loc = np.flatnonzero(p.local_sites)
+    occ = np.diagonal(c[0]) + np.diagonal(c[1])
+    np.testing.assert_allclose(occ[loc], 1.0, atol=1e-13)
+    for s in (0, 1):
+        off = c[s] - np.diag(np.diagonal(c[s]))
+        assert np.all(off[loc, :] == 0.0) and np.all(off[:, loc] == 0.0)
+    e = sum(-t * (c[0, i, j] + c[1, i, j]) for i, j, t in zip(p.hop_i, p.hop_j, p.hop_t))
+    e += sum(J * c[5, i, j] for i, j, J in zip(p.ex_i, p.ex_j, p.ex_J))
+    assert e == pytest.approx(enumerate_expectations(wf)["energy"], rel=1e-11, abs=1e-12)
