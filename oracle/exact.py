@@ -5,6 +5,7 @@ matrices for the current parameters."""
 import numpy as np
 
 from .hamiltonian import basis, local_energy
+from .sr import sr_matrices
 
 
 def enumerate_expectations(wf):
@@ -17,10 +18,7 @@ def enumerate_expectations(wf):
     w = w[keep] / w[keep].sum()
     E = np.array([local_energy(wf, n) for n in states])
     O = np.array([wf.log_derivatives(n) for n in states])
-    energy = float(w @ E)
-    obar = w @ O
-    S = (O * w[:, None]).T @ O - np.outer(obar, obar)
-    g = (O * w[:, None]).T @ E - energy * obar
+    S, g, obar, energy = sr_matrices(E, O, w)
     var = float(w @ (E - energy) ** 2)
     return dict(energy=energy, variance=var, S=S, g=g, obar=obar,
                 states=states, weights=w, E=E, O=O)

@@ -13,14 +13,24 @@
 import numpy as np
 
 
-def sr_matrices(E, O):
+def sr_matrices(E, O, weights=None):
+    """S, g, <O>, <E> of Sec. 3.3.1 for real parameters.
+
+    <A> is the sample mean over the N_MC rows (Eq. MC), or, with `weights`
+    (one non-negative weight per row, normalised here), the weighted mean
+    sum_u w_u A_u: exact enumeration passes rho(x) = |psi(x)|^2 / <psi|psi>
+    and so obtains the exact S and g from this same function."""
     E = np.asarray(E, np.float64)
     O = np.asarray(O, np.float64)
-    nmc = E.size
-    obar = O.mean(axis=0)
-    ebar = E.mean()
-    S = (O.T @ O) / nmc - np.outer(obar, obar)
-    g = (O.T @ E) / nmc - ebar * obar
+    if weights is None:
+        w = np.full(E.size, 1.0 / E.size)
+    else:
+        w = np.asarray(weights, np.float64)
+        w = w / w.sum()
+    obar = w @ O
+    ebar = float(w @ E)
+    S = (O * w[:, None]).T @ O - np.outer(obar, obar)
+    g = (O * w[:, None]).T @ E - ebar * obar
     return S, g, obar, ebar
 
 
