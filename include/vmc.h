@@ -151,9 +151,20 @@ typedef struct {
   int32_t n_params;
   double rel_residual;           /* refinement: |g - S~ x| / |g| reached (else 0) */
   int32_t fallback;              /* refinement: 1 if the FP64 Cholesky solved instead */
+  int32_t s_kernel;              /* kernel that built the dense S~: VMC_S_KERNEL_* */
 } vmc_sr_report;
 
-/* Create a context for one system (Sec. 2.3-2.2 problem statement).
+/* vmc_sr_report.s_kernel: no dense S~ (SR-CG product); FP64 SIMT product
+ * (plain form); persistent TMA-fed tcgen05 kernel (mixed form); one CTA per
+ * tile tcgen05 kernel with cp.async staging (mixed form, used when the
+ * driver's tensor-map encoder is unavailable or VMC_TC_KERNEL=tiles is set). */
+enum { VMC_S_KERNEL_NONE = 0, VMC_S_KERNEL_FP64 = 1, VMC_S_KERNEL_TMA = 2,
+       VMC_S_KERNEL_TILES = 3 };
+
+/* Create a context for one system (the problem statement of Sec. 2.3: the
+ * Hamiltonian, and the variational wave function of Sec. 3.2).
+ * The sector is S^z = 0 (Ne/2 up and Ne/2 down electrons, the anti-parallel
+ * pair product of Eq. AP-Pf); there is no argument for another S^z.
  * params: initial parameter vector [n_g + n_v + n_f (+ MLP block)].  p_exchange: the
  * probability that a proposal is an exchange (Sec. 3.1.2); forced to 1 when
  * local_spin.  Walker configurations start from a seeded random placement;
@@ -339,12 +350,17 @@ int vmc_tune_delay(vmc_ctx *ctx, int32_t sweeps, const int32_t *cand, int32_t n_
  *    (nothing is launched); VMC_EINVAL also for NULL pointers, rows < 1,
  *    Np < 1 or ldO < Np.
  *  - The first call on a device looks up the array's device address (with
- *    that device current); make that first call before any stream capture.
+ *    that device current, under a lock, so host threads may race to it);
+ *    make that first call before any stream capture.  The address is kept
+ *    for the life of the process: do not call it on a device after
+ *    cudaDeviceReset() of that device.
  *  - Every call uses the same array.  Each call writes every scratch entry it
  *    reads, so no state carries over, but calls that overlap on the GPU (on
  *    different streams or host threads) race on it and must be serialised by
  *    the caller.
- * Errors: VMC_EINVAL as above, VMC_ECUDA if a CUDA call fails. */
+ * Errors: VMC_EINVAL as above; VMC_ECUDA if one of its launches fails, or,
+ * before anything is launched, if a launch error from the caller's earlier
+ * work is already pending (that error is left pending, not cleared). */
 #define VMC_FORCE_STATIC_MAX_DOUBLES (1 << 20)
 int vmc_sr_force_static(const float *O, int32_t ldO, int32_t rows, int32_t Np,
                         const double *E, double *obar, double *g, double *ebar,

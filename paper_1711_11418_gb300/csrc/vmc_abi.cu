@@ -28,6 +28,7 @@ struct SysHost {
   void *tc_hi = nullptr, *tc_lo = nullptr;   // split-BF16 operands (mixed form)
   int *tc_status = nullptr;
   int2 *tc_tiles = nullptr;                   // tile order of the S GEMM
+  int s_kernel = VMC_S_KERNEL_NONE;           // kernel of the last dense S~ build
 };
 
 }  // namespace
@@ -369,9 +370,10 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S, bool need_ir = false) {
 int build_S_launch(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs, cudaStream_t st) {
   if (c->precision == VMC_MIXED) {
     CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, s.tc_tiles,
-                          st, &c->n_launch));
+                          st, &c->n_launch, &s.s_kernel));
   } else {
     CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, st, &c->n_launch));
+    s.s_kernel = VMC_S_KERNEL_FP64;
   }
   return VMC_OK;
 }
@@ -380,7 +382,7 @@ int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
   TimedRegion tr(c, 3);
   if (c->precision == VMC_MIXED) {
     CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, s.tc_tiles,
-                          c->st, &c->n_launch));
+                          c->st, &c->n_launch, &s.s_kernel));
     int bad = 0;
     CKC(cudaMemcpyAsync(&bad, s.tc_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CKC(cudaStreamSynchronize(c->st));
@@ -388,6 +390,7 @@ int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
     return VMC_OK;
   }
   CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, c->st, &c->n_launch));
+  s.s_kernel = VMC_S_KERNEL_FP64;
   return VMC_OK;
 }
 
@@ -893,6 +896,7 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
   const bool ir = o->solver == VMC_SOLVE_MIXED_IR;
   CK(sr_alloc(c, s, chol || dense || ir, ir));
   SrWork &w = s.sr;
+  s.s_kernel = VMC_S_KERNEL_NONE;
   TimedRegion tr(c, 2);
   CKC(vmc_sr_means(w, c->st, &c->n_launch));
   CKC(vmc_sr_build_g(w, c->st, &c->n_launch));
@@ -940,6 +944,7 @@ int vmc_sr_step(vmc_ctx *c, int32_t system, const vmc_sr_opts *o, vmc_sr_report 
     rep->n_params = s.Np;
     rep->rel_residual = rel_res;
     rep->fallback = fallback;
+    rep->s_kernel = s.s_kernel;
   }
   return VMC_OK;
 }
@@ -1099,6 +1104,7 @@ int vmc_sr_step_all(vmc_ctx *c, const vmc_sr_opts *o, vmc_sr_report *reps) {
       r.n_params = s.Np;
       r.rel_residual = relres[si];
       r.fallback = fallback[si];
+      r.s_kernel = s.s_kernel;
     }
   }
   CK(join());

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include "../../include/vmc.h"
 #include <stdint.h>
 
 #define VMC_NT 128          // threads per walker CTA (one per row of M^-1)
@@ -178,8 +179,11 @@ int vmc_sr_cg_solve(const SrWork &w, double shift_rel, double shift_abs, double 
                     int kmax, int *iters, cudaStream_t st, long long *nl, int dense);
 void vmc_tc_dims(int rows, int Np, int *ldK, int *Np_pad);
 int vmc_tc_tile_list(int Np, int2 *out);
+// which (may be NULL) receives the kernel that built S: VMC_S_KERNEL_TMA or
+// VMC_S_KERNEL_TILES (include/vmc.h).
 cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
-                              double shift_abs, const int2 *tiles, cudaStream_t st, long long *nl);
+                              double shift_abs, const int2 *tiles, cudaStream_t st, long long *nl,
+                              int *which);
 cudaError_t vmc_sr_update_params(double *params, const double *x, double dtau, int Np,
                                  cudaStream_t st, long long *nl);
 cudaError_t vmc_dot_host(const double *a, const double *b, int n, double *out_host,

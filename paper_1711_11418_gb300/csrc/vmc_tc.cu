@@ -552,7 +552,8 @@ int vmc_tc_tile_list(int Np, int2 *out) {
 }
 
 cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, double shift_rel,
-                              double shift_abs, const int2 *tiles, cudaStream_t st, long long *nl) {
+                              double shift_abs, const int2 *tiles, cudaStream_t st, long long *nl,
+                              int *which) {
   int ldK, Np_pad;
   vmc_tc_dims(w.rows, w.Np, &ldK, &Np_pad);
   cudaError_t e = cudaMemsetAsync(hi, 0, sizeof(__nv_bfloat16) * (size_t)Np_pad * ldK, st);
@@ -587,7 +588,9 @@ cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, 
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_syrk_tma<double><<<grid, XW * 32, TC_SMEM, st>>>(mh, ml, ldK / TKC, w.Np, 1.0 / w.rows, w.S,
                                                         w.Np, tiles, ntiles, status);
+    if (which) *which = VMC_S_KERNEL_TMA;
   } else {
+    if (which) *which = VMC_S_KERNEL_TILES;
     k_syrk_tc<double><<<ntiles, 128, TC_SMEM, st>>>(
         (const __nv_bfloat16 *)hi, (const __nv_bfloat16 *)lo, ldK, ldK, w.Np, 1.0 / w.rows, w.S,
         w.Np, tiles, status);

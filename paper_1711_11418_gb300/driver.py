@@ -68,7 +68,9 @@ def optimize(ctx, n_steps, n_samples, sweeps_between=1, n_warmup=10, dtau=0.05,
 
 def measure_physics(ctx, n_measurements, sweeps_between=1, n_warmup=0, system=0, log=None):
     """n_measurements times: advance every chain by ``sweeps_between``
-    sweeps (``ctx.sample``), then ``ctx.measure_corr``.  Returns
+    sweeps (``ctx.sample(sweeps_between, 0, 0)``: sweeps only, so no E_loc
+    or O_k row is measured and the stored samples of an earlier ``optimize``
+    step are left as they were), then ``ctx.measure_corr``.  Returns
     (mean [6, Ns, Ns], standard error of the mean [6, Ns, Ns], records).
     The error treats the measurements as independent; with
     sweeps_between >= the autocorrelation time it is the Monte Carlo
@@ -83,7 +85,7 @@ def measure_physics(ctx, n_measurements, sweeps_between=1, n_warmup=0, system=0,
             ctx.sample(n_warmup, 0, 0)
         for k in range(n_measurements):
             t0 = time.perf_counter()
-            ctx.sample(0, 1, sweeps_between)
+            ctx.sample(sweeps_between, 0, 0)
             c = np.asarray(ctx.measure_corr(system=system), np.float64)
             acc = c.copy() if acc is None else acc + c
             acc2 = c * c if acc2 is None else acc2 + c * c

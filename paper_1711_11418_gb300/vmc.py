@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libvmc.so")
 FP64, MIXED = 0, 1
 FORCE_STATIC_MAX_DOUBLES = 1 << 20
 CHOLESKY, CG, CG_DENSE, MIXED_IR = 0, 1, 2, 3
+S_KERNELS = ("none", "fp64_simt", "tcgen05_tma_persistent", "tcgen05_tiles")
 CORR_KINDS = ("cdag_c_up", "cdag_c_dn", "n_n", "sz_sz", "sp_sm", "s_s")
 _I32P = C.POINTER(C.c_int32)
 _F64P = C.POINTER(C.c_double)
@@ -63,7 +64,7 @@ class VmcSrOpts(C.Structure):
 class VmcSrReport(C.Structure):
     _fields_ = [("energy", C.c_double), ("norm_g", C.c_double), ("norm_dalpha", C.c_double),
                 ("cg_iters", C.c_int32), ("n_params", C.c_int32), ("rel_residual", C.c_double),
-                ("fallback", C.c_int32)]
+                ("fallback", C.c_int32), ("s_kernel", C.c_int32)]
 
 
 class VmcError(RuntimeError):

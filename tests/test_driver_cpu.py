@@ -66,7 +66,9 @@ def test_measure_physics_mean_and_error(tmp_path):
     log = tmp_path / "m.jsonl"
     mean, err, recs = driver.measure_physics(ctx, 4, sweeps_between=3, n_warmup=5, log=str(log))
     assert ctx.calls[0] == ("sample", 5, 0, 0)
-    assert [c for c in ctx.calls[1:] if c[0] == "sample"] == [("sample", 0, 1, 3)] * 4
+    # the chains advance by sweeps only: no sample rows are measured or replaced
+    assert [c for c in ctx.calls[1:] if c[0] == "sample"] == [("sample", 3, 0, 0)] * 4
+    assert [c[0] for c in ctx.calls[1:]] == ["sample", "measure_corr"] * 4
     # kind 5 takes the values 1, 2, 3, 4: mean 2.5, standard error of the mean
     np.testing.assert_allclose(mean[5], 2.5)
     np.testing.assert_allclose(err[5], np.std([1, 2, 3, 4], ddof=1) / 2.0)

@@ -48,7 +48,42 @@ def test_force_static_matches_context_entry_point():
         o_ref = O.astype(np.float32).astype(np.float64).mean(axis=0)
         assert np.max(np.abs(obar.cpu().numpy() - o_ref)) <= 1e-10 * np.max(np.abs(o_ref)), call
         assert ebar.item() == pytest.approx(E.mean(), rel=1e-12), call
-    # beyond the static scratch: rejected before anything is launched
-    too_many = (vmc.FORCE_STATIC_MAX_DOUBLES // Np + 1) * 2048
-    rc = L.vmc_sr_force_static(ptr(O32), Np, too_many, Np, ptr(Ed), ptr(obar), ptr(g), ptr(ebar), None)
+    # Beyond the static scratch: rejected before anything is launched.  One
+    # row of Np = 2^20 + 1 parameters needs 2^20 + 1 scratch doubles; every
+    # buffer passed is large enough for the arguments, so a regression of the
+    # guard could not read or write outside them.
+    Nbig = vmc.FORCE_STATIC_MAX_DOUBLES + 1
+    Obig = torch.zeros(Nbig, dtype=torch.float32, device="cuda")
+    ob = torch.zeros(Nbig, dtype=torch.float64, device="cuda")
+    gb = torch.zeros(Nbig, dtype=torch.float64, device="cuda")
+    rc = L.vmc_sr_force_static(ptr(Obig), Nbig, 1, Nbig, ptr(Ed), ptr(ob), ptr(gb), ptr(ebar), None)
     assert rc == -1
+    torch.cuda.synchronize()
+    assert float(ob.abs().max()) == 0.0 and float(gb.abs().max()) == 0.0
+
+
+def test_force_static_more_row_chunks_than_grid_rows():
+    """65,536 chunks of 2048 rows (one parameter): more chunks than a grid
+    has rows in y, taken by a loop inside the kernel."""
+    torch = pytest.importorskip("torch")
+    from paper_1711_11418_gb300 import build, vmc
+    build.build()
+    L = vmc.load()
+    rows = 65535 * 2048 + 5
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    O = torch.rand(rows, dtype=torch.float32, device="cuda", generator=gen)
+    # E correlated with O, so that g (about var O = 1/12) is far from zero
+    E = O.double() + 0.5 * torch.rand(rows, dtype=torch.float64, device="cuda", generator=gen)
+    obar = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ebar = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    rc = L.vmc_sr_force_static(ptr(O), 1, rows, 1, ptr(E), ptr(obar), ptr(g), ptr(ebar), None)
+    torch.cuda.synchronize()
+    assert rc == 0
+    O64 = O.double()
+    o_ref = O64.mean()
+    g_ref = ((O64 - o_ref) * (E - E.mean())).mean()
+    assert abs(obar.item() - o_ref.item()) <= 1e-12 * abs(o_ref.item())
+    assert abs(ebar.item() - E.mean().item()) <= 1e-12 * abs(E.mean().item())
+    assert abs(g.item() - g_ref.item()) <= 1e-10 * abs(g_ref.item())
