@@ -86,6 +86,11 @@ typedef struct {
   const int32_t *J_i, *J_j;
   const double *J_val;
   int32_t local_spin;            /* 1: no doublons (g -> -inf), exchange moves only */
+  const int8_t *local_site;      /* [Ns] or NULL.  1 marks a site that holds exactly one
+                                    electron: a local spin of the Kondo lattice (Sec. 2.3
+                                    Kondo model, Sec. 4.2), with double occupancy excluded
+                                    and no empty state.  Hops never enter or leave a marked
+                                    site; only exchanges change its spin.  0 elsewhere. */
 } vmc_model;
 
 /* Variational-parameter layout of one system (host arrays, copied). */
@@ -120,7 +125,8 @@ typedef struct {
   double acceptance;             /* accepted / proposals, cumulative */
   int64_t n_proposals, n_accepted;
   int32_t n_samples;             /* stored rows (walkers x samples) */
-  int32_t n_flagged;             /* walkers with a numerical fault */
+  int32_t n_flagged;             /* walkers with a numerical fault, or skipped by the last
+                                    vmc_sample because a bounded wait expired */
   double max_drift;              /* max |Minv_updated - Minv_fresh| / max |Minv_fresh|
                                     seen at the in-sweep FP64 recomputes */
   int64_t n_hop_tested;          /* valid hop proposals whose ratio was computed */
@@ -170,7 +176,8 @@ enum { VMC_S_KERNEL_NONE = 0, VMC_S_KERNEL_FP64 = 1, VMC_S_KERNEL_TMA = 2,
  * local_spin.  Walker configurations start from a seeded random placement;
  * vmc_set_configs replaces them.
  * Errors: VMC_EINVAL (sizes, Ne odd, Ne/2 > 128, Ns > 4096, index out of
- * range), VMC_ENOMEM, VMC_ECUDA. */
+ * range, local_site entries other than 0/1, or marked sites that Ne/2 up and
+ * Ne/2 down electrons cannot fill one each), VMC_ENOMEM, VMC_ECUDA. */
 int vmc_create(vmc_ctx **out, const vmc_model *model, int32_t Ne,
                const vmc_layout *layout, const double *params,
                double p_exchange, const vmc_opts *opts);
@@ -189,7 +196,8 @@ const char *vmc_strerror(int code);
  * (label order, see above), counters [n_walkers] Philox proposal counters
  * (NULL = keep).  Inverses are rebuilt from scratch (FP64) on the next
  * vmc_sample.  Errors: VMC_EINVAL (out-of-range or doubly occupied spin
- * orbital; doublon under local_spin). */
+ * orbital; doublon under local_spin; a local_site not holding exactly one
+ * electron). */
 int vmc_set_configs(vmc_ctx *ctx, int32_t system, const int32_t *ele,
                     const uint64_t *counters);
 int vmc_get_configs(vmc_ctx *ctx, int32_t system, int32_t *ele,
@@ -277,7 +285,10 @@ int vmc_num_params(vmc_ctx *ctx, int32_t system);
  * system, psi(x')/psi(x) of n_moves candidate moves of its current
  * configuration, each moves[3k..3k+2] = {kind, a, b}: kind 0 = hop of
  * electron a to site b; kind 1 = exchange of up electron a with down
- * electron b.  Invalid moves give 0.  Uses the same device routines as the
+ * electron b.  Invalid moves give 0 (a hop onto an occupied spin orbital,
+ * onto any electron under local_spin, or into or out of a local_site; an
+ * exchange unless both sites are singly occupied).  Uses the same device
+ * routines as the
  * sampler, on the walker's current inverse.  ratios: host [n_moves]. */
 int vmc_eval_ratios(vmc_ctx *ctx, int32_t system, int32_t walker,
                     int32_t n_moves, const int32_t *moves, double *ratios);
@@ -290,6 +301,27 @@ int vmc_get_inverse(vmc_ctx *ctx, int32_t system, int32_t walker,
 
 /* Number of kernels this context has launched since creation. */
 int64_t vmc_kernel_launches(vmc_ctx *ctx);
+
+/* Failure-detection test hook (no counterpart in the paper; off unless
+ * called).  Arms, for one call, a device wait that cannot complete: the
+ * kernel polls, a bounded number of times (2^14), an mbarrier on which no copy
+ * or MMA was issued, gives up with nothing in flight, and the call reports
+ * VMC_ETIMEOUT exactly as for a real expired wait.
+ *   VMC_STALL_SAMPLE: the next vmc_sample: the CTA that takes `walker` of
+ *     `system` issues no copy of that walker's inverse and waits instead; the
+ *     walker is skipped (its chain, counters and sample rows stay as they
+ *     were) and that CTA stops; every other walker is sampled as usual.  The
+ *     next vmc_sample samples it again.
+ *   VMC_STALL_S_BUILD: the next dense S~ build of `system` by the persistent
+ *     tensor-core kernel (mixed form; vmc_sr_step with a dense solver or
+ *     vmc_get_sr_matrices): its first CTA waits before allocating tensor
+ *     memory or issuing any copy or MMA; the SR step fails before the
+ *     parameters change.
+ *   VMC_STALL_NONE: disarm.
+ * Errors: VMC_EINVAL (bad system or walker; VMC_STALL_S_BUILD on a FP64
+ * context). */
+enum { VMC_STALL_NONE = 0, VMC_STALL_SAMPLE = 1, VMC_STALL_S_BUILD = 2 };
+int vmc_test_stall(vmc_ctx *ctx, int32_t target, int32_t system, int32_t walker);
 
 /* Kernel timing with CUDA events on the context's stream (no counterpart in
  * the paper; used to report achieved throughput).  vmc_enable_timing(ctx, 1)

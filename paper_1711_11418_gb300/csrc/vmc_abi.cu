@@ -29,6 +29,7 @@ struct SysHost {
   int *tc_status = nullptr;
   int2 *tc_tiles = nullptr;                   // tile order of the S GEMM
   int s_kernel = VMC_S_KERNEL_NONE;           // kernel of the last dense S~ build
+  std::vector<signed char> lsite;             // local_site mask (empty = none)
 };
 
 }  // namespace
@@ -134,7 +135,12 @@ uint64_t splitmix(uint64_t &s) {
   return z ^ (z >> 31);
 }
 
-void random_placement(int Ns, int Ne, bool local_spin, uint64_t &state, int32_t *ele) {
+// Seeded placement of N up and N down electrons (label order).  Under
+// local_spin every site holds at most one electron; with a local_site mask
+// each marked site gets exactly one electron (a shuffled half up, within
+// what the itinerant sites can take) and the rest go to unmarked sites.
+void random_placement(int Ns, int Ne, bool local_spin, const signed char *lsite, uint64_t &state,
+                      int32_t *ele) {
   const int N = Ne / 2;
   std::vector<int> perm(Ns);
   auto shuffle = [&]() {
@@ -147,6 +153,26 @@ void random_placement(int Ns, int Ne, bool local_spin, uint64_t &state, int32_t 
   shuffle();
   if (local_spin) {
     for (int k = 0; k < Ne; ++k) ele[k] = perm[k];
+    return;
+  }
+  if (lsite) {
+    std::vector<int> loc, itin;
+    for (int q = 0; q < Ns; ++q) (lsite[perm[q]] ? loc : itin).push_back(perm[q]);
+    const int nl = (int)loc.size(), ni = (int)itin.size();
+    // up electrons on marked sites: k with k <= N, nl - k <= N, N - k <= ni,
+    // N - (nl - k) <= ni; the one nearest nl / 2 (validated at create)
+    int k = nl / 2;
+    const int lo = std::max(std::max(0, nl - N), std::max(N - ni, 0));
+    const int hi = std::min(std::min(nl, N), ni + nl - N);
+    k = std::min(std::max(k, lo), hi);
+    int u = 0, d = N;
+    for (int q = 0; q < nl; ++q) ele[q < k ? u++ : d++] = loc[q];
+    for (int q = 0; u < N; ++q) ele[u++] = itin[q];
+    shuffle();
+    std::vector<int> it2;
+    for (int q = 0; q < Ns; ++q)
+      if (!lsite[perm[q]]) it2.push_back(perm[q]);
+    for (int q = 0; d < Ne; ++q) ele[d++] = it2[q];
     return;
   }
   for (int k = 0; k < N; ++k) ele[k] = perm[k];
@@ -168,6 +194,9 @@ int validate_configs(const SysHost &s, bool local_spin, const int32_t *ele, int 
     if (local_spin)
       for (int i = 0; i < s.Ns; ++i)
         if (occ[i] && occ[s.Ns + i]) return VMC_EINVAL;
+    if (!s.lsite.empty())
+      for (int i = 0; i < s.Ns; ++i)
+        if (s.lsite[i] && occ[i] + occ[s.Ns + i] != 1) return VMC_EINVAL;
   }
   return VMC_OK;
 }
@@ -178,6 +207,19 @@ int validate_system(const vmc_model *m, int32_t Ne, const vmc_layout *l, const d
   if (Ns < 2 || Ns > 4096) return VMC_EINVAL;
   if (Ne < 2 || Ne % 2 || Ne / 2 > VMC_MAX_N || Ne / 2 > Ns) return VMC_EINVAL;
   if (m->local_spin && Ne != Ns) return VMC_EINVAL;
+  if (m->local_site) {
+    // each marked site takes one electron: some split k (up) + nl - k (down)
+    // of the marked sites must leave N - k up and N - nl + k down electrons
+    // for the ni unmarked sites
+    int nl = 0;
+    for (int i = 0; i < Ns; ++i) {
+      if (m->local_site[i] != 0 && m->local_site[i] != 1) return VMC_EINVAL;
+      nl += m->local_site[i];
+    }
+    const int N = Ne / 2, ni = Ns - nl;
+    const int lo = std::max(std::max(0, nl - N), N - ni), hi = std::min(std::min(nl, N), ni + nl - N);
+    if (lo > hi || m->local_spin) return VMC_EINVAL;
+  }
   if (m->n_hop < 0 || m->n_V < 0 || m->n_J < 0) return VMC_EINVAL;
   if (m->n_hop && (!m->hop_i || !m->hop_j || !m->hop_t)) return VMC_EINVAL;
   if (m->n_V && (!m->V_i || !m->V_j || !m->V_val)) return VMC_EINVAL;
@@ -369,8 +411,10 @@ int sr_alloc(vmc_ctx *c, SysHost &s, bool need_S, bool need_ir = false) {
 // status stays on the device).
 int build_S_launch(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs, cudaStream_t st) {
   if (c->precision == VMC_MIXED) {
-    CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, s.tc_tiles,
-                          st, &c->n_launch, &s.s_kernel));
+    const cudaError_t e = vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel,
+                                            shift_abs, s.tc_tiles, st, &c->n_launch, &s.s_kernel);
+    s.sr.stall = 0;   // the test hook is armed for one build
+    CKC(e);
   } else {
     CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, st, &c->n_launch));
     s.s_kernel = VMC_S_KERNEL_FP64;
@@ -381,8 +425,11 @@ int build_S_launch(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs, c
 int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
   TimedRegion tr(c, 3);
   if (c->precision == VMC_MIXED) {
-    CKC(vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel, shift_abs, s.tc_tiles,
-                          c->st, &c->n_launch, &s.s_kernel));
+    const cudaError_t e = vmc_sr_build_S_tc(s.sr, s.tc_hi, s.tc_lo, s.tc_status, shift_rel,
+                                            shift_abs, s.tc_tiles, c->st, &c->n_launch,
+                                            &s.s_kernel);
+    s.sr.stall = 0;   // the test hook is armed for one build
+    CKC(e);
     int bad = 0;
     CKC(cudaMemcpyAsync(&bad, s.tc_status, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     CKC(cudaStreamSynchronize(c->st));
@@ -453,6 +500,12 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     d.n_V = m.n_V;
     d.n_J = m.n_J;
     d.local_spin = m.local_spin ? 1 : 0;
+    d.stall_walker = -1;
+    d.lsite = nullptr;
+    if (m.local_site) {
+      s.lsite.assign((const signed char *)m.local_site, (const signed char *)m.local_site + m.Ns);
+      if ((rc = dupload(c, (signed char **)&d.lsite, s.lsite.data(), (size_t)m.Ns))) return fail(rc);
+    }
     {
       const double t = s.p_exchange * 4294967296.0;
       d.pex = t >= 4294967296.0 ? 4294967296ull : (unsigned long long)t;
@@ -577,7 +630,8 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     std::vector<int32_t> ele(W * s.Ne);
     uint64_t state = o->seed ^ (0xA0761D6478BD642Full * (uint64_t)(si + 1));
     for (size_t w = 0; w < W; ++w)
-      random_placement(s.Ns, s.Ne, m.local_spin != 0, state, ele.data() + w * s.Ne);
+      random_placement(s.Ns, s.Ne, m.local_spin != 0, s.lsite.empty() ? nullptr : s.lsite.data(),
+                       state, ele.data() + w * s.Ne);
     if (cudaMemcpyAsync(d.ele, ele.data(), sizeof(int32_t) * ele.size(), cudaMemcpyHostToDevice,
                         c->st) != cudaSuccess)
       return fail(VMC_ECUDA);
@@ -630,7 +684,9 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
         return fail(VMC_ECUDA);
       for (int w = 0; w < s.W; ++w)
         if (st[w] & (VMC_ST_SINGULAR | VMC_ST_ILLCOND))
-          random_placement(s.Ns, s.Ne, models[si].local_spin != 0, state, ele.data() + (size_t)w * s.Ne);
+          random_placement(s.Ns, s.Ne, models[si].local_spin != 0,
+                           s.lsite.empty() ? nullptr : s.lsite.data(), state,
+                           ele.data() + (size_t)w * s.Ne);
       std::vector<int> zero(s.W, 0);
       if (cudaMemcpy(s.dev.ele, ele.data(), sizeof(int32_t) * ele.size(), cudaMemcpyHostToDevice) ||
           cudaMemcpy(s.dev.status, zero.data(), sizeof(int) * s.W, cudaMemcpyHostToDevice))
@@ -722,6 +778,8 @@ int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_b
     }
   }
   CK(upload_sysdesc(c));
+  // the sweep test hook is armed for this call's launches only
+  for (auto &s : c->sys) s.dev.stall_walker = -1;
   auto sweep = [&](int n_first, int ns, int sb, int base) -> int {
     TimedRegion tr(c, 0);
     CKC(vmc_launch_sample(c->d_sys, c->d_work, c->n_work, c->d_work_ctr, c->precision, c->seed,
@@ -784,7 +842,7 @@ int vmc_measure(vmc_ctx *c, int32_t system, vmc_stats *out) {
   for (int w = 0; w < s.W; ++w) {
     out->n_proposals += np[w];
     out->n_accepted += na[w];
-    out->n_flagged += (st[w] & (VMC_ST_SINGULAR | VMC_ST_NUMERIC)) != 0;
+    out->n_flagged += (st[w] & (VMC_ST_SINGULAR | VMC_ST_NUMERIC | VMC_ST_TIMEOUT)) != 0;
     out->max_drift = std::max(out->max_drift, dr[w]);
     out->n_hop_tested += cn[8 * w + 0];
     out->n_exchange_tested += cn[8 * w + 1];
@@ -1247,6 +1305,27 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
 }
 
 int64_t vmc_kernel_launches(vmc_ctx *c) { return c ? c->n_launch : -1; }
+
+int vmc_test_stall(vmc_ctx *c, int32_t target, int32_t system, int32_t walker) {
+  if (!sys_ok(c, system)) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  switch (target) {
+    case VMC_STALL_NONE:
+      s.dev.stall_walker = -1;
+      s.sr.stall = 0;
+      return VMC_OK;
+    case VMC_STALL_SAMPLE:
+      if (walker < 0 || walker >= s.W) return VMC_EINVAL;
+      s.dev.stall_walker = walker;
+      return VMC_OK;
+    case VMC_STALL_S_BUILD:
+      if (c->precision != VMC_MIXED) return VMC_EINVAL;
+      s.sr.stall = 1;
+      return VMC_OK;
+    default:
+      return VMC_EINVAL;
+  }
+}
 
 int vmc_set_delay(vmc_ctx *c, int32_t k) {
   if (!c) return VMC_EINVAL;

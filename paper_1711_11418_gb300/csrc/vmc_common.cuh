@@ -21,6 +21,7 @@
 struct SysDev {
   int Ns, Ne, N, ldm;          // ldm: row stride of M^-1 (odd, >= N)
   int n_hop, n_V, n_J, local_spin;
+  const signed char *lsite;    // [Ns] 1 = site with exactly one electron (Kondo local spin), or NULL
   unsigned long long pex;      // exchange iff r0 < pex (pex <= 2^32)
   int Np, n_g, n_v, n_f, ldO;
   int W;                       // walkers
@@ -70,6 +71,7 @@ struct SysDev {
   double *drift;               // [W]
   int recompute_every;         // accepted moves between FP64 from-scratch inverses (0 = never)
   int delay_k;                 // pending delayed updates before a flush (<= 1: immediate)
+  int stall_walker;            // test hook: this walker's copy is not issued (-1: none)
   // MLP correlation factor exp(w2 . tanh(W1 n + b1) + b2) (H = 0: absent);
   // params hold [W1 (H x 2Ns) | b1 | w2 | b2] after the pair orbitals.
   int n_hidden;
@@ -157,6 +159,8 @@ struct SrWork {
   void *ir_graph;
   int ir_iter;
   double ir_eps;
+  int stall;                   // test hook: CTA 0 of the next tensor-core S build waits on a
+                               // barrier nothing arrives on (then no copy or MMA is issued)
 };
 int vmc_colreduce_parts(int rows, int Np);
 cudaError_t vmc_sr_means(const SrWork &w, cudaStream_t st, long long *nl);

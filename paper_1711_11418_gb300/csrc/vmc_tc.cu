@@ -33,6 +33,7 @@ constexpr int TILE_BYTES = TM * TKC * 2;          // 16 KB per operand tile
 constexpr int STAGE_BYTES = 4 * TILE_BYTES;       // A_hi, A_lo, B_hi, B_lo
 constexpr int TC_SMEM = STAGES * STAGE_BYTES + 1024;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 24;
+constexpr uint32_t STALL_POLLS = 1u << 14;   // attempts of the test hook's wait
 
 __device__ __forceinline__ uint32_t su32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -323,11 +324,12 @@ template <typename TS>
 __global__ void __launch_bounds__(XW * 32, 1)
     k_syrk_tma(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo,
                int nchunks, int Np, double scale, TS *S, int ldS, const int2 *tiles, int ntiles,
-               int *status) {
+               int *status, int stall) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[2], tempty[2];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
+  __shared__ int stalled_sh;
   volatile int *abort = &abort_sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   unsigned char *base = (unsigned char *)(((uintptr_t)smem + 1023) & ~(uintptr_t)1023);
@@ -342,6 +344,32 @@ __global__ void __launch_bounds__(XW * 32, 1)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" ::"r"(su32(&tempty[b])) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // test hook (vmc_test_stall): CTA 0 first waits, bounded, on a barrier
+    // that no copy or MMA targets; it gives up before allocating TMEM or
+    // issuing any copy or MMA, and reports the timeout
+    stalled_sh = 0;
+    if (stall && blockIdx.x == 0) {
+      __shared__ __align__(8) uint64_t never;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&never)) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      bool ok = false;
+      for (uint32_t it = 0; it < STALL_POLLS && !ok; ++it) {
+        uint32_t r;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(r)
+            : "r"(su32(&never)), "r"(0u)
+            : "memory");
+        ok = r != 0;
+      }
+      if (!ok) stalled_sh = 1;
+    }
+  }
+  __syncthreads();
+  if (stalled_sh) {
+    if (tid == 0) atomicExch(status, 1);
+    return;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
@@ -587,7 +615,7 @@ cudaError_t vmc_sr_build_S_tc(const SrWork &w, void *hi, void *lo, int *status, 
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int grid = ntiles < nsm ? ntiles : nsm;
     k_syrk_tma<double><<<grid, XW * 32, TC_SMEM, st>>>(mh, ml, ldK / TKC, w.Np, 1.0 / w.rows, w.S,
-                                                        w.Np, tiles, ntiles, status);
+                                                        w.Np, tiles, ntiles, status, w.stall);
     if (which) *which = VMC_S_KERNEL_TMA;
   } else {
     if (which) *which = VMC_S_KERNEL_TILES;

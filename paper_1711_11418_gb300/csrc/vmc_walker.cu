@@ -67,12 +67,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Wait for the phase with the given parity; false after WAIT_LIMIT attempts.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it)
+// Wait for the phase with the given parity; false after `limit` attempts.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          uint32_t limit = WAIT_LIMIT) {
+  for (uint32_t it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
+// Attempts of the test hook's wait (vmc_test_stall): a short bounded wait on
+// a barrier no copy was issued for.
+constexpr uint32_t STALL_LIMIT = 1u << 14;
 __device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
                "r"(smem_u32(src)), "r"(bytes)
@@ -714,6 +718,8 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   if (sm.occ[s * Ns + t] >= 0) return;
   if (S.local_spin && sm.occ[(1 - s) * Ns + t] >= 0) return;
   const int rs = sm.ele[e];
+  // Kondo local spins hold one electron each: no hop enters or leaves them
+  if (S.lsite && (S.lsite[t] | S.lsite[rs])) return;
   mc.hop_t++;
   // P(x')/P(x): one thread evaluates it; the barrier inside hop_pf_ratio publishes it.
   const int slot = buf;
@@ -1309,8 +1315,12 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     // --- load the walker: M^-1 block by a TMA bulk copy, configuration and
     // Jastrow field by plain loads while the copy is in flight
     const uint32_t nbytes = (uint32_t)minv_bytes(N, ldm, sizeof(T));
+    // test hook (vmc_test_stall): for this walker no copy is issued, so the
+    // bounded wait below runs out with nothing in flight
+    const bool stall = (w == S.stall_walker);
     {
-      if (tid == 0) bulk_load(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, nbytes, &bar);
+      if (tid == 0 && !stall)
+        bulk_load(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, nbytes, &bar);
       for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
       for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
       for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
@@ -1321,17 +1331,19 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
         sm.th[k] = tanh_t<T>(h);
       }
     }
-    const bool loaded = mbar_wait(&bar, phase);
-    phase ^= 1;
+    const bool loaded = mbar_wait(&bar, phase, stall ? STALL_LIMIT : WAIT_LIMIT);
+    if (!stall) phase ^= 1;
     if (__syncthreads_or(!loaded)) {
-      // the copy did not complete within the limit: flag, wait once more for it
-      // (bounded), skip the walker and stop this CTA
+      // the copy did not complete within the limit: flag, wait once more for
+      // it (bounded; nothing to wait for after the test hook's wait), skip the
+      // walker (its chain does not advance) and stop this CTA
       if (tid == 0) {
         S.status[w] |= VMC_ST_TIMEOUT;
-        mbar_wait(&bar, phase ^ 1);
+        if (!stall) mbar_wait(&bar, phase ^ 1);
       }
       break;
     }
+    if (tid == 0) S.status[w] &= ~VMC_ST_TIMEOUT;   // loaded: an earlier timeout is over
     unsigned long long ctr = S.ctr[w];
     int rpos = NT;
     MoveCounts mc;
@@ -1590,7 +1602,8 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
     if (kind == 0) {
       if (a >= 0 && a < Ne && b >= 0 && b < Ns) {
         const int s = (a >= N) ? 1 : 0;
-        if (sm.occ[s * Ns + b] < 0 && !(S.local_spin && sm.occ[(1 - s) * Ns + b] >= 0)) {
+        if (sm.occ[s * Ns + b] < 0 && !(S.local_spin && sm.occ[(1 - s) * Ns + b] >= 0) &&
+            !(S.lsite && (S.lsite[b] | S.lsite[sm.ele[a]]))) {
           T fval, mlp;
           const T rpf = hop_pf_ratio(S, sm, a, b, fval, buf, mlp, 0);
           res = (double)rpf * (double)corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, s, sm.ele[a], b)) *

@@ -263,11 +263,25 @@ def project_to_classes(fmat, f_idx, f_sign, n_f):
 
 
 def initial_configs(Ns: int, Ne: int, n_walkers: int, local_spin: bool,
-                    seed: int) -> np.ndarray:
-    """Random electron placements, int32 [n_walkers, Ne] in label order."""
+                    seed: int, local_sites=None) -> np.ndarray:
+    """Random electron placements, int32 [n_walkers, Ne] in label order.
+    With a local_sites mask (Kondo local spins) each marked site receives
+    exactly one electron, half of them up (rounded down), and the remaining
+    electrons go to unmarked sites."""
     rng = np.random.default_rng(seed)
     N = Ne // 2
     out = np.empty((n_walkers, Ne), np.int32)
+    if local_sites is not None:
+        loc = np.flatnonzero(np.asarray(local_sites, bool))
+        itin = np.flatnonzero(~np.asarray(local_sites, bool))
+        k = len(loc) // 2
+        for w in range(n_walkers):
+            lp = rng.permutation(loc)
+            out[w, :k] = lp[:k]
+            out[w, k:N] = rng.choice(itin, N - k, replace=False)
+            out[w, N:N + len(loc) - k] = lp[k:]
+            out[w, N + len(loc) - k:] = rng.choice(itin, N - (len(loc) - k), replace=False)
+        return out
     for w in range(n_walkers):
         if local_spin:
             p = rng.permutation(Ns)

@@ -30,7 +30,8 @@ class VmcModel(C.Structure):
     _fields_ = [("Ns", C.c_int32), ("n_hop", C.c_int32), ("hop_i", _I32P), ("hop_j", _I32P),
                 ("hop_t", _F64P), ("U", _F64P), ("n_V", C.c_int32), ("V_i", _I32P),
                 ("V_j", _I32P), ("V_val", _F64P), ("n_J", C.c_int32), ("J_i", _I32P),
-                ("J_j", _I32P), ("J_val", _F64P), ("local_spin", C.c_int32)]
+                ("J_j", _I32P), ("J_val", _F64P), ("local_spin", C.c_int32),
+                ("local_site", _I8P)]
 
 
 class VmcLayout(C.Structure):
@@ -80,7 +81,9 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_sr_step", "vmc_get_sr_matrices", "vmc_get_params", "vmc_set_params",
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
            "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
-           "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all", "vmc_measure_corr"]
+           "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all", "vmc_measure_corr",
+           "vmc_test_stall"]
+STALL_NONE, STALL_SAMPLE, STALL_S_BUILD = 0, 1, 2
 
 
 def load(path: str = LIB_PATH):
@@ -124,6 +127,7 @@ def load(path: str = LIB_PATH):
     L.vmc_set_delay.argtypes = [P, C.c_int32]
     L.vmc_get_delay.argtypes = [P]
     L.vmc_tune_delay.argtypes = [P, C.c_int32, _I32P, C.c_int32, _I32P, _F64P]
+    L.vmc_test_stall.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     for name in EXPORTS:
         if name not in ("vmc_destroy", "vmc_strerror", "vmc_kernel_launches"):
             getattr(L, name).restype = C.c_int
@@ -154,11 +158,14 @@ class _Arrays:
         self.f_idx = i32(prob.f_idx)
         self.f_sign = np.ascontiguousarray(prob.f_sign, np.int8)
         self.params = f64(prob.params)
+        ls = getattr(prob, "local_sites", None)
+        self.local_site = None if ls is None else np.ascontiguousarray(np.asarray(ls, bool), np.int8)
         self.model = VmcModel(
             prob.lat.Ns, self.hop_i.size, _p(self.hop_i, _I32P), _p(self.hop_j, _I32P),
             _p(self.hop_t, _F64P), _p(self.U, _F64P), self.V_i.size, _p(self.V_i, _I32P),
             _p(self.V_j, _I32P), _p(self.V_val, _F64P), self.J_i.size, _p(self.J_i, _I32P),
-            _p(self.J_j, _I32P), _p(self.J_val, _F64P), int(prob.local_spin))
+            _p(self.J_j, _I32P), _p(self.J_val, _F64P), int(prob.local_spin),
+            _p(self.local_site, _I8P))
         self.layout = VmcLayout(prob.n_g, prob.n_v, prob.n_f, _p(self.g_idx, _I32P),
                                 _p(self.v_idx, _I32P), _p(self.f_idx, _I32P),
                                 _p(self.f_sign, _I8P), int(getattr(prob, "n_hidden", 0) or 0))
@@ -171,10 +178,6 @@ class Context:
                  delay_k=0, recompute_every=0, stream=None):
         L = load()
         probs = problems if isinstance(problems, (list, tuple)) else [problems]
-        for pr in probs:
-            if getattr(pr, "local_sites", None) is not None and not pr.local_spin:
-                raise VmcError(-1, "vmc_create: per-site local-spin constraint (Kondo "
-                                   "lattice) is not supported by the library")
         self.problems = list(probs)
         self.n_walkers = int(n_walkers)
         self.precision = precision
@@ -332,6 +335,13 @@ class Context:
 
     def kernel_launches(self):
         return int(self._L.vmc_kernel_launches(self._h))
+
+    def test_stall(self, target, system=0, walker=0):
+        """Failure-detection test hook (vmc_test_stall): arm one bounded wait
+        that cannot complete in the next vmc_sample (STALL_SAMPLE, `walker`)
+        or dense S build (STALL_S_BUILD); STALL_NONE disarms."""
+        _check(self._L.vmc_test_stall(self._h, int(target), int(system), int(walker)),
+               "vmc_test_stall")
 
     # -- delayed updates
     def set_delay(self, k):

@@ -3,6 +3,7 @@ entry point that include/vmc.h declares (no CUDA call is made here)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -36,10 +37,25 @@ def test_strerror_is_host_only():
     assert b"invalid" in L.vmc_strerror(-1)
 
 
-def test_context_rejects_per_site_local_spin():
-    """The CUDA path has no per-site local-spin constraint: a Kondo-lattice
-    problem is refused before any CUDA call."""
+def test_context_rejects_an_unfillable_local_site_mask():
+    """Kondo local spins: every marked site must take exactly one electron.
+    Four marked sites and two electrons cannot satisfy that; the library
+    refuses the problem before any CUDA call."""
     from paper_1711_11418_gb300 import build, inputs, vmc
     vmc.load(build.build())
-    with pytest.raises(vmc.VmcError):
-        vmc.Context(inputs.kondo_chain(2), 2)
+    p = inputs.kondo_chain(2)
+    bad = p.copy_with(Ne=2, local_sites=np.ones(p.Ns, bool))
+    with pytest.raises(vmc.VmcError) as e:
+        vmc.Context(bad, 2)
+    assert e.value.code == -1
+
+
+def test_kondo_placements_fill_each_local_site_once():
+    from paper_1711_11418_gb300 import inputs
+    p = inputs.kondo_chain(8)
+    cfg = inputs.initial_configs(p.Ns, p.Ne, 20, False, 3, local_sites=p.local_sites)
+    for e in cfg:
+        up, dn = e[:p.N], e[p.N:]
+        assert len(set(up)) == p.N and len(set(dn)) == p.N
+        occ = np.bincount(e, minlength=p.Ns)
+        assert np.all(occ[p.local_sites] == 1)
