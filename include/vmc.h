@@ -226,7 +226,9 @@ int vmc_measure(vmc_ctx *ctx, int32_t system, vmc_stats *out);
  * vmc_sample calls gives the Monte Carlo estimate of <A>; the structure
  * factors of Sec. 2.4.2 (n_sigma(k), N(k), S^z(k), S(k)) and the doublon
  * density and nearest-neighbour spin correlation of Sec. 4.1.1 follow from
- * these matrices.  Hops and spin swaps are evaluated from the walker's
+ * these matrices.  With local_site marks (Kondo local spins), a hop into or
+ * out of a marked site leaves the constrained space, where psi = 0, so those
+ * entries of kinds 0 and 1 are 0.  Hops and spin swaps are evaluated from the walker's
  * M^-1 in the context's precision (FP64, or FP32 in the mixed form), the
  * diagonal kinds are exact; the walker means are FP64 (summed by atomic
  * adds, so their last bit may differ between calls).
@@ -298,6 +300,33 @@ int vmc_eval_ratios(vmc_ctx *ctx, int32_t system, int32_t walker,
  * from-scratch factorisation. */
 int vmc_get_inverse(vmc_ctx *ctx, int32_t system, int32_t walker,
                     double *minv, double *logabsdet, int32_t *sign);
+
+/* Quantum-number projection of the pair product (Sec. 3.2.2, Eqs. momP and
+ * pointP; boundary signs of App. A): after this call the context samples
+ *   psi(x) = P(x) sum_g w_g <T_g^-1 x | phi_Pf>,
+ * with the correlation factors P applied after the projector, where
+ * T_g c^dag_{r,s} T_g^-1 = sign[g*Ns + r] c^dag_{perm[g*Ns + r], s}: operation g
+ * maps site r to perm[g*Ns + r] with the fermion sign an anti-periodic
+ * boundary gives (a permutation of the sites for every g, signs +1 / -1).
+ * weight: w_g, real (momentum projection L_K with K components 0 or pi:
+ * w_R = cos(K.R) / N_g; point groups: real characters / N_g; products of both
+ * as the composed operations).  vmc_sample, vmc_measure, vmc_sr_step and
+ * vmc_eval_ratios then use the projected state: every walker keeps one M_g^-1
+ * per operation (N_g N^2 entries in device memory, allocated here) and the
+ * share of each operation in its projected amplitude; the E_loc and O_k rows
+ * are those of the projected state (the pair-orbital O_k are the
+ * amplitude-weighted means over the operations).  Inverses are rebuilt (FP64)
+ * before the next sample; walkers whose projected amplitude vanishes get new
+ * seeded placements.  n_ops = 0 removes the projection.
+ * Restrictions: a single-system context, no MLP factor, immediate updates
+ * (delay depth 0 or 1); vmc_measure_corr, vmc_get_inverse and
+ * vmc_tune_delay return VMC_EINVAL while a projection is set, and so does a
+ * local_site mask that some operation does not map onto itself.
+ * Errors: VMC_EINVAL (as above, n_ops > VMC_PROJ_MAX_OPS, a perm that is not
+ * a permutation, a bad sign or weight), VMC_ENOMEM, VMC_ESINGULAR, VMC_ECUDA. */
+#define VMC_PROJ_MAX_OPS 1024
+int vmc_set_projection(vmc_ctx *ctx, int32_t n_ops, const int32_t *perm, const int8_t *sign,
+                       const double *weight);
 
 /* Number of kernels this context has launched since creation. */
 int64_t vmc_kernel_launches(vmc_ctx *ctx);

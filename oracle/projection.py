@@ -133,7 +133,7 @@ def projected_pair_amplitude(wf, n, weighted_ops):
 
 class ProjectedWavefunction:
     """psi(x) = P(x) <x| L |phi_Pf> for real weights: the same interface as
-    Wavefunction for amplitudes and local energies (no O_k)."""
+    Wavefunction for amplitudes, local energies and O_k."""
 
     def __init__(self, wf, weighted_ops):
         for _, w in weighted_ops:
@@ -160,3 +160,29 @@ class ProjectedWavefunction:
     def amplitude(self, n):
         s, l = self.amplitude_slog(n)
         return s * math.exp(l) if s != 0.0 else 0.0
+
+    def log_derivatives(self, n):
+        """O_k = d ln psi / d alpha_k (Sec. 3.3.1) of the projected state.
+        The correlation factors multiply the projected pair product, so their
+        O_k are those of x itself.  The pair-orbital part is the derivative of
+        ln sum_g w_g <T_g^-1 x|phi>: each term contributes its own
+        d ln Pf / d f (Eq. DiffPf, on the mapped configuration) weighted by
+        its share of the sum."""
+        base = self.base
+        out = base.log_derivatives(n)
+        k0, k1 = base.n_g + base.n_v, base.n_g + base.n_v + base.n_f
+        num = np.zeros(k1 - k0)
+        den = 0.0
+        for op, w in self.ops:
+            r = mapped_configuration(op, n, self.Ns)
+            if r is None:
+                continue
+            sgn, n2 = r
+            s, l = pair_amplitude_slog(base, n2)
+            if s == 0.0:
+                continue
+            a = w * sgn * s * math.exp(l)
+            num += a * base.log_derivatives(n2)[k0:k1]
+            den += a
+        out[k0:k1] = num / den
+        return out

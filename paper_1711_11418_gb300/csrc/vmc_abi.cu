@@ -57,6 +57,8 @@ struct vmc_ctx {
   cudaStream_t pool[NPOOL] = {};
   cudaEvent_t fork_ev = nullptr, join_ev[NPOOL] = {};
   size_t smem_cap = 0;        // dynamic shared-memory limit set on the sweep kernels
+  size_t smem_proj = 0;       // projected sweep kernel (vmc_set_projection)
+  int grid_proj = 0;
   void *corr_buf = nullptr;   // vmc_measure_corr scratch (grown on demand)
   size_t corr_bytes = 0;
   // timing (CUDA events on st): 0 sweep, 1 init, 2 SR step, 3 S GEMM
@@ -331,8 +333,12 @@ int ensure_init(vmc_ctx *c, bool redraw_illcond = false) {
   CK(upload_sysdesc(c));
   {
     TimedRegion tr(c, 1);
-    CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 0, 0, c->smem_init, c->st,
-                        &c->n_launch));
+    if (c->n_sys == 1 && c->sys[0].dev.n_ops > 0)
+      CKC(vmc_launch_proj_build(c->d_sys, c->d_work, c->n_work, c->sys[0].dev.n_ops, c->precision,
+                                0, 0, c->smem_init, c->st, &c->n_launch));
+    else
+      CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 0, 0, c->smem_init, c->st,
+                          &c->n_launch));
   }
   int bad = 0;
   for (auto &s : c->sys) {
@@ -439,6 +445,33 @@ int build_S(vmc_ctx *c, SysHost &s, double shift_rel, double shift_abs) {
   CKC(vmc_sr_build_S(s.sr, shift_rel, shift_abs, c->st, &c->n_launch));
   s.s_kernel = VMC_S_KERNEL_FP64;
   return VMC_OK;
+}
+
+// From-scratch inverses of every walker; walkers whose M (or, for a projected
+// context, whose projected amplitude) is singular or ill-conditioned get a
+// new seeded placement, at most 20 times.
+int init_with_redraw(vmc_ctx *c, uint64_t state) {
+  for (int attempt = 0;; ++attempt) {
+    const int rc = ensure_init(c, true);
+    if (rc == VMC_OK) return VMC_OK;
+    if (rc != VMC_ESINGULAR || attempt >= 20) return rc;
+    for (SysHost &s : c->sys) {
+      std::vector<int> st(s.W);
+      std::vector<int32_t> ele((size_t)s.W * s.Ne);
+      if (cudaMemcpy(st.data(), s.dev.status, sizeof(int) * s.W, cudaMemcpyDeviceToHost) ||
+          cudaMemcpy(ele.data(), s.dev.ele, sizeof(int32_t) * ele.size(), cudaMemcpyDeviceToHost))
+        return VMC_ECUDA;
+      for (int w = 0; w < s.W; ++w)
+        if (st[w] & (VMC_ST_SINGULAR | VMC_ST_ILLCOND))
+          random_placement(s.Ns, s.Ne, s.dev.local_spin != 0,
+                           s.lsite.empty() ? nullptr : s.lsite.data(), state,
+                           ele.data() + (size_t)w * s.Ne);
+      std::vector<int> zero(s.W, 0);
+      if (cudaMemcpy(s.dev.ele, ele.data(), sizeof(int32_t) * ele.size(), cudaMemcpyHostToDevice) ||
+          cudaMemcpy(s.dev.status, zero.data(), sizeof(int) * s.W, cudaMemcpyHostToDevice))
+        return VMC_ECUDA;
+    }
+  }
 }
 
 int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t *Ne,
@@ -670,35 +703,15 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
   c->recompute_every = o->recompute_every > 0 ? o->recompute_every
                        : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 256 : 0;
   // Initial inverses; re-draw placements whose M is singular (bounded).
-  uint64_t state = o->seed ^ 0x5851F42D4C957F2Dull;
-  for (int attempt = 0;; ++attempt) {
-    rc = ensure_init(c, true);
-    if (rc == VMC_OK) break;
-    if (rc != VMC_ESINGULAR || attempt >= 20) return fail(rc);
-    for (int si = 0; si < n_sys; ++si) {
-      SysHost &s = c->sys[si];
-      std::vector<int> st(s.W);
-      std::vector<int32_t> ele((size_t)s.W * s.Ne);
-      if (cudaMemcpy(st.data(), s.dev.status, sizeof(int) * s.W, cudaMemcpyDeviceToHost) ||
-          cudaMemcpy(ele.data(), s.dev.ele, sizeof(int32_t) * ele.size(), cudaMemcpyDeviceToHost))
-        return fail(VMC_ECUDA);
-      for (int w = 0; w < s.W; ++w)
-        if (st[w] & (VMC_ST_SINGULAR | VMC_ST_ILLCOND))
-          random_placement(s.Ns, s.Ne, models[si].local_spin != 0,
-                           s.lsite.empty() ? nullptr : s.lsite.data(), state,
-                           ele.data() + (size_t)w * s.Ne);
-      std::vector<int> zero(s.W, 0);
-      if (cudaMemcpy(s.dev.ele, ele.data(), sizeof(int32_t) * ele.size(), cudaMemcpyHostToDevice) ||
-          cudaMemcpy(s.dev.status, zero.data(), sizeof(int) * s.W, cudaMemcpyHostToDevice))
-        return fail(VMC_ECUDA);
-    }
-  }
+  if ((rc = init_with_redraw(c, o->seed ^ 0x5851F42D4C957F2Dull))) return fail(rc);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(VMC_ECUDA);
   *out = c;
   return VMC_OK;
 }
 
 bool sys_ok(vmc_ctx *c, int s) { return c && s >= 0 && s < c->n_sys; }
+
+bool projected(const vmc_ctx *c) { return c->n_sys == 1 && c->sys[0].dev.n_ops > 0; }
 
 
 
@@ -780,11 +793,17 @@ int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_b
   CK(upload_sysdesc(c));
   // the sweep test hook is armed for this call's launches only
   for (auto &s : c->sys) s.dev.stall_walker = -1;
+  const bool proj = projected(c);
   auto sweep = [&](int n_first, int ns, int sb, int base) -> int {
     TimedRegion tr(c, 0);
-    CKC(vmc_launch_sample(c->d_sys, c->d_work, c->n_work, c->d_work_ctr, c->precision, c->seed,
-                          n_first, ns, sb, base, c->grid_sample, c->smem_sample, c->st,
-                          &c->n_launch));
+    if (proj)
+      CKC(vmc_launch_proj_sample(c->d_sys, c->d_work, c->n_work, c->d_work_ctr, c->precision,
+                                 c->seed, n_first, ns, sb, base, c->grid_proj, c->smem_proj, c->st,
+                                 &c->n_launch));
+    else
+      CKC(vmc_launch_sample(c->d_sys, c->d_work, c->n_work, c->d_work_ctr, c->precision, c->seed,
+                            n_first, ns, sb, base, c->grid_sample, c->smem_sample, c->st,
+                            &c->n_launch));
     return VMC_OK;
   };
   if (c->recompute_every <= 0) {
@@ -795,8 +814,13 @@ int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_b
     // accepted moves since their last inverse are rebuilt.
     auto recompute = [&]() -> int {
       TimedRegion tr(c, 1);
-      CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 1, c->recompute_every,
-                          c->smem_init, c->st, &c->n_launch));
+      if (proj)
+        CKC(vmc_launch_proj_build(c->d_sys, c->d_work, c->n_work, c->sys[0].dev.n_ops,
+                                  c->precision, 1, c->recompute_every, c->smem_init, c->st,
+                                  &c->n_launch));
+      else
+        CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 1, c->recompute_every,
+                            c->smem_init, c->st, &c->n_launch));
       return VMC_OK;
     };
     for (int k = 0; k < n_warmup; ++k) {
@@ -1211,8 +1235,10 @@ int vmc_eval_ratios(vmc_ctx *c, int32_t system, int32_t walker, int32_t n_moves,
   }
   int rc = VMC_OK;
   if (cudaMemcpyAsync(dm, moves, sizeof(int) * 3 * n_moves, cudaMemcpyHostToDevice, c->st) ||
-      vmc_launch_eval_ratios(c->d_sys, system, walker, c->precision, n_moves, dm, dout,
-                             c->smem_sample, c->st, &c->n_launch) ||
+      (projected(c) ? vmc_launch_proj_eval(c->d_sys, system, walker, c->precision, n_moves, dm,
+                                           dout, c->smem_proj, c->st, &c->n_launch)
+                    : vmc_launch_eval_ratios(c->d_sys, system, walker, c->precision, n_moves, dm,
+                                             dout, c->smem_sample, c->st, &c->n_launch)) ||
       cudaMemcpyAsync(ratios, dout, sizeof(double) * n_moves, cudaMemcpyDeviceToHost, c->st) ||
       cudaStreamSynchronize(c->st))
     rc = VMC_ECUDA;
@@ -1223,7 +1249,7 @@ int vmc_eval_ratios(vmc_ctx *c, int32_t system, int32_t walker, int32_t n_moves,
 
 int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, double *logabsdet,
                     int32_t *sign) {
-  if (!sys_ok(c, system)) return VMC_EINVAL;
+  if (!sys_ok(c, system) || projected(c)) return VMC_EINVAL;
   SysHost &s = c->sys[system];
   if (walker < 0 || walker >= s.W) return VMC_EINVAL;
   CK(ensure_init(c));
@@ -1249,7 +1275,7 @@ int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, do
 int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
   if (!sys_ok(c, system) || !corr) return VMC_EINVAL;
   SysHost &s = c->sys[system];
-  if (s.dev.n_hidden) return VMC_EINVAL;
+  if (s.dev.n_hidden || projected(c)) return VMC_EINVAL;
   CK(ensure_init(c));
   CK(upload_sysdesc(c));
   const int prec = c->precision == VMC_FP64 ? 0 : 1;
@@ -1287,7 +1313,7 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
       (ms && cudaEventRecord(ev[1], c->st)) ||
       vmc_launch_corr(c->d_sys, system, prec, grid, part, c->smem_sample, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[2], c->st)) ||
-      vmc_launch_corr_reduce(part, 1, cnt, s.Ns, s.W, out, c->st, &c->n_launch) ||
+      vmc_launch_corr_reduce(part, 1, cnt, s.Ns, s.W, s.dev.lsite, out, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[3], c->st)) ||
       cudaMemcpyAsync(corr, out, out_b, cudaMemcpyDeviceToHost, c->st) ||
       cudaStreamSynchronize(c->st))
@@ -1328,8 +1354,70 @@ int vmc_test_stall(vmc_ctx *c, int32_t target, int32_t system, int32_t walker) {
 }
 
 int vmc_set_delay(vmc_ctx *c, int32_t k) {
-  if (!c) return VMC_EINVAL;
+  if (!c || (projected(c) && k > 1)) return VMC_EINVAL;
   return set_delay_impl(c, k);
+}
+
+int vmc_set_projection(vmc_ctx *c, int32_t n_ops, const int32_t *perm, const int8_t *sign,
+                       const double *weight) {
+  if (!c || c->n_sys != 1 || n_ops < 0 || n_ops > VMC_PROJ_MAX_OPS) return VMC_EINVAL;
+  SysHost &s = c->sys[0];
+  if (n_ops == 0) {
+    s.dev.n_ops = 0;
+    s.dirty = true;
+    return upload_sysdesc(c);
+  }
+  if (!perm || !sign || !weight || s.dev.n_hidden || c->delay_k > 1) return VMC_EINVAL;
+  const int Ns = s.Ns;
+  // T_g c^dag_r T_g^-1 = sign[r] c^dag_perm[r]: keep g^-1 and the sign of
+  // T_g^-1 on each site, sign[g^-1(q)]
+  std::vector<int> inv((size_t)n_ops * Ns);
+  std::vector<signed char> isg((size_t)n_ops * Ns);
+  for (int g = 0; g < n_ops; ++g) {
+    if (!isfinite(weight[g])) return VMC_EINVAL;
+    std::vector<char> seen(Ns, 0);
+    for (int r = 0; r < Ns; ++r) {
+      const int q = perm[(size_t)g * Ns + r];
+      const int sg = sign[(size_t)g * Ns + r];
+      if (q < 0 || q >= Ns || seen[q] || (sg != 1 && sg != -1)) return VMC_EINVAL;
+      seen[q] = 1;
+      inv[(size_t)g * Ns + q] = r;
+      isg[(size_t)g * Ns + q] = (signed char)sg;
+    }
+    // the operation must map the local-spin sites onto local-spin sites
+    if (!s.lsite.empty())
+      for (int r = 0; r < Ns; ++r)
+        if (s.lsite[r] != s.lsite[perm[(size_t)g * Ns + r]]) return VMC_EINVAL;
+  }
+  const int esize = c->precision == VMC_FP64 ? 8 : 4;
+  const size_t W = s.W, N = s.N;
+  const size_t smem = vmc_proj_smem(c->precision == VMC_FP64 ? 0 : 1, s.N, s.Ns, n_ops);
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (smem > (size_t)optin) return VMC_EINVAL;
+  CKC(cudaStreamSynchronize(c->st));
+  SysDev &d = s.dev;
+  int rc;
+  if ((rc = dupload(c, (int **)&d.pinv, inv.data(), inv.size()))) return rc;
+  if ((rc = dupload(c, (signed char **)&d.psgn, isg.data(), isg.size()))) return rc;
+  if ((rc = dupload(c, (double **)&d.pw, weight, (size_t)n_ops))) return rc;
+  if ((rc = dalloc(c, &d.pminv, (size_t)esize * W * n_ops * N * N))) return rc;
+  if ((rc = dalloc(c, &d.ppi, sizeof(double) * W * n_ops))) return rc;
+  if ((rc = dalloc(c, &d.plog, sizeof(double) * W * n_ops))) return rc;
+  if ((rc = dalloc(c, &d.psign, sizeof(int) * W * n_ops))) return rc;
+  CKC(vmc_proj_set_smem(smem, c->smem_init));
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int occ = std::max(1, vmc_proj_occupancy(c->precision, smem));
+  c->smem_proj = smem;
+  c->grid_proj = std::min(c->n_work, nsm * occ);
+  d.n_ops = n_ops;
+  s.dirty = true;
+  CK(upload_sysdesc(c));
+  CK(init_with_redraw(c, c->seed ^ 0x2545F4914F6CDD1Dull));
+  CKC(cudaStreamSynchronize(c->st));
+  return VMC_OK;
 }
 
 int32_t vmc_get_delay(vmc_ctx *c) { return c ? c->delay_k : -1; }
@@ -1337,7 +1425,7 @@ int32_t vmc_get_delay(vmc_ctx *c) { return c ? c->delay_k : -1; }
 int vmc_tune_delay(vmc_ctx *c, int32_t sweeps, const int32_t *cand, int32_t n_cand,
                    int32_t *chosen, double *ms) {
   static const int32_t def[] = {1, 4, 8, 16, 32};
-  if (!c || sweeps < 1 || (cand && n_cand < 1) || !chosen) return VMC_EINVAL;
+  if (!c || sweeps < 1 || (cand && n_cand < 1) || !chosen || projected(c)) return VMC_EINVAL;
   if (!cand) {
     cand = def;
     n_cand = 5;

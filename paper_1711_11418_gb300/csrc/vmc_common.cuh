@@ -72,6 +72,15 @@ struct SysDev {
   int recompute_every;         // accepted moves between FP64 from-scratch inverses (0 = never)
   int delay_k;                 // pending delayed updates before a flush (<= 1: immediate)
   int stall_walker;            // test hook: this walker's copy is not issued (-1: none)
+  // quantum-number projection (Sec. 3.2.2): n_ops operations g (0 = none)
+  int n_ops;
+  const int *pinv;             // [n_ops*Ns] g^-1(site)
+  const signed char *psgn;     // [n_ops*Ns] sign of T_g^-1 on that site
+  const double *pw;            // [n_ops] weights w_g
+  void *pminv;                 // [W*n_ops*N*N] M_g^-1 (double or float), row-major, ld N
+  double *ppi;                 // [W*n_ops] shares pi_g of the projected amplitude
+  double *plog;                // [W*n_ops] log|A_g| of the last from-scratch build
+  int *psign;                  // [W*n_ops] sign of A_g (0: M_g singular)
   // MLP correlation factor exp(w2 . tanh(W1 n + b1) + b2) (H = 0: absent);
   // params hold [W1 (H x 2Ns) | b1 | w2 | b2] after the pair orbitals.
   int n_hidden;
@@ -124,12 +133,28 @@ cudaError_t vmc_launch_corr(const SysDev *d_sys, int sys, int precision, int gri
 cudaError_t vmc_launch_corr_occ(const SysDev *d_sys, int sys, int Ns, int *cnt,
                                 cudaStream_t st, long long *n_launch);
 cudaError_t vmc_launch_corr_reduce(const double *part, int n_part, const int *cnt, int Ns,
-                                   int W, double *out, cudaStream_t st, long long *n_launch);
+                                   int W, const signed char *lsite, double *out, cudaStream_t st,
+                                   long long *n_launch);
 size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len);
 size_t vmc_init_smem(int N, int Ns);
 int vmc_sample_occupancy(int precision, size_t smem);
 cudaError_t vmc_walker_set_smem_limits(size_t smem_sample64, size_t smem_sample32,
                                        size_t smem_init);
+
+// Projected wave function (vmc_proj.cu)
+size_t vmc_proj_smem(int precision, int N, int Ns, int n_ops);
+int vmc_proj_occupancy(int precision, size_t smem);
+cudaError_t vmc_proj_set_smem(size_t s_sample, size_t s_build);
+cudaError_t vmc_launch_proj_build(const SysDev *d_sys, const int2 *d_work, int n_work, int n_ops,
+                                  int precision, int only_due, int due_threshold, size_t smem,
+                                  cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_proj_sample(const SysDev *d_sys, const int2 *d_work, int n_work,
+                                   int *d_work_ctr, int precision, uint64_t seed, int n_first,
+                                   int n_samples, int sweeps_between, int sample_base, int grid,
+                                   size_t smem, cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_proj_eval(const SysDev *d_sys, int sys, int walker, int precision,
+                                 int n_moves, const int *d_moves, double *d_out, size_t smem,
+                                 cudaStream_t st, long long *n_launch);
 
 // SR (vmc_sr.cu)
 struct SrWork {

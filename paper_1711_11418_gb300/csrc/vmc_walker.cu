@@ -15,21 +15,13 @@
 // matrix-determinant lemma; the inverse follows by Sherman-Morrison
 // (rank 1) or Woodbury (rank 2).
 #include "vmc_common.cuh"
+#include "vmc_gj.cuh"
+#include "vmc_dev.cuh"
 
 #include <cuda_bf16.h>
 #include <math.h>
 
 namespace {
-
-constexpr int NT = VMC_NT;
-constexpr int NWARP = NT / 32;
-
-template <typename T> __device__ __forceinline__ const T *ftab(const SysDev &s);
-template <> __device__ __forceinline__ const double *ftab<double>(const SysDev &s) { return s.f64; }
-template <> __device__ __forceinline__ const float *ftab<float>(const SysDev &s) { return s.f32; }
-template <typename T> __device__ __forceinline__ const T *fTtab(const SysDev &s);
-template <> __device__ __forceinline__ const double *fTtab<double>(const SysDev &s) { return s.fT64; }
-template <> __device__ __forceinline__ const float *fTtab<float>(const SysDev &s) { return s.fT32; }
 
 __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -156,13 +148,6 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int 
   return off;
 }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return __shfl_sync(0xffffffffu, v, 0);   // lane 0's value: identical in every lane
-}
-
 // Block sum with a double-buffered partial array: every thread returns the
 // same value (same partials, same order).  One __syncthreads.
 template <typename T>
@@ -273,78 +258,58 @@ __device__ __forceinline__ void mlp_apply(const SysDev &S, const WSmem<T> &sm, i
   }
 }
 
-// log of the correlation-factor ratio P(x')/P(x) for a hop of a spin-s
-// electron from site r to site t (Sec. 3.2.3): Gutzwiller g_t n_t,-s - g_r n_r,-s
-// and Jastrow h_t - h_r - v_rt with h_i = sum_{j != i} v_ij (n_j - 1).
-template <typename T> __device__ __forceinline__ const T *vtab(const SysDev &s);
-template <> __device__ __forceinline__ const double *vtab<double>(const SysDev &s) { return s.vmat; }
-template <> __device__ __forceinline__ const float *vtab<float>(const SysDev &s) { return s.vmat32; }
-template <typename T> __device__ __forceinline__ const T *gtab(const SysDev &s);
-template <> __device__ __forceinline__ const double *gtab<double>(const SysDev &s) { return s.gsite; }
-template <> __device__ __forceinline__ const float *gtab<float>(const SysDev &s) { return s.gsite32; }
-
-// In the sweep's arithmetic type (FP32 in the mixed form: GB300's FP64 pipe
-// is too slow for per-proposal work).
-template <typename T>
-__device__ __forceinline__ T corr_hop(const SysDev &S, const int *occ, const T *jf, int s, int r,
-                                      int t) {
-  const int Ns = S.Ns;
-  const int o = (1 - s) * Ns;
-  const T *g = gtab<T>(S);
-  T d = jf[t] - jf[r] - vtab<T>(S)[(size_t)r * Ns + t];
-  d += (occ[o + t] >= 0 ? g[t] : (T)0) - (occ[o + r] >= 0 ? g[r] : (T)0);
-  return d;
-}
-
-template <typename T> __device__ __forceinline__ const T *tvtab(const SysDev &s);
-template <> __device__ __forceinline__ const double *tvtab<double>(const SysDev &s) { return s.tgt_v64; }
-template <> __device__ __forceinline__ const float *tvtab<float>(const SysDev &s) { return s.tgt_v32; }
-
-// Same, with g from shared memory and v_rt given.
-template <typename T>
-__device__ __forceinline__ T corr_hop_v(const int *occ, const T *jf, const T *g, int Ns, int s,
-                                        int r, int t, T vrt) {
-  const int o = (1 - s) * Ns;
-  T d = jf[t] - jf[r] - vrt;
-  d += (occ[o + t] >= 0 ? g[t] : (T)0) - (occ[o + r] >= 0 ? g[r] : (T)0);
-  return d;
-}
-
-template <typename T> __device__ __forceinline__ T corr_factor(T dlog);
-template <> __device__ __forceinline__ double corr_factor<double>(double dlog) { return exp(dlog); }
-template <> __device__ __forceinline__ float corr_factor<float>(float dlog) { return expf(dlog); }
-
 // The shared-memory row loops are staged through registers CH elements at a
 // time, so a chunk's loads are all issued before its stores (the compiler
 // cannot reorder loads of one array past stores to another shared array).
 constexpr int CH = 16;
 
+// Four consecutive entries of a 16-byte-aligned shared vector (the x / y
+// operands below are always slots of the walker's vector area) by 128-bit
+// loads: one load instruction per four entries for FP32, two for FP64.
+__device__ __forceinline__ void ld4(const float *p, float &a, float &b, float &c, float &d) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  a = v.x;
+  b = v.y;
+  c = v.z;
+  d = v.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double &a, double &b, double &c, double &d) {
+  const double2 u = *reinterpret_cast<const double2 *>(p);
+  const double2 v = *reinterpret_cast<const double2 *>(p + 2);
+  a = u.x;
+  b = u.y;
+  c = v.x;
+  d = v.y;
+}
+
+// row[k] -= c x[k]  (x 16-byte aligned)
 template <typename T>
 __device__ __forceinline__ void row_axpy(T *row, const T *x, T c, int N) {
   int k = 0;
   for (; k + CH <= N; k += CH) {
     T a[CH], b[CH];
 #pragma unroll
-    for (int u = 0; u < CH; ++u) {
-      a[u] = row[k + u];
-      b[u] = x[k + u];
-    }
+    for (int u = 0; u < CH; ++u) a[u] = row[k + u];
+#pragma unroll
+    for (int u = 0; u < CH; u += 4) ld4(x + k + u, b[u], b[u + 1], b[u + 2], b[u + 3]);
 #pragma unroll
     for (int u = 0; u < CH; ++u) row[k + u] = a[u] - c * b[u];
   }
   for (; k < N; ++k) row[k] -= c * x[k];
 }
 
+// row[k] -= c1 x[k] + c2 y[k]  (x, y 16-byte aligned)
 template <typename T>
 __device__ __forceinline__ void row_axpy2(T *row, const T *x, const T *y, T c1, T c2, int N) {
   int k = 0;
   for (; k + CH <= N; k += CH) {
     T a[CH], b[CH], d[CH];
 #pragma unroll
-    for (int u = 0; u < CH; ++u) {
-      a[u] = row[k + u];
-      b[u] = x[k + u];
-      d[u] = y[k + u];
+    for (int u = 0; u < CH; ++u) a[u] = row[k + u];
+#pragma unroll
+    for (int u = 0; u < CH; u += 4) {
+      ld4(x + k + u, b[u], b[u + 1], b[u + 2], b[u + 3]);
+      ld4(y + k + u, d[u], d[u + 1], d[u + 2], d[u + 3]);
     }
 #pragma unroll
     for (int u = 0; u < CH; ++u) row[k + u] = a[u] - (c1 * b[u] + c2 * d[u]);
@@ -352,31 +317,36 @@ __device__ __forceinline__ void row_axpy2(T *row, const T *x, const T *y, T c1, 
   for (; k < N; ++k) row[k] -= c1 * x[k] + c2 * y[k];
 }
 
-// sum_k row[k] x[k] with four accumulators
+// sum_k row[k] x[k] with four accumulators (x 16-byte aligned)
 template <typename T>
 __device__ __forceinline__ T row_dot(const T *row, const T *x, int N) {
   T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
   int k = 0;
   for (; k + 4 <= N; k += 4) {
-    a0 += row[k] * x[k];
-    a1 += row[k + 1] * x[k + 1];
-    a2 += row[k + 2] * x[k + 2];
-    a3 += row[k + 3] * x[k + 3];
+    T x0, x1, x2, x3;
+    ld4(x + k, x0, x1, x2, x3);
+    a0 += row[k] * x0;
+    a1 += row[k + 1] * x1;
+    a2 += row[k + 2] * x2;
+    a3 += row[k + 3] * x3;
   }
   for (; k < N; ++k) a0 += row[k] * x[k];
   return (a0 + a1) + (a2 + a3);
 }
 
 // sum_l x[l] M[l][col] (column of the shared matrix) with four accumulators
+// (x 16-byte aligned)
 template <typename T>
 __device__ __forceinline__ T col_dot(const T *M, int ldm, int col, const T *x, int N) {
   T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
   int l = 0;
   for (; l + 4 <= N; l += 4) {
-    a0 += x[l] * M[l * ldm + col];
-    a1 += x[l + 1] * M[(l + 1) * ldm + col];
-    a2 += x[l + 2] * M[(l + 2) * ldm + col];
-    a3 += x[l + 3] * M[(l + 3) * ldm + col];
+    T x0, x1, x2, x3;
+    ld4(x + l, x0, x1, x2, x3);
+    a0 += x0 * M[l * ldm + col];
+    a1 += x1 * M[(l + 1) * ldm + col];
+    a2 += x2 * M[(l + 2) * ldm + col];
+    a3 += x3 * M[(l + 3) * ldm + col];
   }
   for (; l < N; ++l) a0 += x[l] * M[l * ldm + col];
   return (a0 + a1) + (a2 + a3);
@@ -507,9 +477,10 @@ __device__ T exchange_pf_ratio(const SysDev &S, const WSmem<T> &sm, int n, int m
 // Row n replaced by the row in vA (up-electron hop): with w = R^T M^-1,
 // M'^-1 = M^-1 - M^-1[:,n] (w - e_n)^T / w_n.
 template <typename T>
-__device__ void row_update(const SysDev &S, const WSmem<T> &sm, int n) {
+__device__ void row_update(const SysDev &S, const WSmem<T> &sm, int n, const T *R = nullptr) {
   const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
-  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N;
+  const T *vA = R ? R : sm.vec;
+  T *vB = sm.vec + VMC_MAX_N;
   if (tid < N) vB[tid] = col_dot(sm.minv, ldm, tid, vA, N);
   __syncthreads();
   const T inv = (T)1 / vB[n];
@@ -525,9 +496,10 @@ __device__ void row_update(const SysDev &S, const WSmem<T> &sm, int n) {
 // Column m replaced by the column in vA (down-electron hop): with v = M^-1 C,
 // M'^-1 = M^-1 - (v - e_m) M^-1[m,:] / v_m.
 template <typename T>
-__device__ void col_update(const SysDev &S, const WSmem<T> &sm, int m) {
+__device__ void col_update(const SysDev &S, const WSmem<T> &sm, int m, const T *Cn = nullptr) {
   const int N = S.N, ldm = S.ldm, tid = threadIdx.x;
-  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N;
+  const T *vA = Cn ? Cn : sm.vec;
+  T *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N;
   if (tid < N) {
     vB[tid] = row_dot(sm.minv + tid * ldm, vA, N);
     vC[tid] = sm.minv[m * ldm + tid];
@@ -550,11 +522,11 @@ __device__ void col_update(const SysDev &S, const WSmem<T> &sm, int m) {
 // p = M^-1[:,n], q = M^-1 b, z = M^-1[m,:].
 template <typename T>
 __device__ void exchange_update(const SysDev &S, const WSmem<T> &sm, int n, int m, int j,
-                                const T *K, T det) {
+                                const T *K, T det, const T *wv = nullptr, const T *cv = nullptr) {
   const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
   const T *FT = fTtab<T>(S);
-  T *vA = sm.vec, *vB = sm.vec + VMC_MAX_N, *vC = sm.vec + 2 * VMC_MAX_N,
-    *vD = sm.vec + 3 * VMC_MAX_N;
+  T *vA = sm.vec, *vD = sm.vec + 3 * VMC_MAX_N;
+  const T *vB = wv ? wv : sm.vec + VMC_MAX_N, *vC = cv ? cv : sm.vec + 2 * VMC_MAX_N;
   if (tid < N) {
     vA[tid] = (tid == n) ? (T)0 : vC[tid] - FT[(size_t)j * Ns + sm.ele[tid]];
     vD[tid] = sm.minv[m * ldm + tid];
@@ -655,19 +627,6 @@ __device__ void delayed_hop_update(const SysDev &S, const WSmem<T> &sm, int e, i
 // One Metropolis proposal (Sec. 3.1.2).  Every thread runs it; decisions are
 // uniform across the block.
 // ---------------------------------------------------------------------------
-// An accepted move with |det M'/det M| below SMALL_RATIO amplifies the
-// rounding already in the updated inverse by more than 1/SMALL_RATIO: the
-// walker is then marked due for the next from-scratch rebuild whatever its
-// count of accepted moves (the count is set to RECOMPUTE_NOW, above any
-// recompute interval).
-constexpr double SMALL_RATIO = 1e-3;
-constexpr int RECOMPUTE_NOW = 1 << 30;
-
-struct MoveCounts {
-  long long hop_t = 0, ex_t = 0, hop_a = 0, ex_a = 0;
-  long long meas_hop = 0, meas_ex = 0, samples = 0;
-};
-
 template <typename T>
 __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t walker,
                         unsigned long long &ctr, int &rpos, MoveCounts &mc, int &acc_since,
@@ -762,6 +721,31 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   acc_since = (fabs((double)rpf) < SMALL_RATIO) ? RECOMPUTE_NOW : acc_since + 1;
 }
 
+// Sum of eight per-lane values over the warp by a transposed butterfly
+// (nine shuffles instead of eight separate reductions): on return lane l
+// holds the total of value k = 4 bit4(l) + 2 bit3(l) + bit2(l).
+template <typename T>
+__device__ __forceinline__ T reduce8_transposed(const T *p, int lane) {
+  T q[4], r[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T send = b4 ? p[k] : p[k + 4];
+    const T keep = b4 ? p[k + 4] : p[k];
+    q[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T send = b3 ? q[k] : q[k + 2];
+    const T keep = b3 ? q[k + 2] : q[k];
+    r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  T s = (b2 ? r[1] : r[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r[0] : r[1], 4);
+  s += __shfl_xor_sync(0xffffffffu, s, 2);
+  s += __shfl_xor_sync(0xffffffffu, s, 1);
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // Measurement: E_loc (Eq. MC with A = H) and the O_k row (Sec. 3.3.1)
 // ---------------------------------------------------------------------------
@@ -802,31 +786,6 @@ __device__ T exchange_pf_ratio_warp(const SysDev &S, const WSmem<T> &sm, int n, 
 
 template <typename T>
 __device__ __forceinline__ void acc_add(T *p, T v) { atomicAdd(p, v); }
-
-// Sum of eight per-lane values over the warp by a transposed butterfly
-// (nine shuffles instead of eight separate reductions): on return lane l
-// holds the total of value k = 4 bit4(l) + 2 bit3(l) + bit2(l).
-template <typename T>
-__device__ __forceinline__ T reduce8_transposed(const T *p, int lane) {
-  T q[4], r[2];
-  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const T send = b4 ? p[k] : p[k + 4];
-    const T keep = b4 ? p[k + 4] : p[k];
-    q[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const T send = b3 ? q[k] : q[k + 2];
-    const T keep = b3 ? q[k + 2] : q[k];
-    r[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-  T s = (b2 ? r[1] : r[0]) + __shfl_xor_sync(0xffffffffu, b2 ? r[0] : r[1], 4);
-  s += __shfl_xor_sync(0xffffffffu, s, 2);
-  s += __shfl_xor_sync(0xffffffffu, s, 1);
-  return s;
-}
 
 // a[r] for a warp-varying r < 4 without local-memory indexing
 template <typename V>
@@ -1096,200 +1055,8 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
 }
 
 // ---------------------------------------------------------------------------
-// From-scratch inverse: FP64 Gauss-Jordan with partial pivoting, in place on
-// an N x N row-major matrix (row stride lda) in shared or global memory.
-// Column-parallel elimination (coalesced / bank-conflict free).
-// ---------------------------------------------------------------------------
-struct GJShared {
-  double val[NWARP];
-  double amax[NWARP];
-  int idx[NWARP];
-  int piv;
-  int bad;
-  int sign;
-  double logdet;
-  double pmin, pmax;   // smallest / largest |pivot|
-  double ipiv;
-  double colk[VMC_MAX_N];   // pivot column of the current step (row k zeroed)
-  double rowk[VMC_MAX_N];   // scaled pivot row of the current step (column k zeroed)
-  double apiv[VMC_MAX_N];   // |pivot| of every step
-  double pminw[NWARP];
-};
-
-__device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, GJShared &g) {
-  const int tid = threadIdx.x;
-  if (tid == 0) {
-    g.logdet = 0.0;
-    g.sign = 1;
-    g.bad = 0;
-    g.pmin = 1e300;
-    g.pmax = 0.0;
-  }
-  __syncthreads();
-  for (int k = 0; k < N; ++k) {
-    // (1) copy column k and find the pivot among rows >= k
-    double v = -1.0;
-    int vi = N;
-    for (int i = tid; i < N; i += NT) {
-      const double a = A[(size_t)i * lda + k];
-      g.colk[i] = a;
-      if (i >= k && fabs(a) > v) {
-        v = fabs(a);
-        vi = i;
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
-      if (ov > v || (ov == v && oi < vi)) {
-        v = ov;
-        vi = oi;
-      }
-    }
-    if ((tid & 31) == 0) {
-      g.val[tid >> 5] = v;
-      g.idx[tid >> 5] = vi;
-    }
-    __syncthreads();
-    // (2) one thread: pivot row p, swap it into the pivot column copy, 1/pivot
-    if (tid == 0) {
-      double bv = g.val[0];
-      int bi = g.idx[0];
-      for (int q = 1; q < NWARP; ++q)
-        if (g.val[q] > bv || (g.val[q] == bv && g.idx[q] < bi)) {
-          bv = g.val[q];
-          bi = g.idx[q];
-        }
-      if (!(bv > 0.0) || bi >= N) {
-        g.bad = 1;
-        bi = k;
-      }
-      g.piv = bi;
-      perm[k] = bi;
-      const double piv = g.colk[bi];
-      g.colk[bi] = g.colk[k];
-      g.colk[k] = 0.0;   // row k is scaled, not eliminated
-      g.ipiv = 1.0 / piv;
-      g.apiv[k] = fabs(piv);   // log|det| is summed after the elimination
-      if ((piv < 0.0) != (bi != k)) g.sign = -g.sign;
-    }
-    __syncthreads();
-    if (g.bad) return;
-    const int p = g.piv;
-    const double ipiv = g.ipiv;
-    // (3a) the new column k, one row per thread (from the copy); for every
-    // column c != k: swap rows k and p, scale row k, keep it in rowk.
-    for (int i = tid; i < N; i += NT) A[(size_t)i * lda + k] = (i == k) ? ipiv : -g.colk[i] * ipiv;
-    for (int c = tid; c < N; c += NT) {
-      if (c == k) {
-        g.rowk[c] = 0.0;   // column k is final: the update below leaves it
-        continue;
-      }
-      double rkc = A[(size_t)p * lda + c];
-      if (p != k) A[(size_t)p * lda + c] = A[(size_t)k * lda + c];
-      rkc *= ipiv;
-      A[(size_t)k * lda + c] = rkc;
-      g.rowk[c] = rkc;
-    }
-    __syncthreads();
-    // (3b) A_ic -= colk_i rowk_c over all N x N entries, spread flat over the
-    // threads (whole warps for any N; colk_k = 0 leaves row k), four entries
-    // in flight per thread.
-    {
-      const int qn = NT / N, rn = NT - (NT / N) * N;
-      auto adv = [&](int &ii, int &cc) {
-        ii += qn;
-        cc += rn;
-        if (cc >= N) {
-          cc -= N;
-          ++ii;
-        }
-      };
-      int i = tid / N, c = tid - (tid / N) * N;
-      while (i < N) {
-        int i1 = i, c1 = c;
-        adv(i1, c1);
-        int i2 = i1, c2 = c1;
-        adv(i2, c2);
-        int i3 = i2, c3 = c2;
-        adv(i3, c3);
-        const bool b1 = i1 < N, b2 = i2 < N, b3 = i3 < N;
-        double *q0 = A + (size_t)i * lda + c;
-        double *q1 = A + (size_t)(b1 ? i1 : i) * lda + (b1 ? c1 : c);
-        double *q2 = A + (size_t)(b2 ? i2 : i) * lda + (b2 ? c2 : c);
-        double *q3 = A + (size_t)(b3 ? i3 : i) * lda + (b3 ? c3 : c);
-        double a0 = *q0, a1 = *q1, a2 = *q2, a3 = *q3;
-        a0 -= g.colk[i] * g.rowk[c];
-        if (b1) a1 -= g.colk[i1] * g.rowk[c1];
-        if (b2) a2 -= g.colk[i2] * g.rowk[c2];
-        if (b3) a3 -= g.colk[i3] * g.rowk[c3];
-        *q0 = a0;
-        if (b1) *q1 = a1;
-        if (b2) *q2 = a2;
-        if (b3) *q3 = a3;
-        i = i3;
-        c = c3;
-        adv(i, c);
-      }
-    }
-    __syncthreads();
-  }
-  // log|det M| and the pivot range, off the elimination's serial path
-  {
-    double ls = 0.0, mn = 1e300, mx = 0.0;
-    for (int i = tid; i < N; i += NT) {
-      const double a = g.apiv[i];
-      ls += log(a);
-      mn = fmin(mn, a);
-      mx = fmax(mx, a);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      ls += __shfl_xor_sync(0xffffffffu, ls, o);
-      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    if ((tid & 31) == 0) {
-      g.val[tid >> 5] = ls;
-      g.pminw[tid >> 5] = mn;
-      g.amax[tid >> 5] = mx;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double a = 0.0, b = 1e300, c = 0.0;
-      for (int q = 0; q < NWARP; ++q) {
-        a += g.val[q];
-        b = fmin(b, g.pminw[q]);
-        c = fmax(c, g.amax[q]);
-      }
-      g.logdet = a;
-      g.pmin = b;
-      g.pmax = c;
-    }
-  }
-  for (int k = N - 1; k >= 0; --k) {
-    const int p = perm[k];
-    if (p == k) continue;   // uniform: perm is shared
-    for (int r = tid; r < N; r += NT) {
-      const double t0 = A[(size_t)r * lda + k];
-      A[(size_t)r * lda + k] = A[(size_t)r * lda + p];
-      A[(size_t)r * lda + p] = t0;
-    }
-    __syncthreads();
-  }
-  __syncthreads();
-}
-
-// ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-__device__ void load_sys(SysDev *dst, const SysDev *src) {
-  const int nw = sizeof(SysDev) / sizeof(int);
-  const int *s = (const int *)src;
-  int *d = (int *)dst;
-  for (int k = threadIdx.x; k < nw; k += blockDim.x) d[k] = s[k];
-  __syncthreads();
-}
-
 template <typename T>
 __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2 *work, int n_work,
                                                int *work_ctr, uint2 key, int n_first, int n_samples,
@@ -1462,7 +1229,7 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
                                              int only_due, int due_threshold) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SysDev S;
-  __shared__ GJShared g;
+  __shared__ vmc_gj::GJShared g;
   for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
     __syncthreads();
     const int2 wk = work[item];
@@ -1480,7 +1247,7 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
       A[n * ldm + m] = S.f64[(size_t)ele[n] * Ns + ele[N + m]];
     }
     __syncthreads();
-    gj_invert(A, ldm, N, perm, g);
+    vmc_gj::gj_invert(A, ldm, N, perm, g);
     const size_t nb = minv_bytes(N, ldm, sizeof(T));
     T *dst = (T *)((unsigned char *)S.minv + (size_t)w * nb);
     if (!g.bad) {
@@ -1794,9 +1561,12 @@ __global__ void k_corr_occ(const SysDev *systems, int sys, int *cnt) {
 
 // out[kind][i][j] = walker mean of the local estimators (kinds 0..5 of the
 // header): the ratio planes (n_part sets, summed in order) and the integer
-// counts, scaled.
+// counts, scaled.  With a local_site mask (Kondo local spins: exactly one
+// electron each) a hop c^dag_i c_j with i != j into or out of a marked site
+// leaves the constrained space, where psi = 0: those entries of kinds 0 and 1
+// are 0.  Spin swaps keep every site's occupation and are kept.
 __global__ void k_corr_reduce(const double *part, int n_part, const int *cnt, int Ns, int W,
-                              double *out) {
+                              const signed char *lsite, double *out) {
   const size_t ns2 = (size_t)Ns * Ns;
   const double inv = 1.0 / (double)W;
   for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < ns2;
@@ -1820,6 +1590,7 @@ __global__ void k_corr_reduce(const double *part, int n_part, const int *cnt, in
       d4 = uu - ud;
       d5 = 0.5 * (uu - ud + dd - du);
     }
+    if (lsite && i != j && (lsite[i] | lsite[j])) g0 = g1 = 0.0;
     out[q] = (g0 + d0) * inv;
     out[ns2 + q] = (g1 + d1) * inv;
     out[2 * ns2 + q] = (uu + ud + du + dd) * inv;
@@ -1971,11 +1742,12 @@ cudaError_t vmc_launch_corr_occ(const SysDev *d_sys, int sys, int Ns, int *cnt, 
 }
 
 cudaError_t vmc_launch_corr_reduce(const double *part, int n_part, const int *cnt, int Ns, int W,
-                                   double *out, cudaStream_t st, long long *nl) {
+                                   const signed char *lsite, double *out, cudaStream_t st,
+                                   long long *nl) {
   const size_t ns2 = (size_t)Ns * Ns;
   const size_t blocks = (ns2 + 255) / 256;
   const int grid = (int)(blocks < 4096 ? blocks : 4096);
-  k_corr_reduce<<<grid, 256, 0, st>>>(part, n_part, cnt, Ns, W, out);
+  k_corr_reduce<<<grid, 256, 0, st>>>(part, n_part, cnt, Ns, W, lsite, out);
   ++*nl;
   return cudaGetLastError();
 }

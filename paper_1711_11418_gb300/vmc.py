@@ -82,7 +82,7 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
            "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
            "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all", "vmc_measure_corr",
-           "vmc_test_stall"]
+           "vmc_test_stall", "vmc_set_projection"]
 STALL_NONE, STALL_SAMPLE, STALL_S_BUILD = 0, 1, 2
 
 
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
     L.vmc_get_delay.argtypes = [P]
     L.vmc_tune_delay.argtypes = [P, C.c_int32, _I32P, C.c_int32, _I32P, _F64P]
     L.vmc_test_stall.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
+    L.vmc_set_projection.argtypes = [P, C.c_int32, _I32P, _I8P, _F64P]
     for name in EXPORTS:
         if name not in ("vmc_destroy", "vmc_strerror", "vmc_kernel_launches"):
             getattr(L, name).restype = C.c_int
@@ -266,14 +267,16 @@ class Context:
             raise VmcError(n, "vmc_num_params")
         return n
 
-    def get_samples(self, system=0, rows=None):
+    def get_samples(self, system=0, rows=None, with_O=True):
+        """Stored samples (vmc_get_samples): E [rows] and O [rows, Np] (None
+        when with_O is False: only E is copied)."""
         st = self.measure(system)
         rows = st["n_samples"] if rows is None else rows
         Np = self.num_params(system)
         E = np.zeros(rows)
-        O = np.zeros((rows, Np))
-        _check(self._L.vmc_get_samples(self._h, system, _p(E, _F64P), _p(O, _F64P)),
-               "vmc_get_samples")
+        O = np.zeros((rows, Np)) if with_O else None
+        _check(self._L.vmc_get_samples(self._h, system, _p(E, _F64P),
+                                       _p(O, _F64P) if with_O else None), "vmc_get_samples")
         return E, O
 
     def set_samples(self, E, O, system=0):
@@ -335,6 +338,17 @@ class Context:
 
     def kernel_launches(self):
         return int(self._L.vmc_kernel_launches(self._h))
+
+    def set_projection(self, perm, sign, weight):
+        """Quantum-number projection (vmc_set_projection): perm, sign [n_ops, Ns]
+        (T_g c^dag_r T_g^-1 = sign[g, r] c^dag_{perm[g, r]}), real weights
+        [n_ops]; empty arrays remove it."""
+        perm = np.ascontiguousarray(perm, np.int32)
+        sign = np.ascontiguousarray(sign, np.int8)
+        weight = np.ascontiguousarray(weight, np.float64)
+        _check(self._L.vmc_set_projection(self._h, int(weight.size), _p(perm, _I32P),
+                                          _p(sign, _I8P), _p(weight, _F64P)),
+               "vmc_set_projection")
 
     def test_stall(self, target, system=0, walker=0):
         """Failure-detection test hook (vmc_test_stall): arm one bounded wait

@@ -41,9 +41,12 @@ def configs(p, W, seed):
 
 
 def oracle_call(wf, ele, ctr, p, walkers):
-    """One vmc_sample(1, 2, 1) of the given walkers by the oracle."""
-    ref = run_sampling(wf, ele[walkers], 31, 0, 1, 2, 1, p.p_exchange, counters=ctr[walkers])
-    return ref["ele"], ref["counters"], ref["E"]
+    """One vmc_sample(1, 2, 1) by the oracle, every walker on its own Philox
+    stream (walker index = row); the rows of `walkers` are returned."""
+    ref = run_sampling(wf, ele, 31, 0, 1, 2, 1, p.p_exchange, counters=ctr)
+    W = len(ele)
+    return (ref["ele"][walkers], ref["counters"][walkers],
+            ref["E"].reshape(W, 2)[walkers].ravel())
 
 
 def test_sample_timeout_skips_one_walker_and_the_chains_continue(vmc):

@@ -185,3 +185,33 @@ def test_combined_momentum_and_point_group_projection():
     assert np.linalg.norm(v) > 1e-3
     for op, _ in tr + pts:
         np.testing.assert_allclose(op_matrix(op, st, p.Ns) @ v, v, atol=1e-12)
+
+
+@pytest.mark.parametrize("m", ["K0", "Kpi"])
+def test_projected_log_derivatives_match_finite_differences(m):
+    """O_k of the projected state (Sec. 3.3.1 applied to psi = P <x|L|phi>)
+    against central differences of ln|psi(x)| with perturbed parameters."""
+    p = chain6()
+    K = (0.0, 0.0) if m == "K0" else (math.pi, 0.0)
+    ops = momentum_weights(translations(p.lat), K)
+    ops = [(op, complex(w).real) for op, w in ops]
+    wf = Wavefunction(p)
+    pw = ProjectedWavefunction(wf, ops)
+    h = 1e-6
+    checked = 0
+    for n in basis(p.Ns, 2, 2)[::7]:
+        s0, _ = pw.amplitude_slog(n)
+        if s0 == 0.0:
+            continue
+        a = pw.log_derivatives(n)
+        fd = np.zeros_like(a)
+        for k in range(a.size):
+            pp, pm = p.params.copy(), p.params.copy()
+            pp[k] += h
+            pm[k] -= h
+            lp = ProjectedWavefunction(Wavefunction(p, pp), ops).amplitude_slog(n)[1]
+            lm = ProjectedWavefunction(Wavefunction(p, pm), ops).amplitude_slog(n)[1]
+            fd[k] = (lp - lm) / (2 * h)
+        np.testing.assert_allclose(a, fd, rtol=1e-5, atol=1e-6)
+        checked += 1
+    assert checked >= 5
