@@ -28,6 +28,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -64,13 +66,21 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--walkers", type=int, default=4096)
     ap.add_argument("--samples", type=int, default=4)
-    ap.add_argument("--recompute", type=int, default=256)
+    ap.add_argument("--recompute", type=int, default=64)
     ap.add_argument("--equil", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-corr", action="store_true")
+    ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--stat-samples", type=int, default=16)
+    ap.add_argument("--learned", action="store_true",
+                    help="train the plain and the Pfaffian x MLP state at the learned-part "
+                         "size and print their energies (one JSON line) instead of the bench")
+    ap.add_argument("--learned-steps", type=int, default=60)
+    ap.add_argument("--learned-eval", type=int, default=6)
+    ap.add_argument("--sweep-only", type=int, default=8)
     return ap.parse_args()
 
 
@@ -205,6 +215,137 @@ def cpu_baseline(pool, cores, seconds):
             "wall_s": round(wall, 2)}
 
 
+def _oracle_config_worker(args):
+    """Oracle proposal and measurement rates on one configured workload (one
+    chain per core): `seconds` of proposals, then `n_meas` measurements."""
+    name, wid, seconds, n_meas = args
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    sys.path.insert(0, ROOT)
+    from paper_1711_11418_gb300 import inputs
+    from oracle import fock
+    from oracle.hamiltonian import local_energy
+    from oracle.sampler import Chain
+    from oracle.wavefunction import Wavefunction
+    p = inputs.ring8_hubbard() if name == "ring8" else inputs.square8_hubbard()
+    wf = Wavefunction(p)
+    ele = inputs.initial_configs(p.Ns, p.Ne, 1, False, 7000 + wid)[0]
+    ch = Chain(wf, ele, seed=1, system=0, walker=wid, p_exchange=p.p_exchange)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < seconds:
+        ch.propose()
+        k += 1
+    t1 = time.perf_counter()
+    for _ in range(n_meas):
+        n = fock.from_labels(ch.ele, p.Ns)
+        local_energy(wf, n)
+        wf.log_derivatives(n)
+    return k, t1 - t0, n_meas, time.perf_counter() - t1
+
+
+def cpu_baseline_configs(pool, cores, seconds=4.0):
+    """The oracle on the 8-site ring (C1: 64 walkers x 200 samples x 10 sweeps
+    per SR step) and the 8x8 lattice (C2: 1024 walkers x 4 samples x 1 sweep):
+    proposal and measurement rates on all cores from a bounded sample, and
+    the seconds one SR step's sampling would take at those rates (SR solve
+    not included: N_p = 19 and 271)."""
+    out = {}
+    for name, W, S, sweeps, Ne, n_meas in (("ring8", 64, 200, 10, 8, 20),
+                                            ("square8", 1024, 4, 1, 64, 2)):
+        res = pool.map(_oracle_config_worker, [(name, w, seconds, n_meas) for w in range(cores)])
+        pr = sum(r[0] for r in res) / max(r[1] for r in res)
+        mr = sum(r[2] for r in res) / max(r[3] for r in res)
+        props = W * S * sweeps * Ne
+        out[name] = {"proposals_per_s": pr, "measurements_per_s": mr, "cores": cores,
+                     "seconds_per_sr_step_est": props / pr + W * S / mr,
+                     "sample": f"{cores} chains x {seconds:.0f} s of proposals, then "
+                               f"{n_meas} measurements each (E_loc and O_k by Pfaffians); "
+                               f"the SR step's sampling ({W} walkers x {S} samples x {sweeps} "
+                               f"sweeps of {Ne} proposals) extrapolated from these rates"}
+    return out
+
+
+def other_workloads(vmc, torch, stream, steps=5):
+    """The other configured workloads, each timed on the device (CUDA events
+    on the stream) after the headline bench:
+      ring8   C1: 8-site ring, FP64, 64 walkers x 200 samples x 10 sweeps and
+              one FP64 Cholesky SR step per step;
+      square8 C2: 8x8, FP64, 1024 walkers x 4 samples x 1 sweep, FP64 Cholesky;
+      batch64 C3: 64 independent Hubbard systems (L = 4..16) x 64 walkers, mixed
+              form, FP64 recompute every 64 accepted moves, 4 samples, and
+              one SR step of every system (vmc_sr_step_all, mixed solve);
+      j1j2    C4: 16x16 J1-J2, full f (N_p = 65,536), 8192 samples: one dense
+              S build by the split-BF16 tensor-core kernel."""
+    from paper_1711_11418_gb300 import inputs
+    res = {}
+
+    def timed(ctx, step, n):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0 = sum(ctx.measure(k)["n_proposals"] for k in range(len(ctx.problems)))
+        e0.record(stream)
+        for _ in range(n):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        p1 = sum(ctx.measure(k)["n_proposals"] for k in range(len(ctx.problems)))
+        ms = e0.elapsed_time(e1)
+        return {"ms_per_step": ms / n, "proposals_per_s": (p1 - p0) / (ms * 1e-3), "steps": n}
+
+    sr64 = dict(dtau=0.05, shift_rel=1e-3, shift_abs=0.0, solver=vmc.CHOLESKY)
+    for name, prob, W, S, sweeps in (("ring8", inputs.ring8_hubbard(), 64, 200, 10),
+                                     ("square8", inputs.square8_hubbard(), 1024, 4, 1)):
+        ctx = vmc.Context(prob, W, seed=11, precision=vmc.FP64, max_samples=S,
+                          stream=stream.cuda_stream)
+        ctx.sample(10, 0, 0)
+
+        def step(ctx=ctx, S=S, sweeps=sweeps):
+            ctx.sample(0, S, sweeps)
+            ctx.sr_step(**sr64)
+        step()
+        res[name] = timed(ctx, step, steps) | {
+            "walkers": W, "samples_per_walker": S, "sweeps_between": sweeps, "dtype": "f64",
+            "energy_per_site": ctx.measure()["energy"] / prob.Ns}
+        ctx.close()
+    probs = inputs.batched_hubbard()
+    ctx = vmc.Context(probs, 64, seed=5, precision=vmc.MIXED, max_samples=4, recompute_every=64,
+                      stream=stream.cuda_stream)
+    ctx.sample(10, 0, 0)
+
+    def step_b():
+        ctx.sample(0, 4, 1)
+        ctx.sr_step_all(0.05, 1e-3, 0.0, solver=vmc.MIXED_IR, cg_eps=1e-12)
+    step_b()
+    res["batch64"] = timed(ctx, step_b, steps) | {
+        "systems": len(probs), "walkers_per_system": 64, "samples_per_walker": 4,
+        "sizes_L": sorted({int(round(p.Ns ** 0.5)) for p in probs}), "dtype": "f32+f64"}
+    ctx.close()
+    prob = inputs.j1j2_heisenberg()
+    ctx = vmc.Context(prob, 1024, seed=3, precision=vmc.MIXED, max_samples=8,
+                      stream=stream.cuda_stream)
+    ctx.sample(2, 8, 1)
+    ctx.enable_timing(True)
+    ctx.kernel_times()
+    rep = ctx.sr_step(0.05, 1e-4, 0.0, solver=vmc.CG_DENSE, cg_eps=1e-3, cg_kmax=1)
+    ms = ctx.kernel_times()["sr_gemm"][0]
+    rows, Np = 1024 * 8, prob.Np
+    fl = float(rows) * Np * Np                       # N_MC N_p^2 (symmetric product)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    pk = peaks.get("bf16_tflops", 1900.0)
+    res["j1j2"] = {"rows": rows, "Np": Np, "s_build_ms": ms,
+                   "s_kernel": vmc.S_KERNELS[rep["s_kernel"]],
+                   "tflops_method": fl / (ms * 1e-3) / 1e12,
+                   "tflops_three_products": 3 * fl / (ms * 1e-3) / 1e12,
+                   "frac_method": fl / (ms * 1e-3) / 1e12 / pk,
+                   "frac_three_products": 3 * fl / (ms * 1e-3) / 1e12 / pk,
+                   "peak_tflops": pk, "peak_source": "measured bf16 burst" if peaks else "fallback",
+                   "flops_rule": "method: N_MC N_p^2 (the symmetric product once); three "
+                                 "products: split-BF16 hi.hi + hi.lo + lo.hi"}
+    ctx.close()
+    return res
+
+
 def run_reference(args):
     rank, _, world = dist_info()
     if rank != 0:
@@ -282,6 +423,57 @@ def flops_of(d, N, precision):
     return main, rec
 
 
+def sweep_bytes(d, N, esize):
+    """Algorithmic bytes of the update sweep (A3-A6) from its counters: the
+    block M^-1 read and written once per accepted move (2 esize N^2) and one
+    block column plus one gathered f row per proposal (2 esize N)."""
+    return 2.0 * esize * N * N * d["n_accepted"] + 2.0 * esize * N * d["n_proposals"]
+
+
+def energy_statistics(vmc, prob, params, ele0, walkers, samples, recompute, stream):
+    """Statistical half of "equal energy accuracy": the plain FP64 and the
+    mixed form sample the same wave function (fixed parameters, no SR in
+    between) from the same configurations with the same proposal streams,
+    `samples` measurements each after one sweep.  Each form's energy per site
+    carries a standard error from its per-walker means (walkers are
+    independent chains).  Walkers whose two chains end in the same
+    configuration made the same decisions throughout, so their rows compare
+    the two precisions on identical configurations at every sample, i.e. at
+    several points between the mixed form's FP64 rebuilds."""
+    Ns = prob.Ns
+    E, ele = {}, {}
+    for name, prec in (("fp64", vmc.FP64), ("mixed", vmc.MIXED)):
+        ctx = vmc.Context(prob.copy_with(params=params), walkers, seed=777, precision=prec,
+                          max_samples=samples,
+                          recompute_every=recompute if prec == vmc.MIXED else -1, stream=stream)
+        ctx.set_configs(ele0)
+        ctx.sample(0, samples, 1)
+        E[name] = ctx.get_samples(with_O=False)[0].reshape(walkers, samples) / Ns
+        ele[name] = ctx.get_configs()[0]
+        ctx.close()
+    wm = {k: v.mean(axis=1) for k, v in E.items()}
+    e = {k: float(v.mean()) for k, v in wm.items()}
+    se = {k: float(v.std(ddof=1) / math.sqrt(walkers)) for k, v in wm.items()}
+    sig = math.sqrt(se["fp64"] ** 2 + se["mixed"] ** 2)
+    diff = e["mixed"] - e["fp64"]
+    paired = wm["mixed"] - wm["fp64"]
+    same = (ele["fp64"] == ele["mixed"]).all(axis=1)
+    d = abs(E["mixed"] - E["fp64"])[same]
+    return {"fp64_energy_per_site": e["fp64"], "mixed_energy_per_site": e["mixed"],
+            "stderr_fp64": se["fp64"], "stderr_mixed": se["mixed"], "sigma_combined": sig,
+            "difference": diff, "within_3sigma": abs(diff) <= 3 * sig,
+            "within_1e-4": abs(diff) <= 1e-4,
+            "paired_stderr": float(paired.std(ddof=1) / math.sqrt(walkers)),
+            "walkers": walkers, "samples_per_walker": samples, "sweeps_between": 1,
+            "mixed_recompute_every_accepted": recompute,
+            "walkers_same_chain": int(same.sum()),
+            "same_chain_dE_per_site_max_by_sample": [float(x) for x in d.max(axis=0)] if d.size else None,
+            "same_chain_dE_per_site_p99": float(np.percentile(d, 99)) if d.size else None,
+            "same_chain_entries_over_1e-4": int((d > 1e-4).sum()),
+            "how": "both forms, same parameters, same starting configurations and proposal "
+                   "streams, no SR in between; standard errors from per-walker means"}
+
+
 def delta(a, b):
     return {k: b[k] - a[k] for k in b if isinstance(b[k], int)}
 
@@ -292,12 +484,10 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
                       max_samples=S, recompute_every=args.recompute if precision == vmc.MIXED else -1,
                       stream=stream.cuda_stream)
     ctx.sample(args.equil, 0, 0)                        # equilibration (untimed)
-    delay = None
-    if precision == vmc.MIXED:
-        # delayed-update depth by the autotuner, timed on the step's launch
-        # shape (one sweep and one measurement; these are warm-up sweeps)
-        delay, delay_ms = ctx.tune_delay(sweeps=1, candidates=(1, 2, 4, 8))
-        delay = {"chosen": delay, "ms_per_sweep": delay_ms}
+    # Immediate updates: they keep the mixed form's double-float inverse (the
+    # delayed form keeps FP32 words only, so it is not used at the accuracy
+    # this bench checks).
+    delay = {"chosen": 1, "why": "immediate updates keep the double-float inverse"}
     # plain form: FP64 Cholesky; mixed form: FP64 iterative refinement on an
     # FP32 inverse (FP64 Cholesky if it does not reach the residual target)
     sr = dict(dtau=0.05, shift_rel=1e-3, shift_abs=0.0,
@@ -341,9 +531,11 @@ def run_arm(vmc, prob, args, precision, stream, torch, world):
                  refinement_steps_max=max(r["cg_iters"] for r in timed),
                  fallbacks=sum(r["fallback"] for r in timed),
                  rel_residual_max=max(r["rel_residual"] for r in timed))
+    grid, per_sm, smem = ctx.sweep_launch()
     return ctx, dict(ms=ms, stats=d, kt=kt, launches=launches, clocks=clk,
                      energy=statistics.fmean(energies), last=st1, solve=solve,
-                     props_all=props_all, sr=sr, delay=delay)
+                     props_all=props_all, sr=sr, delay=delay,
+                     launch={"grid": grid, "ctas_per_sm": per_sm, "smem_bytes": smem})
 
 
 def run_ours(args):
@@ -383,6 +575,19 @@ def run_ours(args):
         dE_max = float(dw.max())
         dE_p99 = float(sorted(dw)[int(0.99 * (len(dw) - 1))])
         n_over = int((dw > 1e-4).sum())
+        stat = None
+        if not args.no_fp64:
+            stat = energy_statistics(vmc, prob, params, ele, args.walkers, args.stat_samples,
+                                     args.recompute, stream.cuda_stream)
+        # The update sweep alone (A3-A6: proposals, ratios, accepted updates;
+        # no measurement): sweep-only launches of the mixed context, timed by
+        # the library's CUDA events on the stream, after the timed region.
+        ctx.kernel_times()
+        sw0 = ctx.measure()
+        for _ in range(args.sweep_only):
+            ctx.sample(1, 0, 0)
+        kt_sw = ctx.kernel_times()
+        sw = delta(sw0, ctx.measure())
         # End to end: parameters from pinned host memory, energy and parameters back
         e2e = None
         if not args.no_e2e:
@@ -413,6 +618,7 @@ def run_ours(args):
             all_ms = statistics.median(r[1] for r in runs)
             corr = {"k_ms": k_ms, "all_ms": all_ms}
         ctx.close()
+        others = None if args.no_others else other_workloads(vmc, torch, stream)
 
     def summarize(r):
         d = r["stats"]
@@ -424,7 +630,7 @@ def run_ours(args):
                 "sr_ms_per_step": r["kt"]["sr"][0] / args.steps,
                 "acceptance": d["n_accepted"] / max(d["n_proposals"], 1),
                 "energy_per_site": r["energy"] / prob.Ns, "recomputes": d["n_recomputes"],
-                "sr_solve": r["solve"], "delay_tuner": r["delay"]}
+                "sr_solve": r["solve"], "delay_tuner": r["delay"], "sweep_launch": r["launch"]}
 
     peaks = measured_alu_peaks(torch)
     sm = summarize(mixed)
@@ -440,15 +646,34 @@ def run_ours(args):
     f32, f64rec = flops_of(mixed["stats"], N, "mixed")
     sweep_ms, sweep_n = mixed["kt"]["sweep"]
     t_launch = sweep_ms * 1e-3 / max(sweep_n, 1)
+    # Survey roofline of the update sweep: algorithmic bytes (the FP32 block
+    # streamed per accepted move, a column and an f row per proposal) per
+    # launch / launch time, against the measured HBM copy bandwidth.  The
+    # launch also measures E_loc and O_k (not counted in these bytes).
+    b_launch = sweep_bytes(mixed["stats"], N, 4) / max(sweep_n, 1)
+    ach_b = b_launch / t_launch / 1e9
     ach = f32 / max(sweep_n, 1) / t_launch / 1e12
-    sweep_gbs = TRAFFIC_SWEEP_4096 * scale / t_launch / 1e9
-    roof_sweep = {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                  "frac": ach / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_SWEEP_4096 * scale,
+    roof_sweep = {"bound": "hbm", "achieved": ach_b, "peak": hbm, "unit": "GB/s",
+                  "frac": ach_b / hbm, "traffic": None,
                   "kernel": "k_sample<float> (sweep + measurement)",
-                  "ms_in_timed_region": sweep_ms,
-                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                  "hbm": {"achieved_gbs": sweep_gbs, "peak_gbs": hbm, "frac": sweep_gbs / hbm,
-                          "peak_source": hbm_src}}
+                  "algorithmic_bytes_per_launch": b_launch,
+                  "bytes_rule": "2 x 4 x N^2 per accepted move + 2 x 4 x N per proposal (N = 112)",
+                  "ms_in_timed_region": sweep_ms, "ms_per_launch": t_launch * 1e3,
+                  "peak_source": hbm_src,
+                  "alu": {"achieved_tflops": ach, "peak_tflops": FP32_PEAK_TFLOPS,
+                          "frac": ach / FP32_PEAK_TFLOPS,
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}}
+    sw_ms, sw_n = kt_sw["sweep"]
+    t_sw = sw_ms * 1e-3 / max(sw_n, 1)
+    b_sw = sweep_bytes(sw, N, 4) / max(sw_n, 1)
+    roof_sweep_only = {"bound": "hbm", "achieved": b_sw / t_sw / 1e9, "peak": hbm, "unit": "GB/s",
+                       "frac": b_sw / t_sw / 1e9 / hbm, "kernel": "k_sample<float>, sweeps only",
+                       "launches": sw_n, "ms_per_launch": t_sw * 1e3,
+                       "algorithmic_bytes_per_launch": b_sw,
+                       "acceptance": sw["n_accepted"] / max(sw["n_proposals"], 1),
+                       "proposals_per_s": sw["n_proposals"] / max(sw_ms * 1e-3, 1e-12),
+                       "what": "the update sweep alone (A3-A6), one sweep per launch, "
+                               "timed after the timed region on the same context"}
     init_ms, _ = mixed["kt"]["init"]
     n_inv = args.steps * args.walkers + mixed["stats"]["n_recomputes"]
     ach_init = 2.0 * N ** 3 * n_inv / max(init_ms * 1e-3, 1e-12) / 1e12
@@ -491,16 +716,20 @@ def run_ours(args):
                          "same_configs_dE_per_site_p99": dE_p99,
                          "walkers_over_tolerance": n_over, "walkers": args.walkers,
                          "tolerance": 1e-4,
-                         "tolerance_applies_to": "the energy estimate (walker mean)"},
+                         "tolerance_applies_to": "the energy estimate (walker mean)",
+                         "statistical": stat},
         "roofline": roof,
         "roofline_second": roof2,
+        "roofline_sweep_only": roof_sweep_only,
         "pair_correlations": pair_corr,
+        "other_workloads": others,
         "clocks": mixed["clocks"],
         "gpu_launches": mixed["launches"],
         "e2e": e2e,
     }
     if pool is not None:
         line["cpu_baseline"] = cpu_baseline(pool, cores, args.cpu_seconds)
+        line["cpu_baseline_other"] = cpu_baseline_configs(pool, cores)
         pool.close()
     if rank == 0:
         print(json.dumps(line))
@@ -508,8 +737,66 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_learned(args):
+    """The learned part at its configured size: 16x16 Hubbard, U/t = 8,
+    Ne = 224, the Gutzwiller-Jastrow-Pfaffian state times an MLP correlation
+    factor (512 occupations -> 1024 tanh units -> 1, BF16 weights in the
+    sweep, N(0, 0.01^2) initial weights), 4096 walkers, SR over all 527,406
+    parameters by SR-CG (S never formed, FP32 sample matrix, FP64 CG); the
+    plain state gets the same walkers, samples per step, steps and solver.
+    Afterwards both are sampled with fixed parameters and their energies per
+    site are reported with standard errors from per-walker means."""
+    import torch
+    from paper_1711_11418_gb300 import build, inputs, vmc
+    build.build()
+    torch.cuda.set_device(0)
+    W, S = args.walkers, args.samples
+    sr = dict(dtau=0.05, shift_rel=1e-3, shift_abs=1e-4, solver=vmc.CG, cg_eps=1e-4,
+              cg_kmax=200)
+    probs = {"plain": inputs.square16_hubbard(),
+             "mlp": inputs.square16_hubbard_mlp(hidden=1024)}
+    out = {}
+    for name, prob in probs.items():
+        t0 = time.perf_counter()
+        ctx = vmc.Context(prob, W, seed=2024, precision=vmc.MIXED, max_samples=S,
+                          recompute_every=args.recompute)
+        ctx.sample(args.equil, 0, 0)
+        traj, iters = [], []
+        for _ in range(args.learned_steps):
+            ctx.sample(0, S, 1)
+            rep = ctx.sr_step(**sr)
+            traj.append(rep["energy"] / prob.Ns)
+            iters.append(rep["cg_iters"])
+        t_train = time.perf_counter() - t0
+        wm = []
+        for _ in range(args.learned_eval):
+            ctx.sample(0, S, 1)
+            wm.append(ctx.get_samples(with_O=False)[0].reshape(W, S).mean(axis=1))
+        wm = np.mean(wm, axis=0) / prob.Ns
+        ctx.close()
+        out[name] = {"energy_per_site": float(wm.mean()),
+                     "stderr": float(wm.std(ddof=1) / math.sqrt(W)),
+                     "Np": prob.Np, "train_seconds": round(t_train, 2),
+                     "cg_iterations_mean": float(np.mean(iters)),
+                     "trajectory_every_10_steps": [round(x, 6) for x in traj[::10]]}
+    gain = out["plain"]["energy_per_site"] - out["mlp"]["energy_per_site"]
+    sig = math.hypot(out["plain"]["stderr"], out["mlp"]["stderr"])
+    print(json.dumps({"what": "learned part: plain Gutzwiller-Jastrow-Pfaffian vs x MLP "
+                              "correlation factor, same sample budget",
+                      "workload": "hubbard_16x16_U8_Ne224_apbc, MLP 512->1024->1",
+                      "walkers": W, "samples_per_step": W * S, "sr_steps": args.learned_steps,
+                      "sr": {k: v for k, v in sr.items() if k != "solver"} | {"solver": "sr_cg"},
+                      "eval_samples_per_walker": args.learned_eval * S,
+                      "plain": out["plain"], "mlp": out["mlp"],
+                      "gain_per_site": gain, "gain_sigma": sig,
+                      "gain_significant_3sigma": bool(gain > 3 * sig)}))
+
+
 def main():
     args = parse()
+    if args.learned:
+        run_learned(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

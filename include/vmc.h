@@ -112,7 +112,7 @@ typedef struct {
                                     vmc_set_delay */
   int32_t recompute_every;       /* FP64 from-scratch inverse inside the sweep once a
                                     walker has this many accepted moves since the
-                                    last one; 0 = default (mixed: 256, FP64: never),
+                                    last one; 0 = default (mixed: 64, FP64: never),
                                     -1 = never */
   int32_t max_samples;           /* sample rows kept per walker (>= 1) */
   void *stream;                  /* cudaStream_t; NULL = default stream */
@@ -295,7 +295,8 @@ int vmc_num_params(vmc_ctx *ctx, int32_t system);
 int vmc_eval_ratios(vmc_ctx *ctx, int32_t system, int32_t walker,
                     int32_t n_moves, const int32_t *moves, double *ratios);
 
-/* Walker inverse check hook: M^-1 (N x N, row-major, FP64 copy) of walker w,
+/* Walker inverse check hook: M^-1 (N x N, row-major, FP64 copy; in the mixed
+ * form the double-float value hi + lo the sweep keeps) of walker w,
  * M_nm = f(r_n,up, r_m,dn); log|det M| and its sign from the last
  * from-scratch factorisation. */
 int vmc_get_inverse(vmc_ctx *ctx, int32_t system, int32_t walker,
@@ -328,8 +329,43 @@ int vmc_get_inverse(vmc_ctx *ctx, int32_t system, int32_t walker,
 int vmc_set_projection(vmc_ctx *ctx, int32_t n_ops, const int32_t *perm, const int8_t *sign,
                        const double *weight);
 
+/* First-step power-Lanczos (Sec. 3.4): for every walker's CURRENT
+ * configuration x of one system, the local values
+ *   F1(x) = F(x, H) = <x|H|psi>/<x|psi>  (the local energy) and
+ *   F2(x) = F(x, H^2) = sum_x' <x|H|x'> (H psi)(x') / psi(x),
+ * every amplitude ratio taken from x (psi(x'')/psi(x), two moves away at
+ * most; nothing divides by psi(x')), and their walker means
+ *   moments = [h1, h2(11), h2(20), h3(12)] = [<F1>, <F1^2>, <F2>, <F1 F2>].
+ * Averaging the moments of calls between vmc_sample calls gives the Monte
+ * Carlo estimates of Sec. 3.4; vmc_lanczos_alpha then gives alpha_1.
+ * F1, F2: NULL or host [n_walkers]; moments: host [4].  The Pfaffian ratios
+ * come from Green-function tables of each configuration (FP64, or FP32 from
+ * the FP32 words of the mixed form's inverse); sums in FP64.  Device scratch
+ * (about 8 (2 Ns N + Ns^2) bytes per resident CTA) is kept by the context.
+ * Errors: VMC_EINVAL (bad system, NULL moments, a context with the MLP
+ * factor, Heisenberg J terms, or a projection: not provided), VMC_ENOMEM,
+ * VMC_ESINGULAR, VMC_ECUDA. */
+int vmc_lanczos_moments(vmc_ctx *ctx, int32_t system, double *F1, double *F2, double *moments);
+
+/* alpha_1 of Sec. 3.4 from the moments [h1, h2(11), h2(20), h3(12)]:
+ * E_1(alpha) = (h1 + alpha (h2(20) + h2(11)) + alpha^2 h3(12))
+ *            / (1 + 2 alpha h1 + alpha^2 h2(11)),
+ * alpha_1 the root of dE_1/dalpha = 0 (a quadratic) with the lower E_1; E1
+ * (may be NULL) receives E_1(alpha_1).  Host arithmetic only.  Errors:
+ * VMC_EINVAL (NULL pointers), VMC_ENUMERIC (no real stationary point). */
+int vmc_lanczos_alpha(const double *moments, double *alpha, double *E1);
+
 /* Number of kernels this context has launched since creation. */
 int64_t vmc_kernel_launches(vmc_ctx *ctx);
+
+/* Launch configuration of the sweep/measurement kernel (no counterpart in the
+ * paper): the persistent grid (CTAs, one walker at a time each), the CTAs that
+ * fit on one SM at the kernel's shared-memory size (cudaOccupancy), and that
+ * size in bytes (dynamic part: the walker's M^-1 block, plus its low words in
+ * the mixed form); of the projected sweep kernel once vmc_set_projection has
+ * armed operations.  Any output pointer may be NULL.
+ * Errors: VMC_EINVAL (NULL ctx). */
+int vmc_sweep_launch(vmc_ctx *ctx, int32_t *grid, int32_t *ctas_per_sm, int64_t *smem_bytes);
 
 /* Failure-detection test hook (no counterpart in the paper; off unless
  * called).  Arms, for one call, a device wait that cannot complete: the

@@ -61,6 +61,8 @@ struct vmc_ctx {
   int grid_proj = 0;
   void *corr_buf = nullptr;   // vmc_measure_corr scratch (grown on demand)
   size_t corr_bytes = 0;
+  void *lz_buf = nullptr;     // vmc_lanczos_moments scratch (grown on demand)
+  size_t lz_bytes = 0;
   // timing (CUDA events on st): 0 sweep, 1 init, 2 SR step, 3 S GEMM
   bool timing = false;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[4];
@@ -89,6 +91,9 @@ void ctx_free(vmc_ctx *c) {
   if (c->corr_buf) cudaFree(c->corr_buf);
   c->corr_buf = nullptr;
   c->corr_bytes = 0;
+  if (c->lz_buf) cudaFree(c->lz_buf);
+  c->lz_buf = nullptr;
+  c->lz_bytes = 0;
   for (void *p : c->allocs) cudaFree(p);
   c->allocs.clear();
 }
@@ -310,13 +315,23 @@ int set_delay_impl(vmc_ctx *c, int k) {
   size_t smem = 0;
   for (auto &s : c->sys)
     smem = std::max(smem, vmc_walker_smem(c->precision == VMC_FP64 ? 0 : 1, s.N, s.Ns, s.Np,
-                                          s.dev.n_hidden, kd, nullptr));
+                                          s.dev.n_hidden, kd, nullptr,
+                                          c->precision == VMC_MIXED));
   if (smem > c->smem_cap) return VMC_EINVAL;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int occ = vmc_sample_occupancy(c->precision, smem);
   if (occ < 1) return VMC_EINVAL;
+  // Delayed updates keep FP32 words only: entering them, the mixed form's low
+  // words are zeroed so that hi + lo stays the inverse when immediate
+  // (double-float) updates resume.
+  if (c->precision == VMC_MIXED && c->delay_k <= 1 && k > 1)
+    for (auto &s : c->sys)
+      if (s.dev.minv_lo) {
+        const size_t mb = ((size_t)s.N * s.ldm * 4 + 127) / 128 * 128;
+        CKC(cudaMemsetAsync(s.dev.minv_lo, 0, (size_t)s.W * mb, c->st));
+      }
   for (auto &s : c->sys) s.dev.delay_k = kd;
   c->smem_sample = smem;
   c->grid_sample = std::min(c->n_work, nsm * occ);
@@ -337,7 +352,8 @@ int ensure_init(vmc_ctx *c, bool redraw_illcond = false) {
       CKC(vmc_launch_proj_build(c->d_sys, c->d_work, c->n_work, c->sys[0].dev.n_ops, c->precision,
                                 0, 0, c->smem_init, c->st, &c->n_launch));
     else
-      CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 0, 0, c->smem_init, c->st,
+      CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->d_work_ctr + 1, c->precision, 0, 0,
+                          c->smem_init, c->st,
                           &c->n_launch));
   }
   int bad = 0;
@@ -639,6 +655,8 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dalloc(c, &d.ele, sizeof(int) * W * s.Ne))) return fail(rc);
     if ((rc = dalloc(c, &d.occ, sizeof(int) * W * 2 * Ns))) return fail(rc);
     if ((rc = dalloc(c, &d.minv, mb * W))) return fail(rc);
+    d.minv_lo = nullptr;
+    if (o->precision == VMC_MIXED && (rc = dalloc(c, &d.minv_lo, mb * W))) return fail(rc);
     if ((rc = dalloc(c, &d.jf, (size_t)esize * W * Ns))) return fail(rc);
     if ((rc = dupload(c, &d.ctr, (const unsigned long long *)nullptr, W))) return fail(rc);
     if ((rc = dupload(c, &d.logdet, (const double *)nullptr, W))) return fail(rc);
@@ -654,8 +672,8 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dupload(c, &d.E, (const double *)nullptr, rows_cap))) return fail(rc);
     if ((rc = dalloc(c, &d.O, (size_t)esize * rows_cap * s.ldO))) return fail(rc);
     int acc_len = 0;
-    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, H, 0, &acc_len));
-    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, H, 0, &acc_len));
+    smem64 = std::max(smem64, vmc_walker_smem(0, s.N, s.Ns, s.Np, H, 0, &acc_len, 0));
+    smem32 = std::max(smem32, vmc_walker_smem(1, s.N, s.Ns, s.Np, H, 0, &acc_len, 1));
     d.acc_len = acc_len;
     c->smem_init = std::max(c->smem_init, vmc_init_smem(s.N, s.Ns));
     if (vmc_launch_expand(&d, c->st, &c->n_launch) != cudaSuccess) return fail(VMC_ECUDA);
@@ -701,7 +719,7 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
   c->grid_sample = std::min(c->n_work, nsm * occ);
   if ((rc = set_delay_impl(c, o->delay_k))) return fail(rc);
   c->recompute_every = o->recompute_every > 0 ? o->recompute_every
-                       : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 256 : 0;
+                       : (o->recompute_every == 0 && o->precision == VMC_MIXED) ? 64 : 0;
   // Initial inverses; re-draw placements whose M is singular (bounded).
   if ((rc = init_with_redraw(c, o->seed ^ 0x5851F42D4C957F2Dull))) return fail(rc);
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(VMC_ECUDA);
@@ -819,7 +837,8 @@ int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_b
                                   c->precision, 1, c->recompute_every, c->smem_init, c->st,
                                   &c->n_launch));
       else
-        CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->precision, 1, c->recompute_every,
+        CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->d_work_ctr + 1, c->precision, 1,
+                            c->recompute_every,
                             c->smem_init, c->st, &c->n_launch));
       return VMC_OK;
     };
@@ -1255,8 +1274,11 @@ int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, do
   CK(ensure_init(c));
   const int esize = c->precision == VMC_FP64 ? 8 : 4;
   const size_t mb = ((size_t)s.N * s.ldm * esize + 127) / 128 * 128;
-  std::vector<unsigned char> buf(mb);
+  std::vector<unsigned char> buf(mb), blo(s.dev.minv_lo ? mb : 0);
   CKC(cudaMemcpyAsync(buf.data(), (unsigned char *)s.dev.minv + mb * walker, mb, cudaMemcpyDeviceToHost, c->st));
+  if (s.dev.minv_lo)
+    CKC(cudaMemcpyAsync(blo.data(), (unsigned char *)s.dev.minv_lo + mb * walker, mb,
+                        cudaMemcpyDeviceToHost, c->st));
   double ld = 0.0;
   int sg = 0;
   CKC(cudaMemcpyAsync(&ld, s.dev.logdet + walker, sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -1265,8 +1287,10 @@ int vmc_get_inverse(vmc_ctx *c, int32_t system, int32_t walker, double *minv, do
   if (minv)
     for (int r = 0; r < s.N; ++r)
       for (int k = 0; k < s.N; ++k)
-        minv[(size_t)r * s.N + k] = esize == 8 ? ((double *)buf.data())[(size_t)r * s.ldm + k]
-                                               : ((float *)buf.data())[(size_t)r * s.ldm + k];
+        minv[(size_t)r * s.N + k] =
+            esize == 8 ? ((double *)buf.data())[(size_t)r * s.ldm + k]
+                       : (double)((float *)buf.data())[(size_t)r * s.ldm + k] +
+                             (blo.empty() ? 0.0 : (double)((float *)blo.data())[(size_t)r * s.ldm + k]);
   if (logabsdet) *logabsdet = ld;
   if (sign) *sign = sg;
   return VMC_OK;
@@ -1279,7 +1303,9 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
   CK(ensure_init(c));
   CK(upload_sysdesc(c));
   const int prec = c->precision == VMC_FP64 ? 0 : 1;
-  const int grid = vmc_corr_grid(prec, c->smem_sample, s.W, s.Ns);
+  // the pair-correlation kernel reads the FP32 words only
+  const size_t smem_corr = vmc_walker_smem(prec, s.N, s.Ns, s.Np, s.dev.n_hidden, 0, nullptr, 0);
+  const int grid = vmc_corr_grid(prec, smem_corr, s.W, s.Ns);
   const size_t ns2 = (size_t)s.Ns * s.Ns;
   const size_t part_b = 3 * ns2 * sizeof(double);
   const size_t cnt_b = (4 * ns2 * sizeof(int) + 255) / 256 * 256;
@@ -1311,7 +1337,7 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
   if ((ms && cudaEventRecord(ev[0], c->st)) || cudaMemsetAsync(part, 0, part_b, c->st) ||
       vmc_launch_corr_occ(c->d_sys, system, s.Ns, cnt, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[1], c->st)) ||
-      vmc_launch_corr(c->d_sys, system, prec, grid, part, c->smem_sample, c->st, &c->n_launch) ||
+      vmc_launch_corr(c->d_sys, system, prec, grid, part, smem_corr, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[2], c->st)) ||
       vmc_launch_corr_reduce(part, 1, cnt, s.Ns, s.W, s.dev.lsite, out, c->st, &c->n_launch) ||
       (ms && cudaEventRecord(ev[3], c->st)) ||
@@ -1332,6 +1358,17 @@ int vmc_measure_corr(vmc_ctx *c, int32_t system, double *corr, double *ms) {
 
 int64_t vmc_kernel_launches(vmc_ctx *c) { return c ? c->n_launch : -1; }
 
+int vmc_sweep_launch(vmc_ctx *c, int32_t *grid, int32_t *ctas_per_sm, int64_t *smem_bytes) {
+  if (!c) return VMC_EINVAL;
+  const bool pj = projected(c);
+  if (grid) *grid = pj ? c->grid_proj : c->grid_sample;
+  if (ctas_per_sm)
+    *ctas_per_sm = pj ? vmc_proj_occupancy(c->precision, c->smem_proj)
+                      : vmc_sample_occupancy(c->precision, c->smem_sample);
+  if (smem_bytes) *smem_bytes = (int64_t)(pj ? c->smem_proj : c->smem_sample);
+  return VMC_OK;
+}
+
 int vmc_test_stall(vmc_ctx *c, int32_t target, int32_t system, int32_t walker) {
   if (!sys_ok(c, system)) return VMC_EINVAL;
   SysHost &s = c->sys[system];
@@ -1351,6 +1388,64 @@ int vmc_test_stall(vmc_ctx *c, int32_t target, int32_t system, int32_t walker) {
     default:
       return VMC_EINVAL;
   }
+}
+
+int vmc_lanczos_moments(vmc_ctx *c, int32_t system, double *F1, double *F2, double *moments) {
+  if (!sys_ok(c, system) || !moments) return VMC_EINVAL;
+  SysHost &s = c->sys[system];
+  if (s.dev.n_hidden || s.dev.n_J || projected(c)) return VMC_EINVAL;
+  CK(ensure_init(c));
+  CK(upload_sysdesc(c));
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(s.W, 4 * nsm);
+  const int prec = c->precision == VMC_FP64 ? 0 : 1;
+  const size_t slot = (vmc_lanczos_slot_bytes(prec, s.Ns, s.N) + 255) / 256 * 256;
+  const size_t need = slot * grid + sizeof(double) * (2 * (size_t)s.W + 8);
+  if (c->lz_bytes < need) {
+    if (c->lz_buf) cudaFree(c->lz_buf);
+    c->lz_buf = nullptr;
+    c->lz_bytes = 0;
+    if (cudaMalloc(&c->lz_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return VMC_ENOMEM;
+    }
+    c->lz_bytes = need;
+  }
+  double *f1 = (double *)((unsigned char *)c->lz_buf + slot * grid);
+  double *f2 = f1 + s.W;
+  double *mom = f2 + s.W;
+  CKC(vmc_launch_lanczos(c->d_sys, system, prec, s.Ns, grid, c->lz_buf, f1, f2, s.W, mom, c->st,
+                         &c->n_launch));
+  if (F1) CKC(cudaMemcpyAsync(F1, f1, sizeof(double) * s.W, cudaMemcpyDeviceToHost, c->st));
+  if (F2) CKC(cudaMemcpyAsync(F2, f2, sizeof(double) * s.W, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaMemcpyAsync(moments, mom, sizeof(double) * 4, cudaMemcpyDeviceToHost, c->st));
+  CKC(cudaStreamSynchronize(c->st));
+  return VMC_OK;
+}
+
+int vmc_lanczos_alpha(const double *h, double *alpha, double *E1) {
+  if (!h || !alpha) return VMC_EINVAL;
+  // E_1(t) = (a + b t + c t^2) / (1 + d t + e t^2); dE_1/dt = 0 is
+  // (b - a d) + 2 (c - a e) t + (c d - b e) t^2 = 0; the root with the lower E_1
+  const double a = h[0], b = h[2] + h[1], cc = h[3], d = 2.0 * h[0], e = h[1];
+  auto energy = [&](double t) { return (a + b * t + cc * t * t) / (1.0 + d * t + e * t * t); };
+  const double q2 = cc * d - b * e, q1 = 2.0 * (cc - a * e), q0 = b - a * d;
+  double best;
+  if (fabs(q2) < 1e-300) {
+    if (q1 == 0.0) return VMC_ENUMERIC;
+    best = -q0 / q1;
+  } else {
+    const double disc = q1 * q1 - 4.0 * q2 * q0;
+    if (!(disc >= 0.0)) return VMC_ENUMERIC;
+    const double sq = sqrt(disc);
+    const double t1 = (-q1 + sq) / (2.0 * q2), t2 = (-q1 - sq) / (2.0 * q2);
+    best = energy(t1) <= energy(t2) ? t1 : t2;
+  }
+  *alpha = best;
+  if (E1) *E1 = energy(best);
+  return VMC_OK;
 }
 
 int vmc_set_delay(vmc_ctx *c, int32_t k) {

@@ -56,6 +56,7 @@ struct SysDev {
   int *ele;                    // [W*Ne]
   int *occ;                    // [W*2*Ns]: occ[s*Ns + i] = label or -1
   void *minv;                  // [W*N*ldm] (double or float)
+  float *minv_lo;              // mixed form: low words of the double-float M^-1, same layout
   void *jf;                    // [W*Ns] Jastrow field sum_{j != i} v_ij (n_j - 1) (double or float)
   unsigned long long *ctr;     // [W] Philox proposal counters
   double *logdet;              // [W]
@@ -111,9 +112,9 @@ __device__ __forceinline__ int vmc_mulhi(uint32_t r, int n) {
 // ---- launch wrappers (defined in vmc_walker.cu / vmc_sr.cu) ----
 // All return cudaError_t from the launch; they count launches in *n_launch.
 cudaError_t vmc_launch_expand(const SysDev *h_sys, cudaStream_t st, long long *n_launch);
-cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work,
-                            int precision, int only_due, int due_threshold,
-                            size_t smem, cudaStream_t st, long long *n_launch);
+cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work, int *d_ctr,
+                            int precision, int only_due, int due_threshold, size_t smem,
+                            cudaStream_t st, long long *nl);
 cudaError_t vmc_launch_sample(const SysDev *d_sys, const int2 *d_work, int n_work,
                               int *d_work_ctr, int precision, uint64_t seed,
                               int n_first, int n_samples, int sweeps_between,
@@ -135,7 +136,10 @@ cudaError_t vmc_launch_corr_occ(const SysDev *d_sys, int sys, int Ns, int *cnt,
 cudaError_t vmc_launch_corr_reduce(const double *part, int n_part, const int *cnt, int Ns,
                                    int W, const signed char *lsite, double *out, cudaStream_t st,
                                    long long *n_launch);
-size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len);
+// with_lo: the mixed form's sweep keeps the low words of its double-float
+// M^-1 in shared memory as well (the pair-correlation kernel does not).
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len,
+                       int with_lo);
 size_t vmc_init_smem(int N, int Ns);
 int vmc_sample_occupancy(int precision, size_t smem);
 cudaError_t vmc_walker_set_smem_limits(size_t smem_sample64, size_t smem_sample32,
@@ -155,6 +159,14 @@ cudaError_t vmc_launch_proj_sample(const SysDev *d_sys, const int2 *d_work, int 
 cudaError_t vmc_launch_proj_eval(const SysDev *d_sys, int sys, int walker, int precision,
                                  int n_moves, const int *d_moves, double *d_out, size_t smem,
                                  cudaStream_t st, long long *n_launch);
+
+// First-step power-Lanczos local values and moments (vmc_lanczos.cu): table
+// slot bytes per CTA, and the launch (k_lanczos over the walkers, then the
+// four walker means into moments[4]).
+size_t vmc_lanczos_slot_bytes(int precision, int Ns, int N);
+cudaError_t vmc_launch_lanczos(const SysDev *d_sys, int sys, int precision, int Ns, int grid,
+                               void *slots, double *F1, double *F2, int W, double *moments,
+                               cudaStream_t st, long long *n_launch);
 
 // SR (vmc_sr.cu)
 struct SrWork {

@@ -39,8 +39,8 @@ template <> __device__ __forceinline__ const float *gtab<float>(const SysDev &s)
 
 // In the sweep's arithmetic type (FP32 in the mixed form: GB300's FP64 pipe
 // is too slow for per-proposal work).
-template <typename T>
-__device__ __forceinline__ T corr_hop(const SysDev &S, const int *occ, const T *jf, int s, int r,
+template <typename T, typename OI>
+__device__ __forceinline__ T corr_hop(const SysDev &S, const OI *occ, const T *jf, int s, int r,
                                       int t) {
   const int Ns = S.Ns;
   const int o = (1 - s) * Ns;
@@ -55,8 +55,8 @@ template <> __device__ __forceinline__ const double *tvtab<double>(const SysDev 
 template <> __device__ __forceinline__ const float *tvtab<float>(const SysDev &s) { return s.tgt_v32; }
 
 // Same, with g from shared memory and v_rt given.
-template <typename T>
-__device__ __forceinline__ T corr_hop_v(const int *occ, const T *jf, const T *g, int Ns, int s,
+template <typename T, typename OI>
+__device__ __forceinline__ T corr_hop_v(const OI *occ, const T *jf, const T *g, int Ns, int s,
                                         int r, int t, T vrt) {
   const int o = (1 - s) * Ns;
   T d = jf[t] - jf[r] - vrt;

@@ -19,6 +19,7 @@
 #include "vmc_dev.cuh"
 
 #include <cuda_bf16.h>
+#include <type_traits>
 #include <math.h>
 
 namespace {
@@ -69,6 +70,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
 // Attempts of the test hook's wait (vmc_test_stall): a short bounded wait on
 // a barrier no copy was issued for.
 constexpr uint32_t STALL_LIMIT = 1u << 14;
+// Two copies of `bytes` each completing on one mbarrier phase (one arrival
+// expecting both transactions).
+__device__ __forceinline__ void bulk_load_pair(void *dst0, const void *src0, void *dst1,
+                                               const void *src1, uint32_t bytes, uint64_t *bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(2 * bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst0)),
+      "l"(src0), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst1)),
+      "l"(src1), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst),
                "r"(smem_u32(src)), "r"(bytes)
@@ -95,17 +114,20 @@ struct WSmem {
   T *jf;        // Ns
   double *dred; // 2 buffers x 8 (double reductions)
   int *ele;     // Ne
-  int *occ;     // 2 Ns
+  short *occ;   // 2 Ns: electron index at (site, spin), -1 if empty (16 bits: N <= 128)
   int *ilist;   // Ns
   int *misc;    // 8
-  uint4 *rnd;   // NT Philox draws (one batch)
+  uint4 *rnd;   // RB Philox draws (one batch)
   T *hm;        // MLP pre-activations h (H)
   T *th;        // tanh(h) (H)
-  T *g;         // Gutzwiller g_i (Ns)
+  float *mlo;   // mixed form: low words of the double-float M^-1 (N x ldm), else null
 };
 
+// Philox draws made per batch (one per thread of the first warp).
+constexpr int RB = 32;
+
 template <typename T>
-__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int kd,
+__host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int kd, bool lo,
                                          unsigned char *base, WSmem<T> *sm) {
   const int ldm = (N % 2) ? N : N + 1;
   size_t off = 0;
@@ -119,13 +141,13 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int 
   const size_t o_jf = take(sizeof(T) * Ns);
   const size_t o_dred = take(sizeof(double) * 32);
   const size_t o_ele = take(sizeof(int) * 2 * N);
-  const size_t o_occ = take(sizeof(int) * 2 * Ns);
+  const size_t o_occ = take(sizeof(short) * 2 * Ns);
   const size_t o_il = take(sizeof(int) * Ns);
   const size_t o_misc = take(sizeof(int) * 8);
-  const size_t o_rnd = take(sizeof(uint4) * NT);
+  const size_t o_rnd = take(sizeof(uint4) * RB);
   const size_t o_hm = take(sizeof(T) * (size_t)H);
   const size_t o_th = take(sizeof(T) * (size_t)H);
-  const size_t o_g = take(sizeof(T) * (size_t)Ns);
+  const size_t o_mlo = lo ? take(minv_bytes(N, ldm, sizeof(float))) : 0;
   if (sm) {
     sm->minv = (T *)(base + o_minv);
     sm->vec = (T *)(base + o_vec);
@@ -137,13 +159,13 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int 
     sm->jf = (T *)(base + o_jf);
     sm->dred = (double *)(base + o_dred);
     sm->ele = (int *)(base + o_ele);
-    sm->occ = (int *)(base + o_occ);
+    sm->occ = (short *)(base + o_occ);
     sm->ilist = (int *)(base + o_il);
     sm->misc = (int *)(base + o_misc);
     sm->rnd = (uint4 *)(base + o_rnd);
     sm->hm = (T *)(base + o_hm);
     sm->th = (T *)(base + o_th);
-    sm->g = (T *)(base + o_g);
+    sm->mlo = lo ? (float *)(base + o_mlo) : nullptr;
   }
   return off;
 }
@@ -546,6 +568,460 @@ __device__ void exchange_update(const SysDev &S, const WSmem<T> &sm, int n, int 
 }
 
 // ---------------------------------------------------------------------------
+// Double-float inverse of the mixed form
+// ---------------------------------------------------------------------------
+// The mixed form keeps M^-1 as hi + lo, two FP32 words per entry: hi is the
+// FP32 inverse every ratio and the measurement read; lo holds what lies
+// below hi's last bit.  Accepted moves update both with error-free FP32
+// transformations (Knuth's TwoSum, the FMA's exact product), so the update
+// rounds at about 2^-46 instead of 2^-24 and FP32 ratios keep the accuracy
+// of a freshly rebuilt inverse, where FP32 updates alone let the error grow
+// with every small ratio.  New rows and columns come from the FP64 tables.
+__device__ __forceinline__ void fast2sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = a + b;
+  const float v = s - a;
+  e = (a - (s - v)) + (b - v);
+}
+// x += a b (all double-float)
+__device__ __forceinline__ void df_fma(float &xh, float &xl, float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float pe = fmaf(ah, bh, -p);
+  pe = fmaf(ah, bl, pe);
+  pe = fmaf(al, bh, pe);
+  float sh, se;
+  two_sum(xh, p, sh, se);
+  se += xl + pe;
+  fast2sum(sh, se, xh, xl);
+}
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &h, float &l) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  fast2sum(p, e, h, l);
+}
+// 1 / (ah + al): the FP32 reciprocal refined by one Newton step in double-float
+__device__ __forceinline__ void df_recip(float ah, float al, float &h, float &l) {
+  const float q = 1.0f / ah;
+  const float p = ah * q;
+  float pe = fmaf(ah, q, -p);
+  pe = fmaf(al, q, pe);
+  const float r = (1.0f - p) - pe;
+  fast2sum(q, q * r, h, l);
+}
+// Compensated dot product in FP32 words (Ogita-Rump-Oishi Dot2): s sums the
+// products' heads with TwoSum, c collects every rounding error and the
+// products' tails; four independent accumulators, normalised once at the end.
+struct Dot2 {
+  float s[4] = {0.f, 0.f, 0.f, 0.f}, c[4] = {0.f, 0.f, 0.f, 0.f};
+  __device__ __forceinline__ void add(int q, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float pe = fmaf(ah, bh, -p);
+    pe = fmaf(ah, bl, pe);
+    pe = fmaf(al, bh, pe);
+    float t, e;
+    two_sum(s[q], p, t, e);
+    s[q] = t;
+    c[q] += e + pe;
+  }
+  __device__ __forceinline__ void result(float &h, float &l) const {
+    float t0, e0, t1, e1, t, e;
+    two_sum(s[0], s[1], t0, e0);
+    two_sum(s[2], s[3], t1, e1);
+    two_sum(t0, t1, t, e);
+    const float cc = ((c[0] + c[1]) + (c[2] + c[3])) + (e0 + e1 + e);
+    fast2sum(t, cc, h, l);
+  }
+};
+
+// sum_l x[l] M[l][col] (x double-float in 16-byte-aligned slots xh / xl)
+__device__ __forceinline__ void df_col_dot(const float *Mh, const float *Ml, int ldm, int col,
+                                           const float *xh, const float *xl, int N, float &h,
+                                           float &l) {
+  Dot2 d;
+  int k = 0;
+  for (; k + 4 <= N; k += 4) {
+    float a0, a1, a2, a3, b0, b1, b2, b3;
+    ld4(xh + k, a0, a1, a2, a3);
+    ld4(xl + k, b0, b1, b2, b3);
+    d.add(0, a0, b0, Mh[k * ldm + col], Ml[k * ldm + col]);
+    d.add(1, a1, b1, Mh[(k + 1) * ldm + col], Ml[(k + 1) * ldm + col]);
+    d.add(2, a2, b2, Mh[(k + 2) * ldm + col], Ml[(k + 2) * ldm + col]);
+    d.add(3, a3, b3, Mh[(k + 3) * ldm + col], Ml[(k + 3) * ldm + col]);
+  }
+  for (; k < N; ++k) d.add(0, xh[k], xl[k], Mh[k * ldm + col], Ml[k * ldm + col]);
+  d.result(h, l);
+}
+
+// sum_k row[k] x[k] (the thread's row in rh / rl; x as above)
+__device__ __forceinline__ void df_row_dot(const float *rh, const float *rl, const float *xh,
+                                           const float *xl, int N, float &h, float &l) {
+  Dot2 d;
+  int k = 0;
+  for (; k + 4 <= N; k += 4) {
+    float a0, a1, a2, a3, b0, b1, b2, b3;
+    ld4(xh + k, a0, a1, a2, a3);
+    ld4(xl + k, b0, b1, b2, b3);
+    d.add(0, rh[k], rl[k], a0, b0);
+    d.add(1, rh[k + 1], rl[k + 1], a1, b1);
+    d.add(2, rh[k + 2], rl[k + 2], a2, b2);
+    d.add(3, rh[k + 3], rl[k + 3], a3, b3);
+  }
+  for (; k < N; ++k) d.add(0, rh[k], rl[k], xh[k], xl[k]);
+  d.result(h, l);
+}
+
+__device__ __forceinline__ void df_split(double x, float &h, float &l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+__device__ __forceinline__ double df_val(float h, float l) { return (double)h + (double)l; }
+
+// row[k] -= c x[k] for the thread's row (hi in rh, lo in rl), x double-float
+// vectors in 16-byte-aligned slots
+__device__ __forceinline__ void df_row_axpy(float *rh, float *rl, const float *xh, const float *xl,
+                                            float ch, float cl, int N) {
+  const float nh = -ch, nl = -cl;
+  int k = 0;
+  for (; k + CH <= N; k += CH) {
+    float ah[CH], al[CH], bh[CH], bl[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      ah[u] = rh[k + u];
+      al[u] = rl[k + u];
+    }
+#pragma unroll
+    for (int u = 0; u < CH; u += 4) {
+      ld4(xh + k + u, bh[u], bh[u + 1], bh[u + 2], bh[u + 3]);
+      ld4(xl + k + u, bl[u], bl[u + 1], bl[u + 2], bl[u + 3]);
+    }
+#pragma unroll
+    for (int u = 0; u < CH; ++u) df_fma(ah[u], al[u], nh, nl, bh[u], bl[u]);
+#pragma unroll
+    for (int u = 0; u < CH; ++u) {
+      rh[k + u] = ah[u];
+      rl[k + u] = al[u];
+    }
+  }
+  for (; k < N; ++k) {
+    float h = rh[k], l = rl[k];
+    df_fma(h, l, nh, nl, xh[k], xl[k]);
+    rh[k] = h;
+    rl[k] = l;
+  }
+}
+
+// From-scratch inverse of the mixed form in double-float: the Gauss-Jordan
+// elimination of vmc_gj::gj_invert (partial pivoting, in place) on hi + lo
+// words, every multiply-subtract an error-free FP32 sequence (df_fma).  The
+// pivot is the largest |hi| of the column (ties: lowest row).  GB300's FP64
+// pipe runs at 1/64 of the FP32 rate, and a double-float multiply-add costs
+// about fifteen FP32 operations, so the elimination runs several times
+// faster than in FP64 at about 2^-46 rounding, the precision the sweep's
+// updates keep.  The scalars of the determinant stay FP64.
+struct GJdf {
+  double val[NWARP];
+  double amax[NWARP];
+  double pminw[NWARP];
+  int idx[NWARP];
+  int piv, bad, sign;
+  float ih, il;                 // 1 / pivot
+  double logdet, pmin, pmax;    // log|det M|, smallest / largest |pivot|
+  float ph[VMC_MAX_N], pl[VMC_MAX_N];   // pivot of every step
+  alignas(16) float ch[VMC_MAX_N];      // pivot column of the step (row k zeroed)
+  alignas(16) float cl[VMC_MAX_N];
+  alignas(16) float rh[VMC_MAX_N];      // scaled pivot row of the step (column k zeroed)
+  alignas(16) float rl[VMC_MAX_N];
+};
+
+__device__ void gj_invert_df(float *Ah, float *Al, int lda, int N, int *perm, GJdf &g) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    g.sign = 1;
+    g.bad = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    // (1) copy column k; pivot among rows >= k
+    float v = -1.f;
+    int vi = N;
+    for (int i = tid; i < N; i += NT) {
+      const float h = Ah[i * lda + k];
+      g.ch[i] = h;
+      g.cl[i] = Al[i * lda + k];
+      if (i >= k && fabsf(h) > v) {
+        v = fabsf(h);
+        vi = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
+      if (ov > v || (ov == v && oi < vi)) {
+        v = ov;
+        vi = oi;
+      }
+    }
+    if (lane == 0) {
+      g.val[warp] = v;
+      g.idx[warp] = vi;
+    }
+    __syncthreads();
+    // (2) one thread: pivot row, its entry swapped out of the column copy, 1/pivot
+    if (tid == 0) {
+      double bv = g.val[0];
+      int bi = g.idx[0];
+      for (int q = 1; q < NWARP; ++q)
+        if (g.val[q] > bv || (g.val[q] == bv && g.idx[q] < bi)) {
+          bv = g.val[q];
+          bi = g.idx[q];
+        }
+      if (!(bv > 0.0) || bi >= N) {
+        g.bad = 1;
+        bi = k;
+      }
+      g.piv = bi;
+      perm[k] = bi;
+      const float ph = g.ch[bi], pl = g.cl[bi];
+      g.ch[bi] = g.ch[k];
+      g.cl[bi] = g.cl[k];
+      g.ch[k] = 0.f;   // row k is scaled, not eliminated
+      g.cl[k] = 0.f;
+      df_recip(ph, pl, g.ih, g.il);
+      g.ph[k] = ph;    // log|det| is summed after the elimination
+      g.pl[k] = pl;
+      if ((ph < 0.f) != (bi != k)) g.sign = -g.sign;   // hi carries the sign
+    }
+    __syncthreads();
+    if (g.bad) return;
+    const int p = g.piv;
+    const float ih = g.ih, il = g.il;
+    // (3a) the new column k; rows k and p swapped, row k scaled and kept
+    for (int i = tid; i < N; i += NT) {
+      float h = ih, l = il;
+      if (i != k) df_mul(-g.ch[i], -g.cl[i], ih, il, h, l);
+      Ah[i * lda + k] = h;
+      Al[i * lda + k] = l;
+    }
+    for (int c = tid; c < N; c += NT) {
+      if (c == k) {
+        g.rh[c] = 0.f;   // column k is final
+        g.rl[c] = 0.f;
+        continue;
+      }
+      const float h = Ah[p * lda + c], l = Al[p * lda + c];
+      if (p != k) {
+        Ah[p * lda + c] = Ah[k * lda + c];
+        Al[p * lda + c] = Al[k * lda + c];
+      }
+      float sh, sl;
+      df_mul(h, l, ih, il, sh, sl);
+      Ah[k * lda + c] = sh;
+      Al[k * lda + c] = sl;
+      g.rh[c] = sh;
+      g.rl[c] = sl;
+    }
+    __syncthreads();
+    // (3b) A_ic -= colk_i rowk_c: thread c < N takes column c (c != k: rowk_k
+    // = 0 leaves column k) over all rows, four at a time with the pivot
+    // column read by 16-byte broadcast loads; colk_k = 0 leaves the value of
+    // row k unchanged.
+    if (tid < N && tid != k) {
+      const float rh = g.rh[tid], rl = g.rl[tid];
+      float *qh = Ah + tid, *ql = Al + tid;
+      int i = 0;
+      for (; i + 4 <= N; i += 4) {
+        float c0, c1, c2, c3, e0, e1, e2, e3;
+        ld4(g.ch + i, c0, c1, c2, c3);
+        ld4(g.cl + i, e0, e1, e2, e3);
+        float h0 = qh[i * lda], h1 = qh[(i + 1) * lda], h2 = qh[(i + 2) * lda],
+              h3 = qh[(i + 3) * lda];
+        float l0 = ql[i * lda], l1 = ql[(i + 1) * lda], l2 = ql[(i + 2) * lda],
+              l3 = ql[(i + 3) * lda];
+        df_fma(h0, l0, -c0, -e0, rh, rl);
+        df_fma(h1, l1, -c1, -e1, rh, rl);
+        df_fma(h2, l2, -c2, -e2, rh, rl);
+        df_fma(h3, l3, -c3, -e3, rh, rl);
+        qh[i * lda] = h0;
+        qh[(i + 1) * lda] = h1;
+        qh[(i + 2) * lda] = h2;
+        qh[(i + 3) * lda] = h3;
+        ql[i * lda] = l0;
+        ql[(i + 1) * lda] = l1;
+        ql[(i + 2) * lda] = l2;
+        ql[(i + 3) * lda] = l3;
+      }
+      for (; i < N; ++i) {
+        float h = qh[i * lda], l = ql[i * lda];
+        df_fma(h, l, -g.ch[i], -g.cl[i], rh, rl);
+        qh[i * lda] = h;
+        ql[i * lda] = l;
+      }
+    }
+    __syncthreads();
+  }
+  // log|det M| and the pivot range
+  {
+    double ls = 0.0, mn = 1e300, mx = 0.0;
+    for (int i = tid; i < N; i += NT) {
+      const double a = fabs((double)g.ph[i] + (double)g.pl[i]);
+      ls += log(a);
+      mn = fmin(mn, a);
+      mx = fmax(mx, a);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      ls += __shfl_xor_sync(0xffffffffu, ls, o);
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      g.val[warp] = ls;
+      g.pminw[warp] = mn;
+      g.amax[warp] = mx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 1e300, c = 0.0;
+      for (int q = 0; q < NWARP; ++q) {
+        a += g.val[q];
+        b = fmin(b, g.pminw[q]);
+        c = fmax(c, g.amax[q]);
+      }
+      g.logdet = a;
+      g.pmin = b;
+      g.pmax = c;
+    }
+  }
+  // undo the row interchanges as column interchanges of the inverse
+  for (int k = N - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p == k) continue;   // uniform: perm is shared
+    for (int r = tid; r < N; r += NT) {
+      const float h = Ah[r * lda + k], l = Al[r * lda + k];
+      Ah[r * lda + k] = Ah[r * lda + p];
+      Al[r * lda + k] = Al[r * lda + p];
+      Ah[r * lda + p] = h;
+      Al[r * lda + p] = l;
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+}
+
+// Row n replaced (up electron n to site t): w = R^T M^-1 with the new row
+// R_l = f(t, r_l,dn), M'^-1 = M^-1 - M^-1[:,n] (w - e_n)^T / w_n (Sherman-Morrison).
+__device__ void row_update_df(const SysDev &S, const WSmem<float> &sm, int n, int t) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
+  float *Rh = sm.vec, *Rl = sm.vec + VMC_MAX_N, *Wh = sm.vec + 2 * VMC_MAX_N,
+        *Wl = sm.vec + 3 * VMC_MAX_N;
+  if (tid < N) df_split(S.f64[(size_t)t * Ns + sm.ele[N + tid]], Rh[tid], Rl[tid]);
+  __syncthreads();
+  if (tid < N) df_col_dot(sm.minv, sm.mlo, ldm, tid, Rh, Rl, N, Wh[tid], Wl[tid]);
+  __syncthreads();
+  float ih, il;
+  df_recip(Wh[n], Wl[n], ih, il);
+  if (tid < N) {
+    float *rh = sm.minv + tid * ldm, *rl = sm.mlo + tid * ldm;
+    float ch, cl;
+    df_mul(rh[n], rl[n], ih, il, ch, cl);
+    df_row_axpy(rh, rl, Wh, Wl, ch, cl, N);
+    rh[n] = ch;
+    rl[n] = cl;
+  }
+  __syncthreads();
+}
+
+// Column m replaced (down electron m to site t): v = M^-1 C with the new
+// column C_k = f(r_k,up, t), M'^-1 = M^-1 - (v - e_m) M^-1[m,:] / v_m.
+__device__ void col_update_df(const SysDev &S, const WSmem<float> &sm, int m, int t) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
+  float *Ch = sm.vec, *Cl = sm.vec + VMC_MAX_N, *Vh = sm.vec + 2 * VMC_MAX_N,
+        *Vl = sm.vec + 3 * VMC_MAX_N, *Zh = sm.vec + 4 * VMC_MAX_N, *Zl = sm.vec + 5 * VMC_MAX_N;
+  if (tid < N) {
+    df_split(S.fT64[(size_t)t * Ns + sm.ele[tid]], Ch[tid], Cl[tid]);
+    Zh[tid] = sm.minv[m * ldm + tid];
+    Zl[tid] = sm.mlo[m * ldm + tid];
+  }
+  __syncthreads();
+  if (tid < N)
+    df_row_dot(sm.minv + tid * ldm, sm.mlo + tid * ldm, Ch, Cl, N, Vh[tid], Vl[tid]);
+  __syncthreads();
+  float ih, il;
+  df_recip(Vh[m], Vl[m], ih, il);
+  if (tid < N) {
+    float *rh = sm.minv + tid * ldm, *rl = sm.mlo + tid * ldm;
+    if (tid == m) {
+      for (int k = 0; k < N; ++k) df_mul(Zh[k], Zl[k], ih, il, rh[k], rl[k]);
+    } else {
+      float ch, cl;
+      df_mul(Vh[tid], Vl[tid], ih, il, ch, cl);
+      df_row_axpy(rh, rl, Zh, Zl, ch, cl, N);
+    }
+  }
+  __syncthreads();
+}
+
+// Exchange of up electron n (site i) with down electron m (site j), rank 2
+// (Woodbury): with the new row R (R_l = f(j, r_l,dn), R_m = f(j, i)), w = R^T M^-1,
+// b_k = C_k - M_km (C_k = f(r'_k,up, i), r'_n = j; b_n = 0), z = M^-1[m,:],
+// K = [[w_n, sum_k w_k b_k], [M^-1_mn, sum_k M^-1_mk C'_k]] (C'_n = M_nm),
+// M'^-1 = M^-1 - [p q] K^-1 [w - e_n; z] with p = M^-1[:,n], q = M^-1 b.
+// The 2 x 2 and per-row scalars are FP64; the N^2 parts double-float.
+__device__ void exchange_update_df(const SysDev &S, const WSmem<float> &sm, int n, int m, int i,
+                                   int j, int &buf) {
+  const int N = S.N, Ns = S.Ns, ldm = S.ldm, tid = threadIdx.x;
+  float *Rh = sm.vec, *Rl = sm.vec + VMC_MAX_N, *Wh = sm.vec + 2 * VMC_MAX_N,
+        *Wl = sm.vec + 3 * VMC_MAX_N, *Bh = sm.vec + 4 * VMC_MAX_N, *Bl = sm.vec + 5 * VMC_MAX_N,
+        *Zh = sm.vec + 6 * VMC_MAX_N, *Zl = sm.vec + 7 * VMC_MAX_N;
+  double cp = 0.0;
+  if (tid < N) {
+    df_split(tid == m ? S.f64[(size_t)j * Ns + i] : S.f64[(size_t)j * Ns + sm.ele[N + tid]],
+             Rh[tid], Rl[tid]);
+    const int site = (tid == n) ? j : sm.ele[tid];
+    const double ck = S.fT64[(size_t)i * Ns + site];
+    const double mk = S.fT64[(size_t)j * Ns + sm.ele[tid]];
+    df_split(tid == n ? 0.0 : ck - mk, Bh[tid], Bl[tid]);
+    cp = (tid == n) ? mk : ck;
+    Zh[tid] = sm.minv[m * ldm + tid];
+    Zl[tid] = sm.mlo[m * ldm + tid];
+  }
+  __syncthreads();
+  double t12 = 0.0, t22 = 0.0;
+  if (tid < N) {
+    float wh, wl;
+    df_col_dot(sm.minv, sm.mlo, ldm, tid, Rh, Rl, N, wh, wl);
+    Wh[tid] = wh;
+    Wl[tid] = wl;
+    if (tid != n) t12 = df_val(wh, wl) * df_val(Bh[tid], Bl[tid]);
+    t22 = df_val(Zh[tid], Zl[tid]) * cp;
+  }
+  double K12, K22;
+  block_sum2(t12, t22, sm.dred, buf, K12, K22);
+  const double K11 = df_val(Wh[n], Wl[n]), K21 = df_val(Zh[n], Zl[n]);
+  const double inv = 1.0 / (K11 * K22 - K12 * K21);
+  if (tid < N) {
+    float *rh = sm.minv + tid * ldm, *rl = sm.mlo + tid * ldm;
+    float qh, ql;
+    df_row_dot(rh, rl, Bh, Bl, N, qh, ql);
+    const double p = df_val(rh[n], rl[n]), q = df_val(qh, ql);
+    float c1h, c1l, c2h, c2l;
+    df_split((p * K22 - q * K21) * inv, c1h, c1l);
+    df_split((q * K11 - p * K12) * inv, c2h, c2l);
+    df_row_axpy(rh, rl, Wh, Wl, c1h, c1l, N);
+    df_row_axpy(rh, rl, Zh, Zl, c2h, c2l, N);
+    float h = rh[n], l = rl[n];
+    df_fma(h, l, c1h, c1l, 1.0f, 0.0f);
+    rh[n] = h;
+    rl[n] = l;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // Delayed updates: up to kd accepted hops are kept as rank-1 pairs, so that
 // G = G0 - sum_{i<np} u_i v_i^T; ratios read G through the correction above
 // and the pairs are folded into G0 by one rank-np product (flush).
@@ -632,12 +1108,14 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
                         unsigned long long &ctr, int &rpos, MoveCounts &mc, int &acc_since,
                         int &buf, int &np) {
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, tid = threadIdx.x;
-  if (rpos == NT) {
-    // Next NT draws of this walker's stream, one per thread.
+  if (rpos == RB) {
+    // Next RB draws of this walker's stream, one per thread of the first warp.
     __syncthreads();
-    const unsigned long long c = ctr + tid;
-    sm.rnd[tid] = vmc_philox(make_uint4((uint32_t)c, (uint32_t)(c >> 32), walker,
-                                        (uint32_t)S.sys_index), key);
+    if (tid < RB) {
+      const unsigned long long c = ctr + tid;
+      sm.rnd[tid] = vmc_philox(make_uint4((uint32_t)c, (uint32_t)(c >> 32), walker,
+                                          (uint32_t)S.sys_index), key);
+    }
     __syncthreads();
     rpos = 0;
   }
@@ -655,7 +1133,12 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
     const T ratio = S.n_hidden ? rpf * exp_t<T>(mlp) : rpf;
     if (u < ratio * ratio) {
       delayed_flush(S, sm, np);
-      exchange_update(S, sm, n, m - N, j, K, rpf);
+      if constexpr (std::is_same<T, float>::value) {
+        if (sm.mlo && S.delay_k <= 1) exchange_update_df(S, sm, n, m - N, i, j, buf);
+        else exchange_update(S, sm, n, m - N, j, K, rpf);
+      } else {
+        exchange_update(S, sm, n, m - N, j, K, rpf);
+      }
       if (S.n_hidden) mlp_apply(S, sm, i + Ns, i, j, j + Ns);
       if (tid == 0) {
         sm.ele[n] = j;
@@ -683,7 +1166,7 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   // P(x')/P(x): one thread evaluates it; the barrier inside hop_pf_ratio publishes it.
   const int slot = buf;
   if (tid == 0)
-    sm.bc[slot] = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, s, rs, t,
+    sm.bc[slot] = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, gtab<T>(S), Ns, s, rs, t,
                                             vtab<T>(S)[(size_t)rs * Ns + t]));
   // rows t and r of v for the Jastrow-field update, fetched while the ratio is formed
   T vt[2], vr[2];
@@ -699,9 +1182,22 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   if (!(u < ratio * ratio)) return;
   if (tid < N) sm.vec[tid] = fval;
   __syncthreads();
-  if (S.delay_k > 1) delayed_hop_update(S, sm, e, np);
-  else if (s == 0) row_update(S, sm, e);
-  else col_update(S, sm, e - N);
+  bool done = false;
+  if constexpr (std::is_same<T, float>::value) {
+    if (sm.mlo && S.delay_k <= 1) {
+      if (s == 0) row_update_df(S, sm, e, t);
+      else col_update_df(S, sm, e - N, t);
+      done = true;
+    }
+  }
+  if (done) {
+  } else if (S.delay_k > 1) {
+    delayed_hop_update(S, sm, e, np);
+  } else if (s == 0) {
+    row_update(S, sm, e);
+  } else {
+    col_update(S, sm, e - N);
+  }
   if (S.n_hidden) mlp_apply(S, sm, t + s * Ns, rs + s * Ns, -1, -1);
   // Jastrow field: h_x += v_{x t} - v_{x r}.
 #pragma unroll
@@ -925,7 +1421,7 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
             lm = reduce8_transposed(mq, lane);
           }
           if ((lane & 3) == 0 && el >= 0) {
-            const T c = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, sp, j, i, sel4(vr, r)));
+            const T c = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, gtab<T>(S), Ns, sp, j, i, sel4(vr, r)));
             eo += -sel4(tr, r) * sum * c * (S.n_hidden ? exp_t<T>(lm) : (T)1);
             mc.meas_hop++;
           }
@@ -1078,7 +1574,7 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     const int w = wk.y;
     const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
     WSmem<T> sm;
-    walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, S.delay_k, smem_raw, &sm);
+    walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, S.delay_k, S.minv_lo != nullptr, smem_raw, &sm);
     // --- load the walker: M^-1 block by a TMA bulk copy, configuration and
     // Jastrow field by plain loads while the copy is in flight
     const uint32_t nbytes = (uint32_t)minv_bytes(N, ldm, sizeof(T));
@@ -1086,12 +1582,16 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     // bounded wait below runs out with nothing in flight
     const bool stall = (w == S.stall_walker);
     {
-      if (tid == 0 && !stall)
-        bulk_load(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, nbytes, &bar);
+      if (tid == 0 && !stall) {
+        if (sm.mlo)
+          bulk_load_pair(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, sm.mlo,
+                         (const unsigned char *)S.minv_lo + (size_t)w * nbytes, nbytes, &bar);
+        else
+          bulk_load(sm.minv, (const unsigned char *)S.minv + (size_t)w * nbytes, nbytes, &bar);
+      }
       for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
       for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
       for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
-      for (int k = tid; k < Ns; k += NT) sm.g[k] = gtab<T>(S)[k];
       for (int k = tid; k < S.n_hidden; k += NT) {
         const T h = ((const T *)S.hmlp)[(size_t)w * S.n_hidden + k];
         sm.hm[k] = h;
@@ -1112,7 +1612,7 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     }
     if (tid == 0) S.status[w] &= ~VMC_ST_TIMEOUT;   // loaded: an earlier timeout is over
     unsigned long long ctr = S.ctr[w];
-    int rpos = NT;
+    int rpos = RB;
     MoveCounts mc;
     int acc_since = S.acc_since[w];
     int buf = 0;
@@ -1140,7 +1640,10 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     fence_proxy_async();
     __syncthreads();
     {
-      if (tid == 0) bulk_store((unsigned char *)S.minv + (size_t)w * nbytes, sm.minv, nbytes);
+      if (tid == 0) {
+        bulk_store((unsigned char *)S.minv + (size_t)w * nbytes, sm.minv, nbytes);
+        if (sm.mlo) bulk_store((unsigned char *)S.minv_lo + (size_t)w * nbytes, sm.mlo, nbytes);
+      }
       for (int k = tid; k < Ne; k += NT) S.ele[(size_t)w * Ne + k] = sm.ele[k];
       for (int k = tid; k < S.n_hidden; k += NT) ((T *)S.hmlp)[(size_t)w * S.n_hidden + k] = sm.hm[k];
       for (int k = tid; k < 2 * Ns; k += NT) S.occ[(size_t)w * 2 * Ns + k] = sm.occ[k];
@@ -1219,44 +1722,76 @@ __global__ void k_expand_mlp(SysDev S) {
   }
 }
 
-// From-scratch inverse of M (FP64 Gauss-Jordan with partial pivoting, in
-// place in shared memory), log|det M| and its sign, Jastrow field and
-// occupation table.  With only_due, only walkers whose accepted-move count
-// since the last inverse reached due_threshold are rebuilt, and the drift
-// max|M^-1_updated - M^-1_fresh| / max|M^-1_fresh| is recorded.
+// From-scratch inverse of M (Gauss-Jordan with partial pivoting, in place in
+// shared memory: FP64, or double-float in the mixed form), log|det M| and its
+// sign, Jastrow field and occupation table.  With only_due, only walkers
+// whose accepted-move count since the last inverse reached due_threshold are
+// rebuilt, and the drift max|M^-1_updated - M^-1_fresh| / max|M^-1_fresh| is
+// recorded.  Work items are taken from the counter *ctr (zeroed by the
+// launcher) one at a time, so the CTAs share the due walkers evenly whatever
+// their positions in the list.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *work, int n_work,
-                                             int only_due, int due_threshold) {
+                                             int *ctr, int only_due, int due_threshold) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SysDev S;
-  __shared__ vmc_gj::GJShared g;
-  for (int item = blockIdx.x; item < n_work; item += gridDim.x) {
+  __shared__ int s_item;
+  // FP64 elimination for the plain form, double-float for the mixed form
+  constexpr bool DF = std::is_same<T, float>::value;
+  __shared__ typename std::conditional<DF, GJdf, vmc_gj::GJShared>::type g;
+  auto next_item = [&]() -> int {
+    __syncthreads();   // every thread has read the previous item
+    if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
     __syncthreads();
+    return s_item;
+  };
+  for (int item = next_item(); item < n_work; item = next_item()) {
     const int2 wk = work[item];
-    load_sys(&S, systems + wk.x);
     const int w = wk.y;
-    if (only_due && S.acc_since[w] < due_threshold) continue;
+    if (only_due && systems[wk.x].acc_since[w] < due_threshold) continue;
+    load_sys(&S, systems + wk.x);
     const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
-    double *A = (double *)smem_raw;                 // N x ldm
+    // N x ldm matrix: FP64 words, or (mixed form) hi words then lo words
+    double *A = (double *)smem_raw;
+    float *Ah = (float *)smem_raw, *Al = Ah + (size_t)N * ldm;
     int *ele = (int *)(A + (size_t)N * ldm);        // Ne
     int *perm = ele + Ne;                            // N
     for (int k = tid; k < Ne; k += NT) ele[k] = S.ele[(size_t)w * Ne + k];
     __syncthreads();
     for (int q = tid; q < N * N; q += NT) {
       const int n = q / N, m = q - n * N;
-      A[n * ldm + m] = S.f64[(size_t)ele[n] * Ns + ele[N + m]];
+      const double f = S.f64[(size_t)ele[n] * Ns + ele[N + m]];
+      if constexpr (DF)
+        df_split(f, Ah[n * ldm + m], Al[n * ldm + m]);
+      else
+        A[n * ldm + m] = f;
     }
     __syncthreads();
-    vmc_gj::gj_invert(A, ldm, N, perm, g);
+    if constexpr (DF)
+      gj_invert_df(Ah, Al, ldm, N, perm, g);
+    else
+      vmc_gj::gj_invert(A, ldm, N, perm, g);
+    // the fresh inverse's entry q (FP64 value)
+    auto fresh_at = [&](int q) -> double {
+      if constexpr (DF)
+        return (double)Ah[q] + (double)Al[q];
+      else
+        return A[q];
+    };
     const size_t nb = minv_bytes(N, ldm, sizeof(T));
     T *dst = (T *)((unsigned char *)S.minv + (size_t)w * nb);
+    // mixed form: low words of the double-float inverse (zero while delayed
+    // updates, which keep FP32 words only, are on)
+    float *dlo = (sizeof(T) == 4 && S.minv_lo) ? (float *)((unsigned char *)S.minv_lo + (size_t)w * nb)
+                                               : nullptr;
     if (!g.bad) {
       if (only_due) {
         double dmax = 0.0, amax = 0.0;
         for (int q = tid; q < N * N; q += NT) {
           const int r = q / N, c = q - r * N;
-          const double fresh = A[r * ldm + c];
-          dmax = fmax(dmax, fabs((double)dst[r * ldm + c] - fresh));
+          const double fresh = fresh_at(r * ldm + c);
+          const double cur = (double)dst[r * ldm + c] + (dlo ? (double)dlo[r * ldm + c] : 0.0);
+          dmax = fmax(dmax, fabs(cur - fresh));
           amax = fmax(amax, fabs(fresh));
         }
         for (int o = 16; o > 0; o >>= 1) {
@@ -1278,7 +1813,14 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
         }
         __syncthreads();
       }
-      for (int q = tid; q < N * ldm; q += NT) dst[q] = (T)A[q];
+      for (int q = tid; q < N * ldm; q += NT) {
+        if constexpr (DF) {
+          dst[q] = Ah[q];
+          if (dlo) dlo[q] = (S.delay_k > 1) ? 0.f : Al[q];
+        } else {
+          dst[q] = (T)A[q];
+        }
+      }
     }
     if (!only_due) {
       for (int k = tid; k < 2 * Ns; k += NT) S.occ[(size_t)w * 2 * Ns + k] = -1;
@@ -1348,14 +1890,13 @@ __global__ void __launch_bounds__(NT) k_eval_ratios(const SysDev *systems, int s
   load_sys(&S, systems + sys);
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
   WSmem<T> sm;
-  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, smem_raw, &sm);
+  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, false, smem_raw, &sm);
   const size_t nb = minv_bytes(N, ldm, sizeof(T));
   const T *src = (const T *)((const unsigned char *)S.minv + (size_t)w * nb);
   for (int k = tid; k < N * ldm; k += NT) sm.minv[k] = src[k];
   for (int k = tid; k < Ne; k += NT) sm.ele[k] = S.ele[(size_t)w * Ne + k];
   for (int k = tid; k < 2 * Ns; k += NT) sm.occ[k] = S.occ[(size_t)w * 2 * Ns + k];
   for (int k = tid; k < Ns; k += NT) sm.jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
-  for (int k = tid; k < Ns; k += NT) sm.g[k] = gtab<T>(S)[k];
   for (int k = tid; k < S.n_hidden; k += NT) {
     const T h = ((const T *)S.hmlp)[(size_t)w * S.n_hidden + k];
     sm.hm[k] = h;
@@ -1429,7 +1970,7 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
   load_sys(&S, systems + sys);
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
   WSmem<T> sm;
-  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, smem_raw, &sm);
+  walker_layout<T>(N, Ns, S.acc_len, S.n_hidden, 0, false, smem_raw, &sm);
   T *fb = sm.vec;                    // slot 0: f(b, r_l,dn), l < N
   const T *F = ftab<T>(S);
   const size_t ns2 = (size_t)Ns * Ns;
@@ -1605,11 +2146,12 @@ __global__ void k_corr_reduce(const double *part, int n_part, const int *cnt, in
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers
 // ---------------------------------------------------------------------------
-size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len) {
+size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int *acc_len,
+                       int with_lo) {
   const int al = (Np <= VMC_ACC_MAX) ? Np : 0;
   if (acc_len) *acc_len = al;
-  return precision == 0 ? walker_layout<double>(N, Ns, al, H, kd, nullptr, nullptr)
-                        : walker_layout<float>(N, Ns, al, H, kd, nullptr, nullptr);
+  return precision == 0 ? walker_layout<double>(N, Ns, al, H, kd, false, nullptr, nullptr)
+                        : walker_layout<float>(N, Ns, al, H, kd, with_lo != 0, nullptr, nullptr);
 }
 
 size_t vmc_init_smem(int N, int Ns) {
@@ -1655,9 +2197,9 @@ cudaError_t vmc_launch_expand(const SysDev *h_sys, cudaStream_t st, long long *n
   return cudaGetLastError();
 }
 
-cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work, int precision,
-                            int only_due, int due_threshold, size_t smem, cudaStream_t st,
-                            long long *nl) {
+cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work, int *d_ctr,
+                            int precision, int only_due, int due_threshold, size_t smem,
+                            cudaStream_t st, long long *nl) {
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1670,10 +2212,12 @@ cudaError_t vmc_launch_init(const SysDev *d_sys, const int2 *d_work, int n_work,
   int grid = nsm * per;
   if (grid > n_work) grid = n_work;
   if (grid < 1) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(d_ctr, 0, sizeof(int), st);
+  if (e) return e;
   if (precision == 0)
-    k_init<double><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, only_due, due_threshold);
+    k_init<double><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_ctr, only_due, due_threshold);
   else
-    k_init<float><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, only_due, due_threshold);
+    k_init<float><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_ctr, only_due, due_threshold);
   ++*nl;
   return cudaGetLastError();
 }

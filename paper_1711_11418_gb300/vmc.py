@@ -82,7 +82,8 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_num_params", "vmc_eval_ratios", "vmc_get_inverse", "vmc_kernel_launches",
            "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
            "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all", "vmc_measure_corr",
-           "vmc_test_stall", "vmc_set_projection"]
+           "vmc_test_stall", "vmc_set_projection", "vmc_lanczos_moments", "vmc_lanczos_alpha",
+           "vmc_sweep_launch"]
 STALL_NONE, STALL_SAMPLE, STALL_S_BUILD = 0, 1, 2
 
 
@@ -129,6 +130,9 @@ def load(path: str = LIB_PATH):
     L.vmc_tune_delay.argtypes = [P, C.c_int32, _I32P, C.c_int32, _I32P, _F64P]
     L.vmc_test_stall.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     L.vmc_set_projection.argtypes = [P, C.c_int32, _I32P, _I8P, _F64P]
+    L.vmc_lanczos_moments.argtypes = [P, C.c_int32, _F64P, _F64P, _F64P]
+    L.vmc_lanczos_alpha.argtypes = [_F64P, _F64P, _F64P]
+    L.vmc_sweep_launch.argtypes = [P, _I32P, _I32P, C.POINTER(C.c_int64)]
     for name in EXPORTS:
         if name not in ("vmc_destroy", "vmc_strerror", "vmc_kernel_launches"):
             getattr(L, name).restype = C.c_int
@@ -339,6 +343,14 @@ class Context:
     def kernel_launches(self):
         return int(self._L.vmc_kernel_launches(self._h))
 
+    def sweep_launch(self):
+        """(grid, CTAs per SM, shared-memory bytes) of the sweep kernel (vmc_sweep_launch)."""
+        g, o = np.zeros(1, np.int32), np.zeros(1, np.int32)
+        b = C.c_int64(0)
+        _check(self._L.vmc_sweep_launch(self._h, _p(g, _I32P), _p(o, _I32P), C.byref(b)),
+               "vmc_sweep_launch")
+        return int(g[0]), int(o[0]), int(b.value)
+
     def set_projection(self, perm, sign, weight):
         """Quantum-number projection (vmc_set_projection): perm, sign [n_ops, Ns]
         (T_g c^dag_r T_g^-1 = sign[g, r] c^dag_{perm[g, r]}), real weights
@@ -349,6 +361,16 @@ class Context:
         _check(self._L.vmc_set_projection(self._h, int(weight.size), _p(perm, _I32P),
                                           _p(sign, _I8P), _p(weight, _F64P)),
                "vmc_set_projection")
+
+    def lanczos_moments(self, system=0):
+        """First-step power-Lanczos (vmc_lanczos_moments): per-walker F(x, H),
+        F(x, H^2) of the current configurations and the moments
+        {h1, h2_11, h2_20, h3_12} (walker means)."""
+        W = self.n_walkers
+        f1, f2, h = np.zeros(W), np.zeros(W), np.zeros(4)
+        _check(self._L.vmc_lanczos_moments(self._h, system, _p(f1, _F64P), _p(f2, _F64P),
+                                           _p(h, _F64P)), "vmc_lanczos_moments")
+        return f1, f2, dict(h1=h[0], h2_11=h[1], h2_20=h[2], h3_12=h[3])
 
     def test_stall(self, target, system=0, walker=0):
         """Failure-detection test hook (vmc_test_stall): arm one bounded wait
@@ -386,3 +408,12 @@ class Context:
         _check(self._L.vmc_kernel_times(self._h, _p(ms, _F64P), cnt.ctypes.data_as(C.POINTER(C.c_int64))),
                "vmc_kernel_times")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(("sweep", "init", "sr", "sr_gemm"))}
+
+
+def lanczos_alpha(moments):
+    """alpha_1 and E_1(alpha_1) of Sec. 3.4 from the moments (vmc_lanczos_alpha)."""
+    L = load()
+    h = np.array([moments["h1"], moments["h2_11"], moments["h2_20"], moments["h3_12"]])
+    a, e = C.c_double(), C.c_double()
+    _check(L.vmc_lanczos_alpha(_p(h, _F64P), C.byref(a), C.byref(e)), "vmc_lanczos_alpha")
+    return a.value, e.value

@@ -72,17 +72,18 @@ def _inverse_errors(vmc, p, W, k, sweeps):
 
 @pytest.mark.parametrize("k", [4, 16])
 def test_delayed_mixed_inverse_matches_fresh(vmc, k):
-    """After sampling with k pending updates, the stored FP32 inverse of every
-    walker matches the FP64 inverse of its M as closely as with immediate
-    updates (FP32 rounding accumulated over the same accepted moves)."""
+    """After sampling with k pending updates the stored inverse of every
+    walker matches the FP64 inverse of its M to FP32 rounding (the delayed
+    form keeps FP32 words only), and the immediate updates, which keep the
+    double-float inverse, are at least as close (here far closer)."""
     p = with_correlations(I.square8_hubbard(), 6)
     W = 16
     e_imm, _ = _inverse_errors(vmc, p, W, 1, 6)
     e_dly, st = _inverse_errors(vmc, p, W, k, 6)
     assert st["n_hop_accepted"] > 4 * W
-    assert np.median(e_dly) < 2 * np.median(e_imm) + 1e-6, (np.median(e_dly), np.median(e_imm))
-    assert e_dly.max() < 3 * e_imm.max() + 1e-5, (e_dly.max(), e_imm.max())
-    assert e_dly.max() < 1e-2
+    assert e_dly.max() < 1e-2, e_dly.max()
+    assert np.median(e_imm) <= np.median(e_dly), (np.median(e_imm), np.median(e_dly))
+    assert e_imm.max() < 1e-6, e_imm.max()
 
 
 def _energy_error(vmc, p, W, k):
@@ -109,15 +110,17 @@ def test_delayed_mixed_energy_matches_fp64_square16(vmc, k):
     assert d.max() < 1e-4, d.max()
 
 
-def test_delayed_mixed_energy_no_worse_than_immediate(vmc):
+def test_delayed_mixed_energy_and_immediate_double_float(vmc):
     """8x8 Hubbard with random Gutzwiller/Jastrow values (some walkers poorly
-    conditioned): the delayed form's E_loc error against FP64 is no larger
-    than the immediate form's."""
+    conditioned): E_loc against FP64 on the same configurations.  The
+    immediate updates (double-float inverse) stay within 1e-5 t per site on
+    every walker; the delayed form (FP32 words) at the FP32 level, no better."""
     p = with_correlations(I.square8_hubbard(), 6)
     d1 = _energy_error(vmc, p, 8, 1)
     d8 = _energy_error(vmc, p, 8, 8)
-    assert np.median(d8) < 3 * np.median(d1) + 1e-7, (np.median(d8), np.median(d1))
-    assert d8.max() < 3 * d1.max() + 1e-6, (d8.max(), d1.max())
+    assert d1.max() < 1e-5, d1.max()
+    assert np.median(d1) <= np.median(d8), (np.median(d1), np.median(d8))
+    assert np.median(d8) < 1e-3, np.median(d8)
 
 
 def test_delayed_batched_uneven_systems(vmc):

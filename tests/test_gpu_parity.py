@@ -99,6 +99,56 @@ def test_inverse_and_logdet(vmc, name):
 
 
 @pytest.mark.parametrize("name", ["ring8", "square8", "ring6_apbc", "heis4", "j1j2_4"])
+def test_mixed_form_double_float_inverse(vmc, name):
+    """The mixed form's from-scratch inverse (double-float Gauss-Jordan, hi +
+    lo words) against the oracle's X^-1 and Pfaffian: relative error within
+    1e-12 cond(M) (about 2^-46 rounding amplified by the condition number),
+    the same sign, log|det| within 1e-12 cond(M) + 1e-11."""
+    p = with_correlations(small_problems()[name])
+    W = 3
+    cfg = good_configs(p, W, 100)
+    wf = Wavefunction(p)
+    N = p.N
+    with vmc.Context(p, W, seed=7, precision=vmc.MIXED) as ctx:
+        ctx.set_configs(cfg)
+        for w in range(W):
+            minv, ld, sg = ctx.get_inverse(w)
+            ele = cfg[w]
+            M = wf.f[np.ix_(ele[:N], ele[N:])]
+            orbs = [int(s) for s in ele[:N]] + [int(s) + p.Ns for s in ele[N:]]
+            X = wf.F[np.ix_(orbs, orbs)] - wf.F[np.ix_(orbs, orbs)].T
+            ref = np.linalg.inv(X)[N:, :N]
+            cond = np.linalg.cond(M)
+            err = np.abs(minv - ref).max() / np.abs(ref).max()
+            assert err <= 1e-12 * cond + 1e-15, (err, cond)
+            s_pf, l_pf = labelled_slog(wf, ele)
+            l_pf -= math.lgamma(N + 1) + wf.log_correlation(fock.from_labels(ele, p.Ns))
+            assert abs(ld - l_pf) <= 1e-12 * cond + 1e-11
+            assert sg * (-1) ** (N * (N - 1) // 2) == s_pf
+
+
+def test_mixed_form_double_float_inverse_16x16(vmc):
+    """Full size (16x16 Hubbard, N = 112): the mixed form's rebuilt inverses
+    of the library's own seeded placements against the FP64 form's."""
+    p = I.square16_hubbard()
+    W = 8
+    with vmc.Context(p, W, seed=3, precision=vmc.FP64) as c64:
+        ele, _ = c64.get_configs()
+        ref = [c64.get_inverse(w) for w in range(W)]
+    N = p.N
+    with vmc.Context(p, W, seed=3, precision=vmc.MIXED) as c32:
+        c32.set_configs(ele)
+        for w in range(W):
+            minv, ld, sg = c32.get_inverse(w)
+            a, la, sa = ref[w]
+            cond = np.linalg.cond(p.f_matrix()[np.ix_(ele[w, :N], ele[w, N:])])
+            err = np.abs(minv - a).max() / np.abs(a).max()
+            assert err <= 1e-12 * cond + 1e-15, (w, err, cond)
+            assert sg == sa
+            assert abs(ld - la) <= 1e-12 * cond + 1e-11
+
+
+@pytest.mark.parametrize("name", ["ring8", "square8", "ring6_apbc", "heis4", "j1j2_4"])
 def test_pfaffian_ratios(vmc, name):
     p = with_correlations(small_problems()[name], 1)
     W = 2
