@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--recompute", type=int, default=64)
     ap.add_argument("--equil", type=int, default=10)
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-df-rebuild", action="store_true",
+                    help="skip the mixed form with the opt-in double-float rebuild")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-corr", action="store_true")
@@ -478,11 +480,11 @@ def delta(a, b):
     return {k: b[k] - a[k] for k in b if isinstance(b[k], int)}
 
 
-def run_arm(vmc, prob, args, precision, stream, torch, world):
+def run_arm(vmc, prob, args, precision, stream, torch, world, rebuild=0):
     W, S = args.walkers, args.samples
     ctx = vmc.Context(prob, W, seed=1234 + int(os.environ.get("RANK", 0)), precision=precision,
                       max_samples=S, recompute_every=args.recompute if precision == vmc.MIXED else -1,
-                      stream=stream.cuda_stream)
+                      stream=stream.cuda_stream, rebuild=rebuild)
     ctx.sample(args.equil, 0, 0)                        # equilibration (untimed)
     # Immediate updates: they keep the mixed form's double-float inverse (the
     # delayed form keeps FP32 words only, so it is not used at the accuracy
@@ -559,6 +561,12 @@ def run_ours(args):
         if not args.no_fp64:
             ctx64, fp64 = run_arm(vmc, prob, args, vmc.FP64, stream, torch, world)
             ctx64.close()
+        # the mixed form with its opt-in double-float rebuild, same step
+        dfr = None
+        if not args.no_df_rebuild:
+            ctxdf, dfr = run_arm(vmc, prob, args, vmc.MIXED, stream, torch, world,
+                                 rebuild=vmc.REBUILD_DOUBLE_FLOAT)
+            ctxdf.close()
         # Energy accuracy of the mixed form on identical configurations
         ele, ctr = ctx.get_configs()
         params = ctx.get_params()
@@ -712,6 +720,9 @@ def run_ours(args):
         "mixed": sm,
         "plain_fp64": summarize(fp64) if fp64 else None,
         "speedup_mixed_over_fp64": (sm["proposals_per_s"] / summarize(fp64)["proposals_per_s"]) if fp64 else None,
+        "mixed_double_float_rebuild": dict(
+            summarize(dfr), what="the same step with the mixed form's opt-in double-float "
+            "from-scratch inverses (VMC_REBUILD_DOUBLE_FLOAT) instead of FP64 ones") if dfr else None,
         "energy_check": {"same_configs_dE_per_site_mean": dE, "same_configs_dE_per_site_max": dE_max,
                          "same_configs_dE_per_site_p99": dE_p99,
                          "walkers_over_tolerance": n_over, "walkers": args.walkers,

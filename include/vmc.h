@@ -116,7 +116,15 @@ typedef struct {
                                     -1 = never */
   int32_t max_samples;           /* sample rows kept per walker (>= 1) */
   void *stream;                  /* cudaStream_t; NULL = default stream */
+  int32_t rebuild;               /* from-scratch inverses of the mixed form:
+                                    VMC_REBUILD_FP64 (0, default: FP64 Gauss-Jordan)
+                                    or VMC_REBUILD_DOUBLE_FLOAT (Gauss-Jordan on
+                                    hi + lo FP32 words, about 2^-46 rounding, the
+                                    precision of the sweep's updates; faster on a
+                                    part whose FP64 rate is 1/64 of FP32).  The
+                                    FP64 form always rebuilds in FP64. */
 } vmc_opts;
+enum { VMC_REBUILD_FP64 = 0, VMC_REBUILD_DOUBLE_FLOAT = 1 };
 
 typedef struct {
   double energy;                 /* mean local energy over the stored samples */

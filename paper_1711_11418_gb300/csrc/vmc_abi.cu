@@ -497,6 +497,7 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
   *out = nullptr;
   if (o->n_walkers < 1 || o->max_samples < 1) return VMC_EINVAL;
   if (o->precision != VMC_FP64 && o->precision != VMC_MIXED) return VMC_EINVAL;
+  if (o->rebuild != VMC_REBUILD_FP64 && o->rebuild != VMC_REBUILD_DOUBLE_FLOAT) return VMC_EINVAL;
   for (int s = 0; s < n_sys; ++s) {
     CK(validate_system(&models[s], Ne[s], &layouts[s], params[s]));
     if (pex && (!(pex[s] >= 0.0) || pex[s] > 1.0)) return VMC_EINVAL;
@@ -657,6 +658,7 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dalloc(c, &d.minv, mb * W))) return fail(rc);
     d.minv_lo = nullptr;
     if (o->precision == VMC_MIXED && (rc = dalloc(c, &d.minv_lo, mb * W))) return fail(rc);
+    d.rebuild_df = (o->precision == VMC_MIXED && o->rebuild == VMC_REBUILD_DOUBLE_FLOAT) ? 1 : 0;
     if ((rc = dalloc(c, &d.jf, (size_t)esize * W * Ns))) return fail(rc);
     if ((rc = dupload(c, &d.ctr, (const unsigned long long *)nullptr, W))) return fail(rc);
     if ((rc = dupload(c, &d.logdet, (const double *)nullptr, W))) return fail(rc);

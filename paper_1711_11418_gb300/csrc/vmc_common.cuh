@@ -57,6 +57,7 @@ struct SysDev {
   int *occ;                    // [W*2*Ns]: occ[s*Ns + i] = label or -1
   void *minv;                  // [W*N*ldm] (double or float)
   float *minv_lo;              // mixed form: low words of the double-float M^-1, same layout
+  int rebuild_df;              // mixed form: from-scratch inverses in double-float (opt-in)
   void *jf;                    // [W*Ns] Jastrow field sum_{j != i} v_ij (n_j - 1) (double or float)
   unsigned long long *ctr;     // [W] Philox proposal counters
   double *logdet;              // [W]

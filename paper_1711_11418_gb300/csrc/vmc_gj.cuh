@@ -13,22 +13,57 @@ constexpr int NT = VMC_NT;
 constexpr int NWARP = NT / 32;
 
 // In place on an N x N row-major matrix (row stride lda) in shared or global
-// memory; column-parallel elimination (coalesced, bank-conflict free).
+// memory.  Two barriers per elimination step:
+//   (P, B) one warp takes the pivot of column k from the per-warp candidates
+//       (largest |a|, ties: lowest row), forms 1/pivot, the multipliers
+//       m_i = a_ik / pivot (pivot row swapped in, m_k = 0, kept negated so
+//       the update is one FMA) and the raw pivot row, swaps rows k and p and
+//       scales row k, so the FP64 work outside the update is one warp's;
+//   (E) a_ic -= m_i r_c over all entries, spread flat over the threads in
+//       whole warps; before it, each thread forms the updated value of its
+//       row of column k+1 once more (one FMA, from a copy of the column taken
+//       in (B)) for the next step's pivot candidates, reduced per warp by
+//       integer compares of |a|'s bit patterns, so the next pivot search
+//       needs no barrier of its own.
 struct GJShared {
   double val[NWARP];
   double amax[NWARP];
-  int idx[NWARP];
-  int piv;
+  unsigned long long ckey[2][NWARP];   // per-warp pivot candidates (|a| bits) ...
+  int cidx[2][NWARP];                  // ... and their rows, double-buffered by step
   int bad;
   int sign;
   double logdet;
   double pmin, pmax;   // smallest / largest |pivot|
-  double ipiv;
-  double colk[VMC_MAX_N];   // pivot column of the current step (row k zeroed)
-  double rowk[VMC_MAX_N];   // scaled pivot row of the current step (column k zeroed)
+  double ipiv;         // 1 / pivot of the current step
+  double colk[VMC_MAX_N];   // negated multipliers -m_i of the current step (m_k = 0)
+  double rowk[VMC_MAX_N];   // raw pivot row of the current step
+  double coln[VMC_MAX_N];   // column k+1 before the current step's update
   double apiv[VMC_MAX_N];   // |pivot| of every step
   double pminw[NWARP];
 };
+
+// |a| as an ordered integer key; NaN below every number (never a pivot)
+__device__ __forceinline__ unsigned long long pivot_key(double a) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+  return b > 0x7FF0000000000000ull ? 0ull : b + 1ull;
+}
+
+// warp-wide largest key (ties: lowest row); lane 0 records it in slot buf
+__device__ __forceinline__ void pivot_candidates(unsigned long long key, int row, GJShared &g,
+                                                 int buf) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, o);
+    const int orow = __shfl_xor_sync(0xffffffffu, row, o);
+    if (ok > key || (ok == key && orow < row)) {
+      key = ok;
+      row = orow;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    g.ckey[buf][threadIdx.x >> 5] = key;
+    g.cidx[buf][threadIdx.x >> 5] = row;
+  }
+}
 
 __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, GJShared &g) {
   const int tid = threadIdx.x;
@@ -39,86 +74,104 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
     g.pmin = 1e300;
     g.pmax = 0.0;
   }
-  __syncthreads();
-  for (int k = 0; k < N; ++k) {
-    // (1) copy column k and find the pivot among rows >= k
-    double v = -1.0;
-    int vi = N;
+  // candidates of column 0
+  {
+    unsigned long long key = 0ull;
+    int row = N;
     for (int i = tid; i < N; i += NT) {
-      const double a = A[(size_t)i * lda + k];
-      g.colk[i] = a;
-      if (i >= k && fabs(a) > v) {
-        v = fabs(a);
-        vi = i;
+      const unsigned long long kk = pivot_key(A[(size_t)i * lda]);
+      if (kk > key) {
+        key = kk;
+        row = i;
       }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, vi, o);
-      if (ov > v || (ov == v && oi < vi)) {
-        v = ov;
-        vi = oi;
-      }
+    pivot_candidates(key, row, g, 0);
+  }
+  __syncthreads();
+  const int qn = NT / N, rn = NT - (NT / N) * N;
+  auto adv = [&](int &ii, int &cc) {
+    ii += qn;
+    cc += rn;
+    if (cc >= N) {
+      cc -= N;
+      ++ii;
     }
-    if ((tid & 31) == 0) {
-      g.val[tid >> 5] = v;
-      g.idx[tid >> 5] = vi;
-    }
-    __syncthreads();
-    // (2) one thread: pivot row p, swap it into the pivot column copy, 1/pivot
-    if (tid == 0) {
-      double bv = g.val[0];
-      int bi = g.idx[0];
-      for (int q = 1; q < NWARP; ++q)
-        if (g.val[q] > bv || (g.val[q] == bv && g.idx[q] < bi)) {
-          bv = g.val[q];
-          bi = g.idx[q];
+  };
+  for (int k = 0; k < N; ++k) {
+    const int buf = k & 1;
+    // (P) + (B) by warp 0 while the others wait: the pivot from the per-warp
+    // candidates, 1/pivot, the negated multipliers (pivot row swapped in), the
+    // inverse's column k, the raw pivot row; rows k and p swapped and row k
+    // scaled.
+    if (tid < 32) {
+      unsigned long long bk = g.ckey[buf][0];
+      int p = g.cidx[buf][0];
+      for (int q = 1; q < NWARP; ++q) {
+        const unsigned long long kq = g.ckey[buf][q];
+        const int iq = g.cidx[buf][q];
+        if (kq > bk || (kq == bk && iq < p)) {
+          bk = kq;
+          p = iq;
         }
-      if (!(bv > 0.0) || bi >= N) {
-        g.bad = 1;
-        bi = k;
       }
-      g.piv = bi;
-      perm[k] = bi;
-      const double piv = g.colk[bi];
-      g.colk[bi] = g.colk[k];
-      g.colk[k] = 0.0;   // row k is scaled, not eliminated
-      g.ipiv = 1.0 / piv;
-      g.apiv[k] = fabs(piv);   // log|det| is summed after the elimination
-      if ((piv < 0.0) != (bi != k)) g.sign = -g.sign;
+      if (bk <= 1ull || p >= N) {   // zero (key 1) or no finite entry: singular
+        if (tid == 0) g.bad = 1;
+      } else {
+        const double piv = A[(size_t)p * lda + k];
+        const double ipiv = 1.0 / piv;
+        if (tid == 0) {
+          perm[k] = p;
+          g.ipiv = ipiv;
+          g.apiv[k] = fabs(piv);   // log|det| is summed after the elimination
+          if ((piv < 0.0) != (p != k)) g.sign = -g.sign;
+        }
+        const double nipiv = -ipiv;   // negated multipliers: the update is one FMA
+        for (int i = tid; i < N; i += 32) {
+          const double a = (i == k) ? 0.0 : A[(size_t)(i == p ? k : i) * lda + k];
+          g.colk[i] = a * nipiv;
+        }
+        __syncwarp();
+        // the inverse's column k: -m_i, and 1/pivot at row k (rowk_k = 0 below
+        // leaves it through the update)
+        for (int i = tid; i < N; i += 32) A[(size_t)i * lda + k] = (i == k) ? ipiv : g.colk[i];
+        for (int c = tid; c < N; c += 32) {
+          if (c == k) {
+            g.rowk[c] = 0.0;
+            continue;
+          }
+          const double r = A[(size_t)p * lda + c];
+          g.rowk[c] = r;
+          if (p != k) A[(size_t)p * lda + c] = A[(size_t)k * lda + c];
+          A[(size_t)k * lda + c] = r * ipiv;
+        }
+        __syncwarp();
+        // column k+1 as the update below finds it (rows swapped)
+        if (k + 1 < N)
+          for (int i = tid; i < N; i += 32) g.coln[i] = A[(size_t)i * lda + k + 1];
+      }
     }
     __syncthreads();
-    if (g.bad) return;
-    const int p = g.piv;
-    const double ipiv = g.ipiv;
-    // (3a) the new column k, one row per thread (from the copy); for every
-    // column c != k: swap rows k and p, scale row k, keep it in rowk.
-    for (int i = tid; i < N; i += NT) A[(size_t)i * lda + k] = (i == k) ? ipiv : -g.colk[i] * ipiv;
-    for (int c = tid; c < N; c += NT) {
-      if (c == k) {
-        g.rowk[c] = 0.0;   // column k is final: the update below leaves it
-        continue;
+    if (g.bad) return;   // uniform
+    const int k1 = k + 1;
+    // (E0) pivot candidates of column k+1 among rows >= k+1, from the values
+    // the update below stores there (the same FMA), so the next pivot needs
+    // no barrier of its own
+    if (k1 < N) {
+      unsigned long long key = 0ull;
+      int row = N;
+      for (int i = tid; i < N; i += NT) {
+        const double v = fma(g.colk[i], g.rowk[k1], g.coln[i]);
+        const unsigned long long kk = pivot_key(v);
+        const bool t = (i >= k1) & (kk > key);
+        key = t ? kk : key;
+        row = t ? i : row;
       }
-      double rkc = A[(size_t)p * lda + c];
-      if (p != k) A[(size_t)p * lda + c] = A[(size_t)k * lda + c];
-      rkc *= ipiv;
-      A[(size_t)k * lda + c] = rkc;
-      g.rowk[c] = rkc;
+      pivot_candidates(key, row, g, buf ^ 1);
     }
-    __syncthreads();
-    // (3b) A_ic -= colk_i rowk_c over all N x N entries, spread flat over the
-    // threads (whole warps for any N; colk_k = 0 leaves row k), four entries
-    // in flight per thread.
+    // (E) a_ic += (-m_i) r_c over all entries, spread flat over the threads
+    // in whole warps, four entries in flight per thread (m_k = 0 leaves row
+    // k, r_k = 0 leaves column k)
     {
-      const int qn = NT / N, rn = NT - (NT / N) * N;
-      auto adv = [&](int &ii, int &cc) {
-        ii += qn;
-        cc += rn;
-        if (cc >= N) {
-          cc -= N;
-          ++ii;
-        }
-      };
       int i = tid / N, c = tid - (tid / N) * N;
       while (i < N) {
         int i1 = i, c1 = c;
@@ -133,10 +186,10 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
         double *q2 = A + (size_t)(b2 ? i2 : i) * lda + (b2 ? c2 : c);
         double *q3 = A + (size_t)(b3 ? i3 : i) * lda + (b3 ? c3 : c);
         double a0 = *q0, a1 = *q1, a2 = *q2, a3 = *q3;
-        a0 -= g.colk[i] * g.rowk[c];
-        if (b1) a1 -= g.colk[i1] * g.rowk[c1];
-        if (b2) a2 -= g.colk[i2] * g.rowk[c2];
-        if (b3) a3 -= g.colk[i3] * g.rowk[c3];
+        a0 = fma(g.colk[i], g.rowk[c], a0);
+        a1 = fma(g.colk[i1], g.rowk[c1], a1);
+        a2 = fma(g.colk[i2], g.rowk[c2], a2);
+        a3 = fma(g.colk[i3], g.rowk[c3], a3);
         *q0 = a0;
         if (b1) *q1 = a1;
         if (b2) *q2 = a2;

@@ -715,14 +715,15 @@ __device__ __forceinline__ void df_row_axpy(float *rh, float *rl, const float *x
   }
 }
 
-// From-scratch inverse of the mixed form in double-float: the Gauss-Jordan
-// elimination of vmc_gj::gj_invert (partial pivoting, in place) on hi + lo
-// words, every multiply-subtract an error-free FP32 sequence (df_fma).  The
-// pivot is the largest |hi| of the column (ties: lowest row).  GB300's FP64
-// pipe runs at 1/64 of the FP32 rate, and a double-float multiply-add costs
-// about fifteen FP32 operations, so the elimination runs several times
-// faster than in FP64 at about 2^-46 rounding, the precision the sweep's
-// updates keep.  The scalars of the determinant stay FP64.
+// From-scratch inverse in double-float, the mixed form's opt-in alternative
+// to the FP64 elimination (VMC_REBUILD_DOUBLE_FLOAT): Gauss-Jordan with
+// partial pivoting, in place, on hi + lo words, every multiply-subtract an
+// error-free FP32 sequence (df_fma).  The pivot is the largest |hi| of the
+// column (ties: lowest row).  GB300's FP64 pipe runs at 1/64 of the FP32
+// rate and a double-float multiply-add costs about fifteen FP32 operations,
+// so the elimination is faster than in FP64 at about 2^-46 rounding, the
+// precision the sweep's updates keep.  The scalars of the determinant stay
+// FP64.
 struct GJdf {
   double val[NWARP];
   double amax[NWARP];
@@ -827,33 +828,31 @@ __device__ void gj_invert_df(float *Ah, float *Al, int lda, int N, int *perm, GJ
     }
     __syncthreads();
     // (3b) A_ic -= colk_i rowk_c: thread c < N takes column c (c != k: rowk_k
-    // = 0 leaves column k) over all rows, four at a time with the pivot
+    // = 0 leaves column k) over all rows, eight at a time with the pivot
     // column read by 16-byte broadcast loads; colk_k = 0 leaves the value of
     // row k unchanged.
     if (tid < N && tid != k) {
       const float rh = g.rh[tid], rl = g.rl[tid];
       float *qh = Ah + tid, *ql = Al + tid;
       int i = 0;
-      for (; i + 4 <= N; i += 4) {
-        float c0, c1, c2, c3, e0, e1, e2, e3;
-        ld4(g.ch + i, c0, c1, c2, c3);
-        ld4(g.cl + i, e0, e1, e2, e3);
-        float h0 = qh[i * lda], h1 = qh[(i + 1) * lda], h2 = qh[(i + 2) * lda],
-              h3 = qh[(i + 3) * lda];
-        float l0 = ql[i * lda], l1 = ql[(i + 1) * lda], l2 = ql[(i + 2) * lda],
-              l3 = ql[(i + 3) * lda];
-        df_fma(h0, l0, -c0, -e0, rh, rl);
-        df_fma(h1, l1, -c1, -e1, rh, rl);
-        df_fma(h2, l2, -c2, -e2, rh, rl);
-        df_fma(h3, l3, -c3, -e3, rh, rl);
-        qh[i * lda] = h0;
-        qh[(i + 1) * lda] = h1;
-        qh[(i + 2) * lda] = h2;
-        qh[(i + 3) * lda] = h3;
-        ql[i * lda] = l0;
-        ql[(i + 1) * lda] = l1;
-        ql[(i + 2) * lda] = l2;
-        ql[(i + 3) * lda] = l3;
+      for (; i + 8 <= N; i += 8) {
+        float c[8], e[8], h[8], l[8];
+        ld4(g.ch + i, c[0], c[1], c[2], c[3]);
+        ld4(g.ch + i + 4, c[4], c[5], c[6], c[7]);
+        ld4(g.cl + i, e[0], e[1], e[2], e[3]);
+        ld4(g.cl + i + 4, e[4], e[5], e[6], e[7]);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          h[r] = qh[(i + r) * lda];
+          l[r] = ql[(i + r) * lda];
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) df_fma(h[r], l[r], -c[r], -e[r], rh, rl);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          qh[(i + r) * lda] = h[r];
+          ql[(i + r) * lda] = l[r];
+        }
       }
       for (; i < N; ++i) {
         float h = qh[i * lda], l = ql[i * lda];
@@ -1723,7 +1722,7 @@ __global__ void k_expand_mlp(SysDev S) {
 }
 
 // From-scratch inverse of M (Gauss-Jordan with partial pivoting, in place in
-// shared memory: FP64, or double-float in the mixed form), log|det M| and its
+// shared memory: FP64, or double-float by the mixed form's opt-in), log|det M| and its
 // sign, Jastrow field and occupation table.  With only_due, only walkers
 // whose accepted-move count since the last inverse reached due_threshold are
 // rebuilt, and the drift max|M^-1_updated - M^-1_fresh| / max|M^-1_fresh| is
@@ -1736,9 +1735,14 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ SysDev S;
   __shared__ int s_item;
-  // FP64 elimination for the plain form, double-float for the mixed form
-  constexpr bool DF = std::is_same<T, float>::value;
-  __shared__ typename std::conditional<DF, GJdf, vmc_gj::GJShared>::type g;
+  __shared__ double red_d[NWARP], red_a[NWARP];
+  // FP64 elimination; the mixed form's opt-in double-float one
+  // (VMC_REBUILD_DOUBLE_FLOAT) shares the scratch
+  constexpr bool F32 = std::is_same<T, float>::value;
+  __shared__ union {
+    vmc_gj::GJShared d;
+    GJdf f;
+  } gs;
   auto next_item = [&]() -> int {
     __syncthreads();   // every thread has read the previous item
     if (threadIdx.x == 0) s_item = atomicAdd(ctr, 1);
@@ -1751,7 +1755,8 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
     if (only_due && systems[wk.x].acc_since[w] < due_threshold) continue;
     load_sys(&S, systems + wk.x);
     const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
-    // N x ldm matrix: FP64 words, or (mixed form) hi words then lo words
+    const bool use_df = F32 && S.rebuild_df;
+    // N x ldm matrix: FP64 words, or (double-float) hi words then lo words
     double *A = (double *)smem_raw;
     float *Ah = (float *)smem_raw, *Al = Ah + (size_t)N * ldm;
     int *ele = (int *)(A + (size_t)N * ldm);        // Ne
@@ -1761,30 +1766,32 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
     for (int q = tid; q < N * N; q += NT) {
       const int n = q / N, m = q - n * N;
       const double f = S.f64[(size_t)ele[n] * Ns + ele[N + m]];
-      if constexpr (DF)
+      if (use_df)
         df_split(f, Ah[n * ldm + m], Al[n * ldm + m]);
       else
         A[n * ldm + m] = f;
     }
     __syncthreads();
-    if constexpr (DF)
-      gj_invert_df(Ah, Al, ldm, N, perm, g);
+    if (use_df)
+      gj_invert_df(Ah, Al, ldm, N, perm, gs.f);
     else
-      vmc_gj::gj_invert(A, ldm, N, perm, g);
+      vmc_gj::gj_invert(A, ldm, N, perm, gs.d);
+    const int g_bad = use_df ? gs.f.bad : gs.d.bad;
+    const int g_sign = use_df ? gs.f.sign : gs.d.sign;
+    const double g_logdet = use_df ? gs.f.logdet : gs.d.logdet;
+    const double g_pmin = use_df ? gs.f.pmin : gs.d.pmin;
+    const double g_pmax = use_df ? gs.f.pmax : gs.d.pmax;
     // the fresh inverse's entry q (FP64 value)
     auto fresh_at = [&](int q) -> double {
-      if constexpr (DF)
-        return (double)Ah[q] + (double)Al[q];
-      else
-        return A[q];
+      return use_df ? (double)Ah[q] + (double)Al[q] : A[q];
     };
     const size_t nb = minv_bytes(N, ldm, sizeof(T));
     T *dst = (T *)((unsigned char *)S.minv + (size_t)w * nb);
     // mixed form: low words of the double-float inverse (zero while delayed
     // updates, which keep FP32 words only, are on)
-    float *dlo = (sizeof(T) == 4 && S.minv_lo) ? (float *)((unsigned char *)S.minv_lo + (size_t)w * nb)
-                                               : nullptr;
-    if (!g.bad) {
+    float *dlo = (F32 && S.minv_lo) ? (float *)((unsigned char *)S.minv_lo + (size_t)w * nb)
+                                    : nullptr;
+    if (!g_bad) {
       if (only_due) {
         double dmax = 0.0, amax = 0.0;
         for (int q = tid; q < N * N; q += NT) {
@@ -1799,26 +1806,29 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
           amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
         }
         if ((tid & 31) == 0) {
-          g.val[tid >> 5] = dmax;
-          g.amax[tid >> 5] = amax;
+          red_d[tid >> 5] = dmax;
+          red_a[tid >> 5] = amax;
         }
         __syncthreads();
         if (tid == 0) {
           double d = 0.0, a = 0.0;
           for (int q = 0; q < NWARP; ++q) {
-            d = fmax(d, g.val[q]);
-            a = fmax(a, g.amax[q]);
+            d = fmax(d, red_d[q]);
+            a = fmax(a, red_a[q]);
           }
           S.drift[w] = fmax(S.drift[w], (a > 0.0) ? d / a : d);
         }
         __syncthreads();
       }
+      const bool keep_lo = dlo && S.delay_k <= 1;
       for (int q = tid; q < N * ldm; q += NT) {
-        if constexpr (DF) {
+        if (use_df) {
           dst[q] = Ah[q];
-          if (dlo) dlo[q] = (S.delay_k > 1) ? 0.f : Al[q];
+          if (dlo) dlo[q] = keep_lo ? Al[q] : 0.f;
         } else {
-          dst[q] = (T)A[q];
+          const T h = (T)A[q];
+          dst[q] = h;
+          if (dlo) dlo[q] = keep_lo ? (float)(A[q] - (double)h) : 0.f;
         }
       }
     }
@@ -1867,14 +1877,14 @@ __global__ void __launch_bounds__(NT) k_init(const SysDev *systems, const int2 *
     if (tid == 0) {
       S.acc_since[w] = 0;
       if (only_due) S.n_rec[w] += 1;
-      if (g.bad) {
+      if (g_bad) {
         S.status[w] |= VMC_ST_SINGULAR;
       } else {
         S.status[w] &= ~(VMC_ST_SINGULAR | VMC_ST_ILLCOND);
-        if (g.pmin < 1e-12 * g.pmax) S.status[w] |= VMC_ST_ILLCOND;
-        S.logdet[w] = g.logdet;
-        S.detsign[w] = g.sign;
-        if (!isfinite(g.logdet)) S.status[w] |= VMC_ST_NUMERIC;
+        if (g_pmin < 1e-12 * g_pmax) S.status[w] |= VMC_ST_ILLCOND;
+        S.logdet[w] = g_logdet;
+        S.detsign[w] = g_sign;
+        if (!isfinite(g_logdet)) S.status[w] |= VMC_ST_NUMERIC;
       }
     }
     __syncthreads();

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvmc.so")
 
 FP64, MIXED = 0, 1
+REBUILD_FP64, REBUILD_DOUBLE_FLOAT = 0, 1
 FORCE_STATIC_MAX_DOUBLES = 1 << 20
 CHOLESKY, CG, CG_DENSE, MIXED_IR = 0, 1, 2, 3
 S_KERNELS = ("none", "fp64_simt", "tcgen05_tma_persistent", "tcgen05_tiles")
@@ -43,7 +44,7 @@ class VmcLayout(C.Structure):
 class VmcOpts(C.Structure):
     _fields_ = [("n_walkers", C.c_int32), ("seed", C.c_uint64), ("precision", C.c_int32),
                 ("delay_k", C.c_int32), ("recompute_every", C.c_int32),
-                ("max_samples", C.c_int32), ("stream", C.c_void_p)]
+                ("max_samples", C.c_int32), ("stream", C.c_void_p), ("rebuild", C.c_int32)]
 
 
 class VmcStats(C.Structure):
@@ -180,7 +181,7 @@ class Context:
     """One vmc_ctx: a single system or a batch of systems."""
 
     def __init__(self, problems, n_walkers, seed=1, precision=FP64, max_samples=1,
-                 delay_k=0, recompute_every=0, stream=None):
+                 delay_k=0, recompute_every=0, stream=None, rebuild=REBUILD_FP64):
         L = load()
         probs = problems if isinstance(problems, (list, tuple)) else [problems]
         self.problems = list(probs)
@@ -189,7 +190,7 @@ class Context:
         arrs = [_Arrays(p) for p in probs]
         opts = VmcOpts(int(n_walkers), int(seed) & 0xFFFFFFFFFFFFFFFF, int(precision),
                        int(delay_k), int(recompute_every), int(max_samples),
-                       C.c_void_p(stream) if stream else None)
+                       C.c_void_p(stream) if stream else None, int(rebuild))
         h = C.c_void_p()
         if len(probs) == 1:
             rc = L.vmc_create(C.byref(h), C.byref(arrs[0].model), int(probs[0].Ne),

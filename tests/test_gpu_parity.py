@@ -98,10 +98,12 @@ def test_inverse_and_logdet(vmc, name):
             assert np.allclose(M @ minv, np.eye(N), atol=1e-9)
 
 
+@pytest.mark.parametrize("rebuild", ["fp64", "double_float"])
 @pytest.mark.parametrize("name", ["ring8", "square8", "ring6_apbc", "heis4", "j1j2_4"])
-def test_mixed_form_double_float_inverse(vmc, name):
-    """The mixed form's from-scratch inverse (double-float Gauss-Jordan, hi +
-    lo words) against the oracle's X^-1 and Pfaffian: relative error within
+def test_mixed_form_double_float_inverse(vmc, name, rebuild):
+    """The mixed form's from-scratch inverse, stored as hi + lo FP32 words,
+    from the FP64 Gauss-Jordan (default) or the double-float one (opt-in),
+    against the oracle's X^-1 and Pfaffian: relative error within
     1e-12 cond(M) (about 2^-46 rounding amplified by the condition number),
     the same sign, log|det| within 1e-12 cond(M) + 1e-11."""
     p = with_correlations(small_problems()[name])
@@ -109,7 +111,8 @@ def test_mixed_form_double_float_inverse(vmc, name):
     cfg = good_configs(p, W, 100)
     wf = Wavefunction(p)
     N = p.N
-    with vmc.Context(p, W, seed=7, precision=vmc.MIXED) as ctx:
+    mode = vmc.REBUILD_FP64 if rebuild == "fp64" else vmc.REBUILD_DOUBLE_FLOAT
+    with vmc.Context(p, W, seed=7, precision=vmc.MIXED, rebuild=mode) as ctx:
         ctx.set_configs(cfg)
         for w in range(W):
             minv, ld, sg = ctx.get_inverse(w)
@@ -127,7 +130,8 @@ def test_mixed_form_double_float_inverse(vmc, name):
             assert sg * (-1) ** (N * (N - 1) // 2) == s_pf
 
 
-def test_mixed_form_double_float_inverse_16x16(vmc):
+@pytest.mark.parametrize("rebuild", ["fp64", "double_float"])
+def test_mixed_form_double_float_inverse_16x16(vmc, rebuild):
     """Full size (16x16 Hubbard, N = 112): the mixed form's rebuilt inverses
     of the library's own seeded placements against the FP64 form's."""
     p = I.square16_hubbard()
@@ -136,7 +140,8 @@ def test_mixed_form_double_float_inverse_16x16(vmc):
         ele, _ = c64.get_configs()
         ref = [c64.get_inverse(w) for w in range(W)]
     N = p.N
-    with vmc.Context(p, W, seed=3, precision=vmc.MIXED) as c32:
+    mode = vmc.REBUILD_FP64 if rebuild == "fp64" else vmc.REBUILD_DOUBLE_FLOAT
+    with vmc.Context(p, W, seed=3, precision=vmc.MIXED, rebuild=mode) as c32:
         c32.set_configs(ele)
         for w in range(W):
             minv, ld, sg = c32.get_inverse(w)
