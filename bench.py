@@ -40,11 +40,12 @@ if ROOT not in sys.path:
 SMS, FP32_LANES, FP64_UNITS, SM_MAX_MHZ = 152, 128, 2, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
 FP64_PEAK_TFLOPS = SMS * FP64_UNITS * 2 * SM_MAX_MHZ * 1e6 / 1e12
-# DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernels at 4096 walkers (profiles/k_sample_float_hubbard16x16_w4096.md,
-# profiles/k_init_float_hubbard16x16_w4096.md); proportional to walkers.
-TRAFFIC_SWEEP_4096 = 225.731328e6 + 181.081344e6
-TRAFFIC_INIT_4096 = 6.181120e6 + 160.923392e6
+# DRAM bytes (read + write) per launch from one ncu capture (one-pass
+# metrics) of the current kernels at 4096 walkers
+# (profiles/dram_k_sample_k_init_hubbard16x16_w4096.md): a sweep-only launch
+# of k_sample<float> and the full rebuild launch of k_init<float>.
+TRAFFIC_SWEEP_ONLY_4096 = 433.96e6 + 368.55e6
+TRAFFIC_INIT_4096 = 6.44e6 + 366.92e6
 # k_corr<float> (pair correlations), DRAM read + write per launch at 4096
 # walkers (profiles/k_corr_float_hubbard16x16_w4096.md).
 TRAFFIC_CORR_4096 = 229.7047e6
@@ -82,6 +83,8 @@ def parse():
                          "size and print their energies (one JSON line) instead of the bench")
     ap.add_argument("--learned-steps", type=int, default=60)
     ap.add_argument("--learned-eval", type=int, default=6)
+    ap.add_argument("--learned-finetune", type=int, default=40,
+                    help="warm-start protocol: SR steps after the plain state's training")
     ap.add_argument("--sweep-only", type=int, default=8)
     return ap.parse_args()
 
@@ -268,6 +271,54 @@ def cpu_baseline_configs(pool, cores, seconds=4.0):
     return out
 
 
+def projected_sampling(vmc, torch, stream, inputs, W=304, calls=2):
+    """Momentum projection at N_g = Ns on the 16x16 workload (mixed form):
+    all 256 translations at K = 0 (Sec. 3.2.2, Eq. momP; App. A signs), one
+    M_g^-1 per translation per walker in HBM (12.8 MB per walker).  Timed:
+    vmc_sample(0, 1, 1) calls (one sweep and one measurement per walker, with
+    the periodic rebuilds of every M_g^-1), CUDA events on the stream.
+    Roofline of the projected sweep kernel on its algorithmic bytes: every
+    proposal reads one column or row of each M_g^-1 (N_g N 4 B), every accepted
+    move reads and writes all of them (N_g 2 N^2 4 B)."""
+    prob = inputs.square16_hubbard()
+    perm, sign = inputs.translation_ops(prob.lat)
+    G, N = perm.shape[0], prob.N
+    ctx = vmc.Context(prob, W, seed=7, precision=vmc.MIXED, max_samples=1,
+                      stream=stream.cuda_stream)
+    ctx.set_projection(perm, sign, np.full(G, 1.0 / G))
+    ctx.sample(1, 0, 0)
+    ctx.enable_timing(True)
+    ctx.kernel_times()
+    s0 = ctx.measure()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(calls):
+        ctx.sample(0, 1, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = ctx.kernel_times()
+    s1 = ctx.measure()
+    grid, per_sm, smem = ctx.sweep_launch()
+    ctx.close()
+    props = s1["n_proposals"] - s0["n_proposals"]
+    acc = s1["n_accepted"] - s0["n_accepted"]
+    sweep_ms, sweep_n = kt["sweep"]
+    b = 4.0 * G * N * props + 8.0 * G * N * N * acc
+    hbm, src = hbm_peak_gbs()
+    ach = b / (sweep_ms * 1e-3) / 1e9
+    return {"walkers": W, "operations": G, "characters": "K = 0", "calls": calls,
+            "ms_per_call": ms / calls, "proposals_per_s": props / (ms * 1e-3),
+            "sweep_kernel_ms_per_launch": sweep_ms / max(sweep_n, 1),
+            "rebuild_ms_per_call": kt["init"][0] / calls,
+            "acceptance": acc / max(props, 1), "sweep_launch": {"grid": grid, "ctas_per_sm": per_sm,
+                                                                "smem_bytes": smem},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": None, "kernel": "k_proj_sample<float>",
+                         "bytes_rule": "N_g N 4 B per proposal + N_g 2 N^2 4 B per accepted move",
+                         "peak_source": src}}
+
+
 def other_workloads(vmc, torch, stream, steps=5):
     """The other configured workloads, each timed on the device (CUDA events
     on the stream) after the headline bench:
@@ -278,7 +329,8 @@ def other_workloads(vmc, torch, stream, steps=5):
               form, FP64 recompute every 64 accepted moves, 4 samples, and
               one SR step of every system (vmc_sr_step_all, mixed solve);
       j1j2    C4: 16x16 J1-J2, full f (N_p = 65,536), 8192 samples: one dense
-              S build by the split-BF16 tensor-core kernel."""
+              S build by the split-BF16 tensor-core kernel;
+      projection_16x16: sampling with all 256 translations (projected_sampling)."""
     from paper_1711_11418_gb300 import inputs
     res = {}
 
@@ -322,6 +374,7 @@ def other_workloads(vmc, torch, stream, steps=5):
         "systems": len(probs), "walkers_per_system": 64, "samples_per_walker": 4,
         "sizes_L": sorted({int(round(p.Ns ** 0.5)) for p in probs}), "dtype": "f32+f64"}
     ctx.close()
+    res["projection_16x16"] = projected_sampling(vmc, torch, stream, inputs)
     prob = inputs.j1j2_heisenberg()
     ctx = vmc.Context(prob, 1024, seed=3, precision=vmc.MIXED, max_samples=8,
                       stream=stream.cuda_stream)
@@ -676,6 +729,7 @@ def run_ours(args):
     b_sw = sweep_bytes(sw, N, 4) / max(sw_n, 1)
     roof_sweep_only = {"bound": "hbm", "achieved": b_sw / t_sw / 1e9, "peak": hbm, "unit": "GB/s",
                        "frac": b_sw / t_sw / 1e9 / hbm, "kernel": "k_sample<float>, sweeps only",
+                       "traffic": TRAFFIC_SWEEP_ONLY_4096 * scale,
                        "launches": sw_n, "ms_per_launch": t_sw * 1e3,
                        "algorithmic_bytes_per_launch": b_sw,
                        "acceptance": sw["n_accepted"] / max(sw["n_proposals"], 1),
@@ -687,6 +741,7 @@ def run_ours(args):
     ach_init = 2.0 * N ** 3 * n_inv / max(init_ms * 1e-3, 1e-12) / 1e12
     roof_init = {"bound": "alu", "achieved": ach_init, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                  "frac": ach_init / FP64_PEAK_TFLOPS, "traffic": TRAFFIC_INIT_4096 * scale,
+                 "traffic_launch": "the full rebuild of all walkers after an SR step",
                  "kernel": "k_init<float> (FP64 from-scratch inverses)",
                  "ms_in_timed_region": init_ms,
                  "peak_source": "derived: 152 SMs x 2 FP64 FMA units x 2 x 2070 MHz "
@@ -752,11 +807,16 @@ def run_learned(args):
     """The learned part at its configured size: 16x16 Hubbard, U/t = 8,
     Ne = 224, the Gutzwiller-Jastrow-Pfaffian state times an MLP correlation
     factor (512 occupations -> 1024 tanh units -> 1, BF16 weights in the
-    sweep, N(0, 0.01^2) initial weights), 4096 walkers, SR over all 527,406
-    parameters by SR-CG (S never formed, FP32 sample matrix, FP64 CG); the
-    plain state gets the same walkers, samples per step, steps and solver.
-    Afterwards both are sampled with fixed parameters and their energies per
-    site are reported with standard errors from per-walker means."""
+    sweep, N(0, 0.01^2) initial weights), 4096 walkers, SR by SR-CG (S never
+    formed, FP32 sample matrix, FP64 CG).  Two protocols with the same
+    walkers, samples per step, SR steps and solver for both states:
+      cold: both trained from the same initial state for `learned_steps`;
+      warm: the plain state trained for `learned_steps`, then continued for
+        `learned_finetune` more steps, beside the MLP state that starts from
+        the trained plain parameters (and its walkers) and trains all
+        527,406 parameters for the same `learned_finetune` steps.
+    Afterwards each state is sampled with fixed parameters; energies per site
+    with standard errors from per-walker means."""
     import torch
     from paper_1711_11418_gb300 import build, inputs, vmc
     build.build()
@@ -764,43 +824,81 @@ def run_learned(args):
     W, S = args.walkers, args.samples
     sr = dict(dtau=0.05, shift_rel=1e-3, shift_abs=1e-4, solver=vmc.CG, cg_eps=1e-4,
               cg_kmax=200)
-    probs = {"plain": inputs.square16_hubbard(),
-             "mlp": inputs.square16_hubbard_mlp(hidden=1024)}
-    out = {}
-    for name, prob in probs.items():
-        t0 = time.perf_counter()
-        ctx = vmc.Context(prob, W, seed=2024, precision=vmc.MIXED, max_samples=S,
-                          recompute_every=args.recompute)
-        ctx.sample(args.equil, 0, 0)
+    plain_p, mlp_p = inputs.square16_hubbard(), inputs.square16_hubbard_mlp(hidden=1024)
+
+    def train(ctx, prob, steps):
         traj, iters = [], []
-        for _ in range(args.learned_steps):
+        for _ in range(steps):
             ctx.sample(0, S, 1)
             rep = ctx.sr_step(**sr)
             traj.append(rep["energy"] / prob.Ns)
             iters.append(rep["cg_iters"])
-        t_train = time.perf_counter() - t0
+        return traj, iters
+
+    def evaluate(ctx, prob):
         wm = []
         for _ in range(args.learned_eval):
             ctx.sample(0, S, 1)
             wm.append(ctx.get_samples(with_O=False)[0].reshape(W, S).mean(axis=1))
         wm = np.mean(wm, axis=0) / prob.Ns
+        return float(wm.mean()), float(wm.std(ddof=1) / math.sqrt(W))
+
+    def record(prob, e, se, t, traj, iters):
+        return {"energy_per_site": e, "stderr": se, "Np": prob.Np, "train_seconds": round(t, 2),
+                "cg_iterations_mean": float(np.mean(iters)) if iters else 0.0,
+                "trajectory_every_10_steps": [round(x, 6) for x in traj[::10]]}
+
+    def gain(a, b):
+        g = a["energy_per_site"] - b["energy_per_site"]
+        sg = math.hypot(a["stderr"], b["stderr"])
+        return {"gain_per_site": g, "gain_sigma": sg, "gain_significant_3sigma": bool(g > 3 * sg)}
+
+    out = {}
+    # cold start: both from the same initial state
+    cold = {}
+    plain_ctx = None
+    for name, prob in (("plain", plain_p), ("mlp", mlp_p)):
+        t0 = time.perf_counter()
+        ctx = vmc.Context(prob, W, seed=2024, precision=vmc.MIXED, max_samples=S,
+                          recompute_every=args.recompute)
+        ctx.sample(args.equil, 0, 0)
+        traj, iters = train(ctx, prob, args.learned_steps)
+        t = time.perf_counter() - t0
+        e, se = evaluate(ctx, prob)
+        cold[name] = record(prob, e, se, t, traj, iters)
+        if name == "plain":
+            plain_ctx = ctx
+        else:
+            ctx.close()
+    out["cold"] = {**cold, **gain(cold["plain"], cold["mlp"])}
+    # warm start: the MLP state from the trained plain state
+    warm = {}
+    if args.learned_finetune > 0:
+        params = plain_ctx.get_params()
+        ele, _ = plain_ctx.get_configs()
+        t0 = time.perf_counter()
+        traj, iters = train(plain_ctx, plain_p, args.learned_finetune)
+        e, se = evaluate(plain_ctx, plain_p)
+        warm["plain"] = record(plain_p, e, se, time.perf_counter() - t0, traj, iters)
+        pm = mlp_p.params.copy()
+        pm[:plain_p.Np] = params          # g, v, f first; the MLP block keeps its start
+        t0 = time.perf_counter()
+        ctx = vmc.Context(mlp_p.copy_with(params=pm), W, seed=2025, precision=vmc.MIXED,
+                          max_samples=S, recompute_every=args.recompute)
+        ctx.set_configs(ele)
+        traj, iters = train(ctx, mlp_p, args.learned_finetune)
+        e, se = evaluate(ctx, mlp_p)
+        warm["mlp"] = record(mlp_p, e, se, time.perf_counter() - t0, traj, iters)
         ctx.close()
-        out[name] = {"energy_per_site": float(wm.mean()),
-                     "stderr": float(wm.std(ddof=1) / math.sqrt(W)),
-                     "Np": prob.Np, "train_seconds": round(t_train, 2),
-                     "cg_iterations_mean": float(np.mean(iters)),
-                     "trajectory_every_10_steps": [round(x, 6) for x in traj[::10]]}
-    gain = out["plain"]["energy_per_site"] - out["mlp"]["energy_per_site"]
-    sig = math.hypot(out["plain"]["stderr"], out["mlp"]["stderr"])
+        out["warm"] = {**warm, **gain(warm["plain"], warm["mlp"])}
+    plain_ctx.close()
     print(json.dumps({"what": "learned part: plain Gutzwiller-Jastrow-Pfaffian vs x MLP "
                               "correlation factor, same sample budget",
                       "workload": "hubbard_16x16_U8_Ne224_apbc, MLP 512->1024->1",
-                      "walkers": W, "samples_per_step": W * S, "sr_steps": args.learned_steps,
+                      "walkers": W, "samples_per_step": W * S,
+                      "sr_steps": args.learned_steps, "finetune_steps": args.learned_finetune,
                       "sr": {k: v for k, v in sr.items() if k != "solver"} | {"solver": "sr_cg"},
-                      "eval_samples_per_walker": args.learned_eval * S,
-                      "plain": out["plain"], "mlp": out["mlp"],
-                      "gain_per_site": gain, "gain_sigma": sig,
-                      "gain_significant_3sigma": bool(gain > 3 * sig)}))
+                      "eval_samples_per_walker": args.learned_eval * S, **out}))
 
 
 def main():

@@ -74,6 +74,23 @@ def square(Lx: int, Ly: int, bc_x: int = 1, bc_y: int = 1) -> Lattice:
     return Lattice(Lx, Ly, bc_x, bc_y)
 
 
+def translation_ops(lat: Lattice):
+    """Every lattice translation R = (dx, dy) as a site map with boundary
+    signs (App. A): perm[g, i] = the site of i + R folded into the cell,
+    sign[g, i] = the sign its folding picks up; g = dx + Lx dy.  Geometry
+    only: the operations of vmc_set_projection's momentum projection."""
+    G = lat.Ns
+    perm = np.zeros((G, lat.Ns), np.int32)
+    sign = np.ones((G, lat.Ns), np.int8)
+    for dy in range(lat.Ly):
+        for dx in range(lat.Lx):
+            g = dx + lat.Lx * dy
+            for i in range(lat.Ns):
+                x, y = lat.xy(i)
+                perm[g, i], sign[g, i] = lat.site(x + dx, y + dy)
+    return perm, sign
+
+
 def _neighbour_vectors(lat: Lattice, order: int):
     """Displacements of nearest (order 1) or next-nearest (order 2) bonds,
     one per undirected bond direction."""

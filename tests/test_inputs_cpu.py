@@ -37,3 +37,20 @@ def test_workload_parameter_counts():
     assert (q.n_g, q.n_v, q.n_f) == (1, 14, 256)
     r = I.ring8_hubbard()
     assert (r.n_g, r.n_v, r.n_f) == (1, 2, 16)
+
+
+def test_translation_ops_match_the_oracle_translations():
+    """inputs.translation_ops (the bench's operation set) against the oracle's
+    translations on periodic and anti-periodic lattices: same site maps and
+    boundary signs, in the same order (g = dx + Lx dy)."""
+    import numpy as np
+    from oracle.projection import translations
+    from paper_1711_11418_gb300 import inputs as I
+    for lat in (I.square(4, 4, -1, -1), I.square(3, 2, 1, -1), I.chain(6, -1)):
+        perm, sign = I.translation_ops(lat)
+        ref = translations(lat)
+        assert perm.shape == (len(ref), lat.Ns)
+        for g, (op, _) in enumerate(ref):
+            assert np.array_equal(perm[g], np.array(op.perm))
+            assert np.array_equal(sign[g], np.array(op.sign, np.int8))
+        assert np.all(np.sort(perm, axis=1) == np.arange(lat.Ns))
