@@ -25,6 +25,9 @@ constexpr int NWARP = NT / 32;
 //       in (B)) for the next step's pivot candidates, reduced per warp by
 //       integer compares of |a|'s bit patterns, so the next pivot search
 //       needs no barrier of its own.
+// Entries of the rank-1 update in flight per thread.
+constexpr int GJ_ILP = 4;
+
 struct GJShared {
   double val[NWARP];
   double amax[NWARP];
@@ -169,33 +172,38 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
       pivot_candidates(key, row, g, buf ^ 1);
     }
     // (E) a_ic += (-m_i) r_c over all entries, spread flat over the threads
-    // in whole warps, four entries in flight per thread (m_k = 0 leaves row
-    // k, r_k = 0 leaves column k)
+    // in whole warps, GJ_ILP entries in flight per thread (m_k = 0 leaves
+    // row k, r_k = 0 leaves column k)
     {
       int i = tid / N, c = tid - (tid / N) * N;
       while (i < N) {
-        int i1 = i, c1 = c;
-        adv(i1, c1);
-        int i2 = i1, c2 = c1;
-        adv(i2, c2);
-        int i3 = i2, c3 = c2;
-        adv(i3, c3);
-        const bool b1 = i1 < N, b2 = i2 < N, b3 = i3 < N;
-        double *q0 = A + (size_t)i * lda + c;
-        double *q1 = A + (size_t)(b1 ? i1 : i) * lda + (b1 ? c1 : c);
-        double *q2 = A + (size_t)(b2 ? i2 : i) * lda + (b2 ? c2 : c);
-        double *q3 = A + (size_t)(b3 ? i3 : i) * lda + (b3 ? c3 : c);
-        double a0 = *q0, a1 = *q1, a2 = *q2, a3 = *q3;
-        a0 = fma(g.colk[i], g.rowk[c], a0);
-        a1 = fma(g.colk[i1], g.rowk[c1], a1);
-        a2 = fma(g.colk[i2], g.rowk[c2], a2);
-        a3 = fma(g.colk[i3], g.rowk[c3], a3);
-        *q0 = a0;
-        if (b1) *q1 = a1;
-        if (b2) *q2 = a2;
-        if (b3) *q3 = a3;
-        i = i3;
-        c = c3;
+        int ii[GJ_ILP], cc[GJ_ILP];
+        ii[0] = i;
+        cc[0] = c;
+#pragma unroll
+        for (int u = 1; u < GJ_ILP; ++u) {
+          ii[u] = ii[u - 1];
+          cc[u] = cc[u - 1];
+          adv(ii[u], cc[u]);
+        }
+        double *q[GJ_ILP];
+        double a[GJ_ILP];
+#pragma unroll
+        for (int u = 0; u < GJ_ILP; ++u) {
+          const bool ok = ii[u] < N;
+          q[u] = A + (size_t)(ok ? ii[u] : i) * lda + (ok ? cc[u] : c);
+          a[u] = *q[u];
+        }
+#pragma unroll
+        for (int u = 0; u < GJ_ILP; ++u) {
+          const int iu = ii[u] < N ? ii[u] : i, cu = ii[u] < N ? cc[u] : c;
+          a[u] = fma(g.colk[iu], g.rowk[cu], a[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < GJ_ILP; ++u)
+          if (u == 0 || ii[u] < N) *q[u] = a[u];
+        i = ii[GJ_ILP - 1];
+        c = cc[GJ_ILP - 1];
         adv(i, c);
       }
     }

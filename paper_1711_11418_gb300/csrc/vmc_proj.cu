@@ -108,6 +108,93 @@ __device__ __forceinline__ double block_sum_d(double v, double *red, int &buf) {
 }
 
 // ---------------------------------------------------------------------------
+// Streaming one M_g^-1 (N x N row-major in HBM, N <= 128) by one warp: lanes
+// over the columns k = lane + 32 j (j < 4), PR rows loaded before they are
+// used, so PR x 4 loads per lane are in flight.
+// ---------------------------------------------------------------------------
+constexpr int PR = 8;
+
+template <typename T>
+__device__ __forceinline__ void rows_load(const T *M, int N, int l0, T (&v)[PR][4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < PR; ++r)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + r, k = lane + 32 * j;
+      v[r][j] = (l < N && k < N) ? M[(size_t)l * N + k] : (T)0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void rows_store(T *M, int N, int l0, const T (&v)[PR][4]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < PR; ++r)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + r, k = lane + 32 * j;
+      if (l < N && k < N) M[(size_t)l * N + k] = v[r][j];
+    }
+}
+
+// w_k = sum_l x_l M[l][k] (l ascending, one accumulator per k)
+template <typename T>
+__device__ void warp_colsum(const T *M, int N, const T *x, T *w) {
+  const int lane = threadIdx.x & 31;
+  T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+  for (int l0 = 0; l0 < N; l0 += PR) {
+    T v[PR][4];
+    rows_load(M, N, l0, v);
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+      const T xl = (l0 + r < N) ? x[l0 + r] : (T)0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[j] += xl * v[r][j];
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (lane + 32 * j < N) w[lane + 32 * j] = acc[j];
+}
+
+// y_l = sum_k M[l][k] x_k for every row l: per block of PR rows the lanes'
+// partial sums are reduced and scattered over the warp (lane groups by bits
+// 4..2 keep one row each), then summed over the remaining lane bits.
+template <typename T>
+__device__ void warp_rowdot(const T *M, int N, const T *x, T *y) {
+  const int lane = threadIdx.x & 31;
+  T xk[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) xk[j] = (lane + 32 * j < N) ? x[lane + 32 * j] : (T)0;
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  const int row = (b4 ? 4 : 0) + (b3 ? 2 : 0) + (b2 ? 1 : 0);
+  for (int l0 = 0; l0 < N; l0 += PR) {
+    T v[PR][4];
+    rows_load(M, N, l0, v);
+    T s[PR];
+#pragma unroll
+    for (int r = 0; r < PR; ++r) s[r] = v[r][0] * xk[0] + v[r][1] * xk[1] + v[r][2] * xk[2] + v[r][3] * xk[3];
+    T a[4], c[2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const T send = b4 ? s[u] : s[u + 4];
+      a[u] = (b4 ? s[u + 4] : s[u]) + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const T send = b3 ? a[u] : a[u + 2];
+      c[u] = (b3 ? a[u + 2] : a[u]) + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    const T send = b2 ? c[0] : c[1];
+    T d = (b2 ? c[1] : c[0]) + __shfl_xor_sync(0xffffffffu, send, 4);
+    d += __shfl_xor_sync(0xffffffffu, d, 2);
+    d += __shfl_xor_sync(0xffffffffu, d, 1);
+    if ((lane & 3) == 0 && l0 + row < N) y[l0 + row] = d;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Ratios of one mapped move, by one warp (lanes over the electrons)
 // ---------------------------------------------------------------------------
 // Hop of electron e to site t, mapped by g: det M_g'/det M_g.  Up electron n:
@@ -145,11 +232,11 @@ __device__ T proj_exchange_ratio(const SysDev &S, const int *ele, const T *Mg, i
   for (int l = lane; l < N; l += 32)
     R[l] = (l == m) ? F[(size_t)jg * Ns + ig] : F[(size_t)jg * Ns + inv[ele[N + l]]];
   __syncwarp();
+  warp_colsum(Mg, N, R, w);
+  __syncwarp();
   T a12 = (T)0, a22 = (T)0;
   for (int k = lane; k < N; k += 32) {
-    T wk = (T)0;
-    for (int l = 0; l < N; ++l) wk += R[l] * Mg[(size_t)l * N + k];
-    w[k] = wk;
+    const T wk = w[k];
     const int site = (k == n) ? j : ele[k];
     const T c = FT[(size_t)ig * Ns + inv[site]];
     const T mkm = FT[(size_t)jg * Ns + inv[ele[k]]];
@@ -181,18 +268,23 @@ __device__ T proj_exchange_ratio(const SysDev &S, const int *ele, const T *Mg, i
 template <typename T>
 __device__ void proj_row_update(T *Mg, int N, int n, const T *R, T *w, T *p) {
   const int lane = threadIdx.x & 31;
-  for (int k = lane; k < N; k += 32) {
-    T s = (T)0;
-    for (int l = 0; l < N; ++l) s += R[l] * Mg[(size_t)l * N + k];
-    w[k] = s;
-  }
+  warp_colsum(Mg, N, R, w);
   for (int l = lane; l < N; l += 32) p[l] = Mg[(size_t)l * N + n];
   __syncwarp();
   const T inv = (T)1 / w[n];
-  for (int l = 0; l < N; ++l) {
-    const T c = p[l] * inv;
-    for (int k = lane; k < N; k += 32)
-      Mg[(size_t)l * N + k] = (k == n) ? c : Mg[(size_t)l * N + k] - c * w[k];
+  T wk[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) wk[j] = (lane + 32 * j < N) ? w[lane + 32 * j] : (T)0;
+  for (int l0 = 0; l0 < N; l0 += PR) {
+    T v[PR][4];
+    rows_load(Mg, N, l0, v);
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+      const T c = (l0 + r < N) ? p[l0 + r] * inv : (T)0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[r][j] = (lane + 32 * j == n) ? c : v[r][j] - c * wk[j];
+    }
+    rows_store(Mg, N, l0, v);
   }
   __syncwarp();
 }
@@ -202,18 +294,24 @@ __device__ void proj_row_update(T *Mg, int N, int n, const T *R, T *w, T *p) {
 template <typename T>
 __device__ void proj_col_update(T *Mg, int N, int m, const T *C, T *v, T *z) {
   const int lane = threadIdx.x & 31;
-  for (int l = lane; l < N; l += 32) {
-    T s = (T)0;
-    for (int k = 0; k < N; ++k) s += Mg[(size_t)l * N + k] * C[k];
-    v[l] = s;
-  }
+  warp_rowdot(Mg, N, C, v);
   for (int k = lane; k < N; k += 32) z[k] = Mg[(size_t)m * N + k];
   __syncwarp();
   const T inv = (T)1 / v[m];
-  for (int l = 0; l < N; ++l) {
-    const T c = v[l] * inv;
-    for (int k = lane; k < N; k += 32)
-      Mg[(size_t)l * N + k] = (l == m) ? z[k] * inv : Mg[(size_t)l * N + k] - c * z[k];
+  T zk[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) zk[j] = (lane + 32 * j < N) ? z[lane + 32 * j] : (T)0;
+  for (int l0 = 0; l0 < N; l0 += PR) {
+    T a[PR][4];
+    rows_load(Mg, N, l0, a);
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+      const int l = l0 + r;
+      const T c = (l < N) ? v[l] * inv : (T)0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[r][j] = (l == m) ? zk[j] * inv : a[r][j] - c * zk[j];
+    }
+    rows_store(Mg, N, l0, a);
   }
   __syncwarp();
 }
@@ -225,23 +323,35 @@ template <typename T>
 __device__ void proj_exchange_update(T *Mg, int N, int n, int m, const T *w, const T *b,
                                      const T *K, T det, T *p, T *q, T *z) {
   const int lane = threadIdx.x & 31;
-  for (int l = lane; l < N; l += 32) {
-    T s = (T)0;
-    for (int k = 0; k < N; ++k) s += Mg[(size_t)l * N + k] * b[k];
-    q[l] = s;
-    p[l] = Mg[(size_t)l * N + n];
-  }
+  warp_rowdot(Mg, N, b, q);
+  for (int l = lane; l < N; l += 32) p[l] = Mg[(size_t)l * N + n];
   for (int k = lane; k < N; k += 32) z[k] = Mg[(size_t)m * N + k];
   __syncwarp();
   const T inv = (T)1 / det;
-  for (int l = 0; l < N; ++l) {
-    const T c1 = (p[l] * K[3] - q[l] * K[2]) * inv;
-    const T c2 = (q[l] * K[0] - p[l] * K[1]) * inv;
-    for (int k = lane; k < N; k += 32) {
-      T v = Mg[(size_t)l * N + k] - (c1 * w[k] + c2 * z[k]);
-      if (k == n) v += c1;
-      Mg[(size_t)l * N + k] = v;
+  T wk[4], zk[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int k = lane + 32 * j;
+    wk[j] = (k < N) ? w[k] : (T)0;
+    zk[j] = (k < N) ? z[k] : (T)0;
+  }
+  for (int l0 = 0; l0 < N; l0 += PR) {
+    T a[PR][4];
+    rows_load(Mg, N, l0, a);
+#pragma unroll
+    for (int r = 0; r < PR; ++r) {
+      const int l = l0 + r;
+      const T pl = (l < N) ? p[l] : (T)0, ql = (l < N) ? q[l] : (T)0;
+      const T c1 = (pl * K[3] - ql * K[2]) * inv;
+      const T c2 = (ql * K[0] - pl * K[1]) * inv;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        T x = a[r][j] - (c1 * wk[j] + c2 * zk[j]);
+        if (lane + 32 * j == n) x += c1;
+        a[r][j] = x;
+      }
     }
+    rows_store(Mg, N, l0, a);
   }
   __syncwarp();
 }
