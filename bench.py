@@ -319,6 +319,45 @@ def projected_sampling(vmc, torch, stream, inputs, W=304, calls=2):
                          "peak_source": src}}
 
 
+def lanczos_moments_timing(vmc, torch, stream, inputs, W=1024, calls=3):
+    """First-step power-Lanczos moments (Sec. 3.4) on the 16x16 workload,
+    mixed form: vmc_lanczos_moments on the walkers' current configurations,
+    CUDA events on the stream around each call.  Roofline of its table
+    products (Gu, Gd: Ns N^2 FMA each; T: Ns^2 N FMA, per walker) against the
+    FP32 peak; the two-move ratios (first term x second term, O(1) each from
+    the tables) come on top."""
+    prob = inputs.square16_hubbard()
+    ctx = vmc.Context(prob, W, seed=17, precision=vmc.MIXED, max_samples=1,
+                      stream=stream.cuda_stream)
+    ctx.sample(4, 0, 0)
+    ctx.lanczos_moments()                  # device scratch
+    ms = []
+    for _ in range(calls):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, h = ctx.lanczos_moments()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    ctx.close()
+    t = statistics.median(ms)
+    N, Ns = prob.N, prob.Ns
+    fl = 2.0 * (2 * Ns * N * N + Ns * Ns * N) * W
+    ach = fl / (t * 1e-3) / 1e12
+    try:
+        a, e1 = vmc.lanczos_alpha(h)
+        e1 /= Ns
+    except vmc.VmcError:                   # no real stationary point of E_1(alpha)
+        a = e1 = None
+    return {"walkers": W, "ms_per_call": t, "configurations_per_s": W / (t * 1e-3),
+            "alpha_1": a, "E1_per_site": e1, "h1_per_site": h["h1"] / Ns,
+            "roofline_tables": {"bound": "alu", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                                "kernel": "k_lanczos<float> (whole call)",
+                                "flops_rule": "2 (2 Ns N^2 + Ns^2 N) per walker",
+                                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}}
+
+
 def other_workloads(vmc, torch, stream, steps=5):
     """The other configured workloads, each timed on the device (CUDA events
     on the stream) after the headline bench:
@@ -330,7 +369,9 @@ def other_workloads(vmc, torch, stream, steps=5):
               one SR step of every system (vmc_sr_step_all, mixed solve);
       j1j2    C4: 16x16 J1-J2, full f (N_p = 65,536), 8192 samples: one dense
               S build by the split-BF16 tensor-core kernel;
-      projection_16x16: sampling with all 256 translations (projected_sampling)."""
+      projection_16x16: sampling with all 256 translations (projected_sampling);
+      kondo_L8: the L = 8 Kondo chain, sampling and an SR step (mixed form);
+      lanczos_16x16: power-Lanczos moments (lanczos_moments_timing)."""
     from paper_1711_11418_gb300 import inputs
     res = {}
 
@@ -375,6 +416,22 @@ def other_workloads(vmc, torch, stream, steps=5):
         "sizes_L": sorted({int(round(p.Ns ** 0.5)) for p in probs}), "dtype": "f32+f64"}
     ctx.close()
     res["projection_16x16"] = projected_sampling(vmc, torch, stream, inputs)
+    # Kondo lattice, Table Kondo's L = 8 chain (16 sites, 8 of them local
+    # spins): sampling and one SR step per step, mixed form
+    prob = inputs.kondo_chain(8)
+    ctx = vmc.Context(prob, 1024, seed=13, precision=vmc.MIXED, max_samples=8,
+                      stream=stream.cuda_stream)
+    ctx.sample(20, 0, 0)
+
+    def step_k():
+        ctx.sample(0, 8, 2)
+        ctx.sr_step(0.05, 1e-3, 1e-4, solver=vmc.CHOLESKY)
+    step_k()
+    res["kondo_L8"] = timed(ctx, step_k, steps) | {
+        "walkers": 1024, "samples_per_walker": 8, "sweeps_between": 2, "dtype": "f32+f64",
+        "energy_per_cell": ctx.measure()["energy"] / 8}
+    ctx.close()
+    res["lanczos_16x16"] = lanczos_moments_timing(vmc, torch, stream, inputs)
     prob = inputs.j1j2_heisenberg()
     ctx = vmc.Context(prob, 1024, seed=3, precision=vmc.MIXED, max_samples=8,
                       stream=stream.cuda_stream)
@@ -690,6 +747,7 @@ def run_ours(args):
                 "init_ms_per_step": r["kt"]["init"][0] / args.steps,
                 "sr_ms_per_step": r["kt"]["sr"][0] / args.steps,
                 "acceptance": d["n_accepted"] / max(d["n_proposals"], 1),
+                "accepted_per_s": r["props_all"] / secs * d["n_accepted"] / max(d["n_proposals"], 1),
                 "energy_per_site": r["energy"] / prob.Ns, "recomputes": d["n_recomputes"],
                 "sr_solve": r["solve"], "delay_tuner": r["delay"], "sweep_launch": r["launch"]}
 

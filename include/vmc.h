@@ -347,8 +347,10 @@ int vmc_set_projection(vmc_ctx *ctx, int32_t n_ops, const int32_t *perm, const i
  * Averaging the moments of calls between vmc_sample calls gives the Monte
  * Carlo estimates of Sec. 3.4; vmc_lanczos_alpha then gives alpha_1.
  * F1, F2: NULL or host [n_walkers]; moments: host [4].  The Pfaffian ratios
- * come from Green-function tables of each configuration (FP64, or FP32 from
- * the FP32 words of the mixed form's inverse); sums in FP64.  Device scratch
+ * come from Green-function tables of each configuration: FP64, or in the
+ * mixed form FP32 tables from the hi words of its inverse and FP32 ratio and
+ * correlation-factor arithmetic per term; the sums over first terms and over
+ * walkers in FP64.  Device scratch
  * (about 8 (2 Ns N + Ns^2) bytes per resident CTA) is kept by the context.
  * Errors: VMC_EINVAL (bad system, NULL moments, a context with the MLP
  * factor, Heisenberg J terms, or a projection: not provided), VMC_ENOMEM,

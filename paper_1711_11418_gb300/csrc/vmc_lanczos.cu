@@ -46,12 +46,15 @@ __device__ __forceinline__ const T *minv_of(const SysDev &S, int w) {
 
 // log P(y')/P(y) of a hop of a spin-s electron from site r to site t on a
 // configuration y given by its occupations (occ, with the hop's own electron
-// at r) and Jastrow field jf (Sec. 3.2.3).
-__device__ __forceinline__ double corr_log(const SysDev &S, const int *occ, const double *jf,
-                                           int s, int r, int t) {
+// at r) and Jastrow field jf (Sec. 3.2.3), in the ratios' type (FP64, or FP32
+// in the mixed form: GB300's FP64 pipe is 1/64 of the FP32 rate).
+template <typename T>
+__device__ __forceinline__ T corr_log(const SysDev &S, const int *occ, const T *jf, int s, int r,
+                                      int t) {
   const int Ns = S.Ns, o = (1 - s) * Ns;
-  double d = jf[t] - jf[r] - S.vmat[(size_t)r * Ns + t];
-  d += (occ[o + t] >= 0 ? S.gsite[t] : 0.0) - (occ[o + r] >= 0 ? S.gsite[r] : 0.0);
+  const T *g = gtab<T>(S);
+  T d = jf[t] - jf[r] - vtab<T>(S)[(size_t)r * Ns + t];
+  d += (occ[o + t] >= 0 ? g[t] : (T)0) - (occ[o + r] >= 0 ? g[r] : (T)0);
   return d;
 }
 
@@ -83,10 +86,12 @@ __global__ void __launch_bounds__(NT) k_lanczos(const SysDev *systems, int sys, 
   __shared__ double red[2 * 16];
   load_sys(&S, systems + sys);
   const int N = S.N, Ns = S.Ns, Ne = S.Ne, tid = threadIdx.x;
-  double *jf = (double *)smem_raw;             // Ns
-  int *occ = (int *)(jf + Ns);                 // 2 Ns
+  T *jf = (T *)smem_raw;                       // Ns (space for Ns doubles)
+  int *occ = (int *)((double *)smem_raw + Ns); // 2 Ns
   const int warp = tid >> 5, lane = tid & 31;
-  const double *F = S.f64;
+  const T *F = ftab<T>(S);
+  const T *V = vtab<T>(S);
+  const T *G = gtab<T>(S);
   T *Gu = slots + (size_t)blockIdx.x * lz_slot_elems(Ns, N);
   T *Gd = Gu + (size_t)Ns * N;
   T *Tt = Gd + (size_t)Ns * N;
@@ -95,7 +100,7 @@ __global__ void __launch_bounds__(NT) k_lanczos(const SysDev *systems, int sys, 
     __syncthreads();
     for (int k = tid; k < Ne; k += NT) ele[k] = S.ele[(size_t)w * Ne + k];
     for (int k = tid; k < 2 * Ns; k += NT) occ[k] = S.occ[(size_t)w * 2 * Ns + k];
-    for (int k = tid; k < Ns; k += NT) jf[k] = (double)((const T *)S.jf)[(size_t)w * Ns + k];
+    for (int k = tid; k < Ns; k += NT) jf[k] = ((const T *)S.jf)[(size_t)w * Ns + k];
     __syncthreads();
     const T *B = minv_of<T>(S, w);
     const int ldm = S.ldm;
@@ -103,8 +108,8 @@ __global__ void __launch_bounds__(NT) k_lanczos(const SysDev *systems, int sys, 
       const int b = (int)(q / N), k = (int)(q % N);
       T gu = (T)0, gd = (T)0;
       for (int l = 0; l < N; ++l) {
-        gu += (T)F[(size_t)b * Ns + ele[N + l]] * B[(size_t)l * ldm + k];
-        gd += (T)F[(size_t)ele[l] * Ns + b] * B[(size_t)k * ldm + l];
+        gu += F[(size_t)b * Ns + ele[N + l]] * B[(size_t)l * ldm + k];
+        gd += F[(size_t)ele[l] * Ns + b] * B[(size_t)k * ldm + l];
       }
       Gu[q] = gu;
       Gd[q] = gd;
@@ -113,27 +118,26 @@ __global__ void __launch_bounds__(NT) k_lanczos(const SysDev *systems, int sys, 
     for (size_t q = tid; q < (size_t)Ns * Ns; q += NT) {
       const int b = (int)(q / Ns), a = (int)(q % Ns);
       T s = (T)0;
-      for (int k = 0; k < N; ++k) s += Gu[(size_t)b * N + k] * (T)F[(size_t)ele[k] * Ns + a];
+      for (int k = 0; k < N; ++k) s += Gu[(size_t)b * N + k] * F[(size_t)ele[k] * Ns + a];
       Tt[q] = s;
     }
     __syncthreads();
     // one-hop Pfaffian ratio from x: electron e (spin by label) to site t
-    auto r1 = [&](int e, int t) -> double {
-      return e < N ? (double)Gu[(size_t)t * N + e] : (double)Gd[(size_t)t * N + (e - N)];
+    auto r1 = [&](int e, int t) -> T {
+      return e < N ? Gu[(size_t)t * N + e] : Gd[(size_t)t * N + (e - N)];
     };
     // two-hop Pfaffian ratio from x: electrons e1 -> t1 and e2 -> t2 (e1 != e2)
-    auto r2 = [&](int e1, int t1, int e2, int t2) -> double {
+    auto r2 = [&](int e1, int t1, int e2, int t2) -> T {
       if (e1 < N && e2 < N)
-        return (double)Gu[(size_t)t1 * N + e1] * (double)Gu[(size_t)t2 * N + e2] -
-               (double)Gu[(size_t)t1 * N + e2] * (double)Gu[(size_t)t2 * N + e1];
+        return Gu[(size_t)t1 * N + e1] * Gu[(size_t)t2 * N + e2] -
+               Gu[(size_t)t1 * N + e2] * Gu[(size_t)t2 * N + e1];
       if (e1 >= N && e2 >= N)
-        return (double)Gd[(size_t)t1 * N + (e1 - N)] * (double)Gd[(size_t)t2 * N + (e2 - N)] -
-               (double)Gd[(size_t)t1 * N + (e2 - N)] * (double)Gd[(size_t)t2 * N + (e1 - N)];
+        return Gd[(size_t)t1 * N + (e1 - N)] * Gd[(size_t)t2 * N + (e2 - N)] -
+               Gd[(size_t)t1 * N + (e2 - N)] * Gd[(size_t)t2 * N + (e1 - N)];
       const int ku = e1 < N ? e1 : e2, bu = e1 < N ? t1 : t2;
       const int md = (e1 < N ? e2 : e1) - N, ad = e1 < N ? t2 : t1;
-      return (double)Gu[(size_t)bu * N + ku] * (double)Gd[(size_t)ad * N + md] -
-             (double)B[(size_t)md * ldm + ku] *
-                 ((double)Tt[(size_t)bu * Ns + ad] - F[(size_t)bu * Ns + ad]);
+      return Gu[(size_t)bu * N + ku] * Gd[(size_t)ad * N + md] -
+             B[(size_t)md * ldm + ku] * (Tt[(size_t)bu * Ns + ad] - F[(size_t)bu * Ns + ad]);
     };
     // a hop term q = 2k + s: the spin-s electron on j = hop_j[k] to i = hop_i[k]
     auto valid_on = [&](const int *oc, int s, int i, int j) -> bool {
@@ -149,12 +153,12 @@ __global__ void __launch_bounds__(NT) k_lanczos(const SysDev *systems, int sys, 
       const int i1 = S.hop_i[k1], j1 = S.hop_j[k1];
       if (!valid_on(occ, s1, i1, j1)) continue;
       const int e1 = occ[s1 * Ns + j1];
-      const double c1 = corr_log(S, occ, jf, s1, j1, i1);
-      const double R1 = r1(e1, i1) * exp(c1);
+      const T c1 = corr_log<T>(S, occ, jf, s1, j1, i1);
+      const double R1 = (double)(r1(e1, i1) * corr_factor<T>(c1));
       const double h1 = -S.hop_t[k1];
       const double dx = diag_energy(S, occ, s1, j1, i1);
       // second terms on x' = (e1: j1 -> i1) x
-      double acc = 0.0;
+      T acc = (T)0;
       for (int q2 = lane; q2 < nterm; q2 += 32) {
         const int k2 = q2 >> 1, s2 = q2 & 1;
         const int i2 = S.hop_i[k2], j2 = S.hop_j[k2];
@@ -170,26 +174,24 @@ __global__ void __launch_bounds__(NT) k_lanczos(const SysDev *systems, int sys, 
         if (S.local_spin && occp(1 - s2, i2) >= 0) continue;
         if (S.lsite && (S.lsite[i2] | S.lsite[j2])) continue;
         const int e2 = occp(s2, j2);
-        double R;
+        T R;
         if (e2 == e1) {
           // e1 moves again: x'' is x with e1 on i2 (x itself if i2 = j1)
-          R = (i2 == j1) ? 1.0 : r1(e1, i2) * exp(corr_log(S, occ, jf, s1, j1, i2));
+          R = (i2 == j1) ? (T)1 : r1(e1, i2) * corr_factor<T>(corr_log<T>(S, occ, jf, s1, j1, i2));
         } else {
           // second hop on x': Jastrow field and occupations of x'
-          const int Nss = Ns;
-          const double jfi = jf[i2] + S.vmat[(size_t)i2 * Nss + i1] - S.vmat[(size_t)i2 * Nss + j1];
-          const double jfj = jf[j2] + S.vmat[(size_t)j2 * Nss + i1] - S.vmat[(size_t)j2 * Nss + j1];
-          double c2 = jfi - jfj - S.vmat[(size_t)j2 * Nss + i2];
-          c2 += (occp(1 - s2, i2) >= 0 ? S.gsite[i2] : 0.0) -
-                (occp(1 - s2, j2) >= 0 ? S.gsite[j2] : 0.0);
-          R = r2(e1, i1, e2, i2) * exp(c1 + c2);
+          const T jfi = jf[i2] + V[(size_t)i2 * Ns + i1] - V[(size_t)i2 * Ns + j1];
+          const T jfj = jf[j2] + V[(size_t)j2 * Ns + i1] - V[(size_t)j2 * Ns + j1];
+          T c2 = jfi - jfj - V[(size_t)j2 * Ns + i2];
+          c2 += (occp(1 - s2, i2) >= 0 ? G[i2] : (T)0) - (occp(1 - s2, j2) >= 0 ? G[j2] : (T)0);
+          R = r2(e1, i1, e2, i2) * corr_factor<T>(c1 + c2);
         }
-        acc += -S.hop_t[k2] * R;
+        acc += (T)(-S.hop_t[k2]) * R;
       }
-      acc = warp_sum(acc);
+      const double accd = warp_sum((double)acc);
       if (lane == 0) {
         f1 += h1 * R1;
-        f2 += h1 * (dx * R1 + acc);
+        f2 += h1 * (dx * R1 + accd);
       }
     }
     // block sums (lane 0 of each warp holds its part)
