@@ -51,6 +51,7 @@ struct vmc_ctx {
   double *d_scalar = nullptr;
   int recompute_every = 0;
   int delay_k = 0;            // as set by the caller (0/1 = immediate)
+  bool rebuild_pending = false;  // the last sweep launch's periodic rebuild is still to run
   unsigned char *pin = nullptr;   // pinned staging for vmc_sr_step_all's results (per system)
   // vmc_sr_step_all: systems run on a small pool of streams forked from st
   static constexpr int NPOOL = 8;
@@ -341,10 +342,37 @@ int set_delay_impl(vmc_ctx *c, int k) {
 
 // Rebuild the walkers' inverses from scratch (FP64) where needed; returns
 // VMC_ESINGULAR if any walker's M is singular.
+bool projected(const vmc_ctx *c);
+
+// Periodic FP64 from-scratch inverses (fast updates accumulate rounding):
+// every walker with at least recompute_every accepted moves since its last
+// inverse is rebuilt.
+int periodic_rebuild(vmc_ctx *c) {
+  TimedRegion tr(c, 1);
+  if (projected(c))
+    CKC(vmc_launch_proj_build(c->d_sys, c->d_work, c->n_work, c->sys[0].dev.n_ops, c->precision,
+                              1, c->recompute_every, c->smem_init, c->st, &c->n_launch));
+  else
+    CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->d_work_ctr + 1, c->precision, 1,
+                        c->recompute_every, c->smem_init, c->st, &c->n_launch));
+  c->rebuild_pending = false;
+  return VMC_OK;
+}
+
+// Every inverse current before it is read: the full rebuild after a parameter
+// or configuration change, else the periodic rebuild the last vmc_sample left
+// pending (a full rebuild makes that one moot).
 int ensure_init(vmc_ctx *c, bool redraw_illcond = false) {
   bool any = false;
   for (auto &s : c->sys) any |= s.dirty;
-  if (!any) return VMC_OK;
+  if (!any) {
+    if (c->rebuild_pending) {
+      CK(upload_sysdesc(c));
+      CK(periodic_rebuild(c));
+    }
+    return VMC_OK;
+  }
+  c->rebuild_pending = false;
   CK(upload_sysdesc(c));
   {
     TimedRegion tr(c, 1);
@@ -829,29 +857,21 @@ int vmc_sample(vmc_ctx *c, int32_t n_warmup, int32_t n_samples, int32_t sweeps_b
   if (c->recompute_every <= 0) {
     CK(sweep(n_warmup, n_samples, sweeps_between, 0));
   } else {
-    // Periodic FP64 from-scratch inverses (fast updates accumulate rounding):
-    // after every sweep launch, walkers with at least recompute_every
-    // accepted moves since their last inverse are rebuilt.
-    auto recompute = [&]() -> int {
-      TimedRegion tr(c, 1);
-      if (proj)
-        CKC(vmc_launch_proj_build(c->d_sys, c->d_work, c->n_work, c->sys[0].dev.n_ops,
-                                  c->precision, 1, c->recompute_every, c->smem_init, c->st,
-                                  &c->n_launch));
-      else
-        CKC(vmc_launch_init(c->d_sys, c->d_work, c->n_work, c->d_work_ctr + 1, c->precision, 1,
-                            c->recompute_every,
-                            c->smem_init, c->st, &c->n_launch));
-      return VMC_OK;
-    };
+    // The periodic rebuild follows every sweep launch but the call's last:
+    // that one is left pending and runs when an inverse is next needed (the
+    // next call's sweeps, or a check hook), unless a parameter change first
+    // makes every inverse a full rebuild, as an SR step does.
+    const int launches = n_warmup + n_samples;
+    int done = 0;
     for (int k = 0; k < n_warmup; ++k) {
       CK(sweep(1, 0, 0, 0));
-      CK(recompute());
+      if (++done < launches) CK(periodic_rebuild(c));
     }
     for (int k = 0; k < n_samples; ++k) {
       CK(sweep(0, 1, sweeps_between, k));
-      CK(recompute());
+      if (++done < launches) CK(periodic_rebuild(c));
     }
+    if (launches > 0) c->rebuild_pending = true;
   }
   int bad = 0;
   for (auto &s : c->sys) {
