@@ -110,10 +110,13 @@ typedef struct {
   int32_t delay_k;               /* delayed-update depth k of the sweep (0 or 1 =
                                     immediate updates, 2..VMC_DELAY_MAX); see
                                     vmc_set_delay */
-  int32_t recompute_every;       /* FP64 from-scratch inverse inside the sweep once a
-                                    walker has this many accepted moves since the
-                                    last one; 0 = default (mixed: 64, FP64: never),
-                                    -1 = never */
+  int32_t recompute_every;       /* FP64 from-scratch inverse between sweep launches
+                                    once a walker has this many accepted moves since
+                                    the last one (the one after a vmc_sample call's
+                                    last launch runs when an inverse is next read,
+                                    and is dropped when a parameter change rebuilds
+                                    every walker first); 0 = default (mixed: 64,
+                                    FP64: never), -1 = never */
   int32_t max_samples;           /* sample rows kept per walker (>= 1) */
   void *stream;                  /* cudaStream_t; NULL = default stream */
   int32_t rebuild;               /* from-scratch inverses of the mixed form:
