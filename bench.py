@@ -271,10 +271,11 @@ def cpu_baseline_configs(pool, cores, seconds=4.0):
     return out
 
 
-def projected_sampling(vmc, torch, stream, inputs, W=304, calls=2):
+def projected_sampling(vmc, torch, stream, inputs, W=608, calls=2):
     """Momentum projection at N_g = Ns on the 16x16 workload (mixed form):
     all 256 translations at K = 0 (Sec. 3.2.2, Eq. momP; App. A signs), one
-    M_g^-1 per translation per walker in HBM (12.8 MB per walker).  Timed:
+    M_g^-1 per translation per walker in HBM (12.8 MB per walker; 608
+    walkers fill the kernel's four CTAs per SM).  Timed:
     vmc_sample(0, 1, 1) calls (one sweep and one measurement per walker, with
     the periodic rebuilds of every M_g^-1), CUDA events on the stream.
     Roofline of the projected sweep kernel on its algorithmic bytes: every

@@ -1421,8 +1421,8 @@ int vmc_lanczos_moments(vmc_ctx *c, int32_t system, double *F1, double *F2, doub
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(s.W, 4 * nsm);
   const int prec = c->precision == VMC_FP64 ? 0 : 1;
+  const int grid = std::min(s.W, std::max(1, vmc_lanczos_occupancy(prec, s.Ns)) * nsm);
   const size_t slot = (vmc_lanczos_slot_bytes(prec, s.Ns, s.N) + 255) / 256 * 256;
   const size_t need = slot * grid + sizeof(double) * (2 * (size_t)s.W + 8);
   if (c->lz_bytes < need) {

@@ -164,6 +164,7 @@ cudaError_t vmc_launch_proj_eval(const SysDev *d_sys, int sys, int walker, int p
 // First-step power-Lanczos local values and moments (vmc_lanczos.cu): table
 // slot bytes per CTA, and the launch (k_lanczos over the walkers, then the
 // four walker means into moments[4]).
+int vmc_lanczos_occupancy(int precision, int Ns);
 size_t vmc_lanczos_slot_bytes(int precision, int Ns, int N);
 cudaError_t vmc_launch_lanczos(const SysDev *d_sys, int sys, int precision, int Ns, int grid,
                                void *slots, double *F1, double *F2, int W, double *moments,

@@ -245,6 +245,21 @@ size_t vmc_lanczos_slot_bytes(int precision, int Ns, int N) {
 
 size_t vmc_lanczos_smem(int Ns) { return (size_t)Ns * (sizeof(double) + 2 * sizeof(int)); }
 
+// CTAs of k_lanczos per SM (registers and shared memory): the kernel waits on
+// L2 reads of its tables, so the grid fills every slot.
+int vmc_lanczos_occupancy(int precision, int Ns) {
+  int nb = 0;
+  const size_t smem = vmc_lanczos_smem(Ns);
+  if (precision == 0) {
+    cudaFuncSetAttribute(k_lanczos<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lanczos<double>, NT, smem);
+  } else {
+    cudaFuncSetAttribute(k_lanczos<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lanczos<float>, NT, smem);
+  }
+  return nb;
+}
+
 cudaError_t vmc_launch_lanczos(const SysDev *d_sys, int sys, int precision, int Ns, int grid,
                                void *slots, double *F1, double *F2, int W, double *moments,
                                cudaStream_t st, long long *nl) {
