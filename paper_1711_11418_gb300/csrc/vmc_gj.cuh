@@ -14,11 +14,11 @@ constexpr int NWARP = NT / 32;
 
 // In place on an N x N row-major matrix (row stride lda) in shared or global
 // memory.  Two barriers per elimination step:
-//   (P, B) one warp takes the pivot of column k from the per-warp candidates
-//       (largest |a|, ties: lowest row), forms 1/pivot, the multipliers
-//       m_i = a_ik / pivot (pivot row swapped in, m_k = 0, kept negated so
-//       the update is one FMA) and the raw pivot row, swaps rows k and p and
-//       scales row k, so the FP64 work outside the update is one warp's;
+//   (P, B) two warps take the pivot of column k from the per-warp
+//       candidates (largest |a|, ties: lowest row) and form 1/pivot; one
+//       forms the multipliers m_i = a_ik / pivot (pivot row swapped in,
+//       m_k = 0, kept negated so the update is one FMA), the other the raw
+//       pivot row, swapping rows k and p and scaling row k;
 //   (E) a_ic -= m_i r_c over all entries, spread flat over the threads in
 //       whole warps; before it, each thread forms the updated value of its
 //       row of column k+1 once more (one FMA, from a copy of the column taken
@@ -102,11 +102,12 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
   };
   for (int k = 0; k < N; ++k) {
     const int buf = k & 1;
-    // (P) + (B) by warp 0 while the others wait: the pivot from the per-warp
-    // candidates, 1/pivot, the negated multipliers (pivot row swapped in), the
-    // inverse's column k, the raw pivot row; rows k and p swapped and row k
-    // scaled.
-    if (tid < 32) {
+    // (P) + (B) by warps 0 and 1 while the others wait: both take the pivot
+    // from the per-warp candidates and form 1/pivot; warp 0 the negated
+    // multipliers (pivot row swapped in) and the inverse's column k, warp 1
+    // the raw pivot row, the swap of rows k and p with row k scaled, and the
+    // copy of column k+1 (the two touch disjoint columns).
+    if (tid < 64) {
       unsigned long long bk = g.ckey[buf][0];
       int p = g.cidx[buf][0];
       for (int q = 1; q < NWARP; ++q) {
@@ -117,11 +118,12 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
           p = iq;
         }
       }
+      const int lane = tid & 31;
       if (bk <= 1ull || p >= N) {   // zero (key 1) or no finite entry: singular
         if (tid == 0) g.bad = 1;
-      } else {
+      } else if (tid < 32) {
         const double piv = A[(size_t)p * lda + k];
-        const double ipiv = 1.0 / piv;
+        const double ipiv = __drcp_rn(piv);
         if (tid == 0) {
           perm[k] = p;
           g.ipiv = ipiv;
@@ -129,15 +131,17 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
           if ((piv < 0.0) != (p != k)) g.sign = -g.sign;
         }
         const double nipiv = -ipiv;   // negated multipliers: the update is one FMA
-        for (int i = tid; i < N; i += 32) {
+        for (int i = lane; i < N; i += 32) {
           const double a = (i == k) ? 0.0 : A[(size_t)(i == p ? k : i) * lda + k];
           g.colk[i] = a * nipiv;
         }
         __syncwarp();
-        // the inverse's column k: -m_i, and 1/pivot at row k (rowk_k = 0 below
+        // the inverse's column k: -m_i, and 1/pivot at row k (rowk_k = 0
         // leaves it through the update)
-        for (int i = tid; i < N; i += 32) A[(size_t)i * lda + k] = (i == k) ? ipiv : g.colk[i];
-        for (int c = tid; c < N; c += 32) {
+        for (int i = lane; i < N; i += 32) A[(size_t)i * lda + k] = (i == k) ? ipiv : g.colk[i];
+      } else {
+        const double ipiv = __drcp_rn(A[(size_t)p * lda + k]);
+        for (int c = lane; c < N; c += 32) {
           if (c == k) {
             g.rowk[c] = 0.0;
             continue;
@@ -150,7 +154,7 @@ __device__ __forceinline__ void gj_invert(double *A, int lda, int N, int *perm, 
         __syncwarp();
         // column k+1 as the update below finds it (rows swapped)
         if (k + 1 < N)
-          for (int i = tid; i < N; i += 32) g.coln[i] = A[(size_t)i * lda + k + 1];
+          for (int i = lane; i < N; i += 32) g.coln[i] = A[(size_t)i * lda + k + 1];
       }
     }
     __syncthreads();
