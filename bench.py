@@ -368,8 +368,10 @@ def other_workloads(vmc, torch, stream, steps=5):
       batch64 C3: 64 independent Hubbard systems (L = 4..16) x 64 walkers, mixed
               form, FP64 recompute every 64 accepted moves, 4 samples, and
               one SR step of every system (vmc_sr_step_all, mixed solve);
-      j1j2    C4: 16x16 J1-J2, full f (N_p = 65,536), 8192 samples: one dense
-              S build by the split-BF16 tensor-core kernel;
+      j1j2    C4: 16x16 J1-J2, full f (N_p = 65,536): 1024 walkers x 8
+              samples (mixed form, proposal batch depth from the tuner), then
+              one dense S build of the 8192 samples by the split-BF16
+              tensor-core kernel;
       projection_16x16: sampling with all 256 translations (projected_sampling);
       kondo_L8: the L = 8 Kondo chain, sampling and an SR step (mixed form);
       lanczos_16x16: power-Lanczos moments (lanczos_moments_timing)."""
@@ -436,7 +438,21 @@ def other_workloads(vmc, torch, stream, steps=5):
     prob = inputs.j1j2_heisenberg()
     ctx = vmc.Context(prob, 1024, seed=3, precision=vmc.MIXED, max_samples=8,
                       stream=stream.cuda_stream)
-    ctx.sample(2, 8, 1)
+    ctx.sample(2, 0, 0)
+    # sampling: every proposal an exchange (an O(N^2) ratio), the batch depth
+    # picked by the tuner; one sampling call of 8 samples timed on the stream
+    b_chosen, b_ms = ctx.tune_proposal_batch(sweeps=2, candidates=(1, 2, 4, 8))
+    s0 = ctx.measure()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.sample(0, 8, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    props = ctx.measure()["n_proposals"] - s0["n_proposals"]
+    sampling = {"walkers": 1024, "samples_per_walker": 8, "sweeps_between": 1,
+                "dtype": "f32+f64", "ms": ms_s, "proposals_per_s": props / (ms_s * 1e-3),
+                "proposal_batch": b_chosen, "ms_per_sweep_by_batch": b_ms}
     ctx.enable_timing(True)
     ctx.kernel_times()
     rep = ctx.sr_step(0.05, 1e-4, 0.0, solver=vmc.CG_DENSE, cg_eps=1e-3, cg_kmax=1)
@@ -454,7 +470,8 @@ def other_workloads(vmc, torch, stream, steps=5):
                    "frac_three_products": 3 * fl / (ms * 1e-3) / 1e12 / pk,
                    "peak_tflops": pk, "peak_source": "measured bf16 burst" if peaks else "fallback",
                    "flops_rule": "method: N_MC N_p^2 (the symmetric product once); three "
-                                 "products: split-BF16 hi.hi + hi.lo + lo.hi"}
+                                 "products: split-BF16 hi.hi + hi.lo + lo.hi",
+                   "sampling": sampling}
     ctx.close()
     return res
 
@@ -597,6 +614,9 @@ def run_arm(vmc, prob, args, precision, stream, torch, world, rebuild=0):
                       max_samples=S, recompute_every=args.recompute if precision == vmc.MIXED else -1,
                       stream=stream.cuda_stream, rebuild=rebuild)
     ctx.sample(args.equil, 0, 0)                        # equilibration (untimed)
+    # proposal batch depth picked by the library's tuner (sweeps only, untimed)
+    b_chosen, b_ms = ctx.tune_proposal_batch(sweeps=2, candidates=(1, 2, 4, 8))
+    pbatch = {"chosen": b_chosen, "ms_per_sweep": b_ms}
     # Immediate updates: they keep the mixed form's double-float inverse (the
     # delayed form keeps FP32 words only, so it is not used at the accuracy
     # this bench checks).
@@ -647,7 +667,7 @@ def run_arm(vmc, prob, args, precision, stream, torch, world, rebuild=0):
     grid, per_sm, smem = ctx.sweep_launch()
     return ctx, dict(ms=ms, stats=d, kt=kt, launches=launches, clocks=clk,
                      energy=statistics.fmean(energies), last=st1, solve=solve,
-                     props_all=props_all, sr=sr, delay=delay,
+                     props_all=props_all, sr=sr, delay=delay, pbatch=pbatch,
                      launch={"grid": grid, "ctas_per_sm": per_sm, "smem_bytes": smem})
 
 
@@ -750,7 +770,8 @@ def run_ours(args):
                 "acceptance": d["n_accepted"] / max(d["n_proposals"], 1),
                 "accepted_per_s": r["props_all"] / secs * d["n_accepted"] / max(d["n_proposals"], 1),
                 "energy_per_site": r["energy"] / prob.Ns, "recomputes": d["n_recomputes"],
-                "sr_solve": r["solve"], "delay_tuner": r["delay"], "sweep_launch": r["launch"]}
+                "sr_solve": r["solve"], "delay_tuner": r["delay"], "proposal_batch_tuner": r["pbatch"],
+                "sweep_launch": r["launch"]}
 
     peaks = measured_alu_peaks(torch)
     sm = summarize(mixed)

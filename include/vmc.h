@@ -439,6 +439,33 @@ int32_t vmc_get_delay(vmc_ctx *ctx);
 int vmc_tune_delay(vmc_ctx *ctx, int32_t sweeps, const int32_t *cand, int32_t n_cand,
                    int32_t *chosen, double *ms);
 
+/* Proposals formed together by the sweep (no counterpart in the paper; a
+ * schedule of Sec. 3.1.2's proposals, not a change of the method).  With
+ * depth b >= 2 each walker takes the next b proposals of its stream, checks
+ * them and forms their ratios at once against the current configuration and
+ * inverse (the exchanges' rows R^T M^-1 in one pass over M^-1), then takes
+ * the Metropolis decisions in the stream's order; the batch ends at the
+ * first accepted proposal, whose move is made, and the proposals after it
+ * are formed again against the updated state.  The chain (configurations,
+ * counters, samples) is the one b = 1 gives, up to the ratios' summation
+ * order.  Applies while the MLP factor and delayed updates are off (the
+ * sweep makes proposals one at a time otherwise).  Default 1.  What pays
+ * depends on the workload: where most proposals are tested exchanges (spin
+ * models) the shared pass over M^-1 wins; where the FP64 pipe or the
+ * inverse updates bound the sweep, the proposals formed past an accepted one
+ * are wasted work -- hence the tuner below. 
+ * vmc_set_proposal_batch returns VMC_EINVAL for b outside [1, VMC_SPEC_MAX].
+ * vmc_tune_proposal_batch times vmc_sample(ctx, sweeps, 0, 0) (sweeps only)
+ * for each candidate depth (NULL: 1, 2, 4, 8) with CUDA events on the
+ * context's stream, keeps the fastest in *chosen and, optionally, the
+ * milliseconds per sweep of each candidate in ms; periodic recomputes are
+ * held off while timing, as in vmc_tune_delay. */
+#define VMC_SPEC_MAX 8
+int vmc_set_proposal_batch(vmc_ctx *ctx, int32_t b);
+int32_t vmc_get_proposal_batch(vmc_ctx *ctx);
+int vmc_tune_proposal_batch(vmc_ctx *ctx, int32_t sweeps, const int32_t *cand,
+                            int32_t n_cand, int32_t *chosen, double *ms);
+
 /* Allocation-free SR means and force.  No counterpart in the paper: it is an
  * access path for callers that cannot let this library allocate device memory
  * (for example because another allocator already owns the GPU's memory, or

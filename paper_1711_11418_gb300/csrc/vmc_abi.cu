@@ -51,6 +51,7 @@ struct vmc_ctx {
   double *d_scalar = nullptr;
   int recompute_every = 0;
   int delay_k = 0;            // as set by the caller (0/1 = immediate)
+  int spec_b = 1;             // proposals formed together by the sweep
   bool rebuild_pending = false;  // the last sweep launch's periodic rebuild is still to run
   unsigned char *pin = nullptr;   // pinned staging for vmc_sr_step_all's results (per system)
   // vmc_sr_step_all: systems run on a small pool of streams forked from st
@@ -579,6 +580,7 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     d.n_J = m.n_J;
     d.local_spin = m.local_spin ? 1 : 0;
     d.stall_walker = -1;
+    d.spec_b = 1;
     d.lsite = nullptr;
     if (m.local_site) {
       s.lsite.assign((const signed char *)m.local_site, (const signed char *)m.local_site + m.Ns);
@@ -1591,6 +1593,67 @@ int vmc_tune_delay(vmc_ctx *c, int32_t sweeps, const int32_t *cand, int32_t n_ca
   }
   *chosen = best;
   return set_delay_impl(c, best);
+}
+
+int vmc_set_proposal_batch(vmc_ctx *c, int32_t b) {
+  if (!c || b < 1 || b > VMC_SPEC_MAX) return VMC_EINVAL;
+  for (auto &s : c->sys) s.dev.spec_b = b;
+  c->spec_b = b;
+  return VMC_OK;
+}
+
+int32_t vmc_get_proposal_batch(vmc_ctx *c) { return c ? c->spec_b : -1; }
+
+int vmc_tune_proposal_batch(vmc_ctx *c, int32_t sweeps, const int32_t *cand, int32_t n_cand,
+                            int32_t *chosen, double *ms) {
+  static const int32_t def[] = {1, 2, 4, 8};
+  if (!c || sweeps < 1 || (cand && n_cand < 1) || !chosen) return VMC_EINVAL;
+  if (!cand) {
+    cand = def;
+    n_cand = 4;
+  }
+  for (int q = 0; q < n_cand; ++q)
+    if (cand[q] < 1 || cand[q] > VMC_SPEC_MAX) return VMC_EINVAL;
+  CK(ensure_init(c));
+  const int prev = c->spec_b;
+  // as in vmc_tune_delay: no periodic rebuilds while timing
+  const int rec = c->recompute_every;
+  c->recompute_every = 0;
+  cudaEvent_t e0, e1;
+  CKC(cudaEventCreate(&e0));
+  CKC(cudaEventCreate(&e1));
+  int best = -1;
+  double best_ms = 0.0;
+  int rc = VMC_OK;
+  for (int q = 0; q < n_cand && rc == VMC_OK; ++q) {
+    if (ms) ms[q] = -1.0;
+    vmc_set_proposal_batch(c, cand[q]);
+    cudaEventRecord(e0, c->st);
+    rc = vmc_sample(c, sweeps, 0, 0);
+    cudaEventRecord(e1, c->st);
+    if (rc != VMC_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      rc = VMC_ECUDA;
+      break;
+    }
+    float t = 0.f;
+    cudaEventElapsedTime(&t, e0, e1);
+    const double per = (double)t / sweeps;
+    if (ms) ms[q] = per;
+    if (best < 0 || per < best_ms) {
+      best = cand[q];
+      best_ms = per;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->recompute_every = rec;
+  if (rc != VMC_OK || best < 0) {
+    vmc_set_proposal_batch(c, prev);
+    return rc != VMC_OK ? rc : VMC_EINVAL;
+  }
+  *chosen = best;
+  return vmc_set_proposal_batch(c, best);
 }
 
 int vmc_enable_timing(vmc_ctx *c, int32_t on) {

@@ -74,6 +74,7 @@ struct SysDev {
   int recompute_every;         // accepted moves between FP64 from-scratch inverses (0 = never)
   int delay_k;                 // pending delayed updates before a flush (<= 1: immediate)
   int stall_walker;            // test hook: this walker's copy is not issued (-1: none)
+  int spec_b;                  // proposals formed together by the sweep (<= 1: one at a time)
   // quantum-number projection (Sec. 3.2.2): n_ops operations g (0 = none)
   int n_ops;
   const int *pinv;             // [n_ops*Ns] g^-1(site)

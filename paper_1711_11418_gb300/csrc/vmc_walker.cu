@@ -135,7 +135,11 @@ __host__ __device__ size_t walker_layout(int N, int Ns, int acc_len, int H, int 
   const size_t o_minv = take(minv_bytes(N, ldm, sizeof(T)));
   const size_t o_vec = take(sizeof(T) * 8 * VMC_MAX_N);
   const size_t dly = (kd > 1) ? sizeof(T) * 2 * (size_t)kd * N : 0;
-  const size_t o_acc = take(sizeof(T) * (size_t)acc_len > dly ? sizeof(T) * (size_t)acc_len : dly);
+  // the O-row accumulator; also the delayed pairs, or a proposal batch's
+  // per-warp partial sums (NWARP x 32 values), none of which live together
+  size_t acc_b = sizeof(T) * (size_t)acc_len > dly ? sizeof(T) * (size_t)acc_len : dly;
+  if (acc_b < sizeof(T) * NWARP * 32) acc_b = sizeof(T) * NWARP * 32;
+  const size_t o_acc = take(acc_b);
   const size_t o_red = take(sizeof(T) * 32);
   const size_t o_bc = take(sizeof(T) * 2);
   const size_t o_jf = take(sizeof(T) * Ns);
@@ -1216,6 +1220,341 @@ __device__ void propose(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t
   acc_since = (fabs((double)rpf) < SMALL_RATIO) ? RECOMPUTE_NOW : acc_since + 1;
 }
 
+// ---------------------------------------------------------------------------
+// Proposals formed in batches (Sec. 3.1.2 proposals, one Markov chain)
+// ---------------------------------------------------------------------------
+// The next B proposals of the walker's stream are checked and their ratios
+// formed together, against the current configuration and inverse; the
+// Metropolis decisions are then taken in the stream's order, and the batch
+// ends at the first accepted proposal, whose move is made as propose() makes
+// it.  The proposals after it are formed again, against the updated state, by
+// the next batch.  The chain is therefore the one propose() gives proposal by
+// proposal (only the ratios' summation order differs); what changes is the
+// cost: the exchanges of a batch share one pass over M^-1, the batch's table
+// gathers are in flight together, and a batch has two block barriers where a
+// proposal had two or three.  Used when the MLP factor and delayed updates
+// are off.
+constexpr int SPEC_MAX = 8;
+
+// Per-warp partial sums of a batch: NWARP x 32 values (inside the O-row
+// accumulator area, which only the measurement uses).
+template <typename T>
+__host__ __device__ constexpr size_t spec_scratch_bytes() {
+  return sizeof(T) * NWARP * 32;
+}
+
+// One step of a transposed butterfly over 2H values per lane: lanes with bit
+// H set keep the upper half, the others the lower half, and each adds its
+// partner's copy of the half it keeps.
+template <int H, typename T>
+__device__ __forceinline__ void tb_step(T *p, int lane) {
+  const bool up = lane & H;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const T send = up ? p[k] : p[k + H];
+    const T keep = up ? p[k + H] : p[k];
+    p[k] = keep + __shfl_xor_sync(0xffffffffu, send, H);
+  }
+}
+
+// Warp sums of 32 per-lane values (31 shuffles): lane l returns the total of
+// value l.
+template <typename T>
+__device__ __forceinline__ T reduce32_transposed(T *p, int lane) {
+  tb_step<16>(p, lane);
+  tb_step<8>(p, lane);
+  tb_step<4>(p, lane);
+  tb_step<2>(p, lane);
+  tb_step<1>(p, lane);
+  return p[0];
+}
+
+// w_q = sum_l R_q[l] M[l][col] for the Q rows R_q in vector slots 0..Q-1:
+// one pass over the column, two accumulators per row.
+template <int Q, typename T>
+__device__ __forceinline__ void spec_gemv(const T *M, int ldm, int col, const T *vec, int N,
+                                          T *w) {
+  T a[Q], b[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    a[q] = (T)0;
+    b[q] = (T)0;
+  }
+  int l = 0;
+  for (; l + 4 <= N; l += 4) {
+    const T m0 = M[l * ldm + col], m1 = M[(l + 1) * ldm + col];
+    const T m2 = M[(l + 2) * ldm + col], m3 = M[(l + 3) * ldm + col];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      T x0, x1, x2, x3;
+      ld4(vec + q * VMC_MAX_N + l, x0, x1, x2, x3);
+      a[q] += x0 * m0;
+      b[q] += x1 * m1;
+      a[q] += x2 * m2;
+      b[q] += x3 * m3;
+    }
+  }
+  for (; l < N; ++l) {
+    const T m0 = M[l * ldm + col];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) a[q] += vec[q * VMC_MAX_N + l] * m0;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) w[q] = a[q] + b[q];
+}
+
+template <typename T>
+__device__ __forceinline__ void spec_gemv_n(int Q, const T *M, int ldm, int col, const T *vec,
+                                            int N, T *w) {
+  switch (Q) {
+    case 1: spec_gemv<1>(M, ldm, col, vec, N, w); break;
+    case 2: spec_gemv<2>(M, ldm, col, vec, N, w); break;
+    case 3: spec_gemv<3>(M, ldm, col, vec, N, w); break;
+    case 4: spec_gemv<4>(M, ldm, col, vec, N, w); break;
+    case 5: spec_gemv<5>(M, ldm, col, vec, N, w); break;
+    case 6: spec_gemv<6>(M, ldm, col, vec, N, w); break;
+    case 7: spec_gemv<7>(M, ldm, col, vec, N, w); break;
+    default: spec_gemv<8>(M, ldm, col, vec, N, w); break;
+  }
+}
+
+// a[q] for a thread-varying q < SPEC_MAX without local-memory indexing
+template <typename T>
+__device__ __forceinline__ T sel_spec(const T *a, int q) {
+  T r = a[0];
+#pragma unroll
+  for (int k = 1; k < SPEC_MAX; ++k) r = (q == k) ? a[k] : r;
+  return r;
+}
+
+// One batch of at most bmax proposals; returns how many it consumed.  Every
+// thread runs it; decisions are uniform across the block.  Each warp decodes
+// and checks the batch's proposals itself (lane b takes proposal b), so the
+// descriptors travel by shuffles; the per-thread products go through one
+// transposed reduction per warp and one barrier.
+template <typename T>
+__device__ int propose_batch(const SysDev &S, const WSmem<T> &sm, uint2 key, uint32_t walker,
+                             unsigned long long &ctr, int &rpos, MoveCounts &mc, int &acc_since,
+                             int &buf, int bmax) {
+  const int N = S.N, Ns = S.Ns, Ne = S.Ne, ldm = S.ldm, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  const unsigned full = 0xffffffffu;
+  const T *F = ftab<T>(S);
+  const T *FT = fTtab<T>(S);
+  int B = S.spec_b < SPEC_MAX ? S.spec_b : SPEC_MAX;
+  if (B > bmax) B = bmax;
+  if (rpos + B > RB) {
+    // draws ctr .. ctr + RB - 1 (the stream is indexed by the counter, so a
+    // refill at any position gives the draws proposal by proposal would use)
+    if (tid < RB) {
+      const unsigned long long c = ctr + tid;
+      sm.rnd[tid] = vmc_philox(make_uint4((uint32_t)c, (uint32_t)(c >> 32), walker,
+                                          (uint32_t)S.sys_index), key);
+    }
+    __syncthreads();
+    rpos = 0;
+  }
+  // --- decode and check (lane b: proposal b), as propose() does
+  int kind = 0, x0 = 0, x1 = 0, x2 = 0, x3 = 0;   // 1 up hop, 2 down hop, 3 exchange
+  T u = (T)1, cf = (T)0;
+  if (lane < B) {
+    const uint4 r = sm.rnd[rpos + lane];
+    u = (T)(r.w >> 8) * (T)(1.0 / 16777216.0);
+    if ((unsigned long long)r.x < S.pex) {
+      const int n = vmc_mulhi(r.y, N), m = vmc_mulhi(r.z, N);
+      const int i = sm.ele[n], j = sm.ele[N + m];
+      if (!(i == j || sm.occ[Ns + i] >= 0 || sm.occ[j] >= 0)) {
+        kind = 3;
+        x0 = n;
+        x1 = m;
+        x2 = i;
+        x3 = j;
+      }
+    } else {
+      const int e = vmc_mulhi(r.y, Ne), t = vmc_mulhi(r.z, Ns);
+      const int s = (e >= N) ? 1 : 0;
+      bool ok = sm.occ[s * Ns + t] < 0;
+      if (ok && S.local_spin && sm.occ[(1 - s) * Ns + t] >= 0) ok = false;
+      const int rs = sm.ele[e];
+      if (ok && S.lsite && (S.lsite[t] | S.lsite[rs])) ok = false;
+      if (ok) {
+        kind = 1 + s;
+        x0 = s ? e - N : e;
+        x1 = t;
+        x2 = rs;
+        cf = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, gtab<T>(S), Ns, s, rs, t,
+                                       vtab<T>(S)[(size_t)rs * Ns + t]));
+      }
+    }
+  }
+  const unsigned exm = __ballot_sync(full, kind == 3);
+  const unsigned hpm = __ballot_sync(full, kind == 1 || kind == 2);
+  const int nex = __popc(exm);
+  // --- per-thread products: hop ratios' terms; the exchanges' new rows R_q
+  // (vector slot q, in the order of the batch) and their row-m and b terms
+  // values: [b] hop term or K22 term, [8 + b] K12 term, [16 + b] K11 (w_n)
+  T val[32], bk[SPEC_MAX];
+  // per slot: exchange row slot q, or -1; and whether this thread is its row n
+  int xq[SPEC_MAX];
+  unsigned isn = 0;
+  const int tr = (tid < N) ? tid : 0;
+  const int eup = sm.ele[tr], edn = sm.ele[N + tr];
+  // All table gathers of the batch are issued before any is used (branch-free
+  // address selection; a slot that fails the checks reads entry 0), so the
+  // batch pays one L2 round trip, not one per proposal.
+  T g1[SPEC_MAX], g2[SPEC_MAX], g3[SPEC_MAX], s1[SPEC_MAX];
+  int kd[SPEC_MAX], z0[SPEC_MAX];
+#pragma unroll
+  for (int b = 0; b < SPEC_MAX; ++b) {
+    const int bb = b < B ? b : 0;
+    const int k = __shfl_sync(full, kind, bb);
+    const int y0 = __shfl_sync(full, x0, bb), y1 = __shfl_sync(full, x1, bb);
+    const int y2 = __shfl_sync(full, x2, bb), y3 = __shfl_sync(full, x3, bb);
+    kd[b] = (b < B) ? k : 0;
+    z0[b] = y0;
+    // up hop (e = y0 to t = y1): f(t, r_tid,dn) and (M^-1)_{tid e}
+    // down hop (m = y0 to t = y1): f(r_tid,up, t) and (M^-1)_{m tid}
+    // exchange (n = y0 at i = y2, m = y1 at j = y3): R_tid, C_tid, f(r_tid,up, j), (M^-1)_{m tid}
+    const T *t1 = (k == 2) ? FT : F;
+    const size_t r1 = (k == 3) ? (size_t)y3 : (size_t)y1;
+    const int c1 = (k == 2) ? eup : (k == 3 && tid == y1) ? y2 : edn;
+    const int site = (tid == y0) ? y3 : eup;
+    const bool ex = (k == 3);
+    const int mi = (k == 1) ? tr * ldm + y0 : y1 * ldm + tr;
+    g1[b] = t1[(k != 0) ? r1 * Ns + c1 : 0];
+    g2[b] = FT[ex ? (size_t)y2 * Ns + site : 0];
+    g3[b] = FT[ex ? (size_t)y3 * Ns + eup : 0];
+    s1[b] = sm.minv[(k == 2) ? y0 * ldm + tr : ((k != 0) ? mi : 0)];
+  }
+#pragma unroll
+  for (int b = 0; b < 32; ++b) val[b] = (T)0;
+#pragma unroll
+  for (int b = 0; b < SPEC_MAX; ++b) {
+    bk[b] = (T)0;
+    xq[b] = -1;
+    const int k = kd[b];
+    if (k == 3) xq[b] = __popc(exm & ((1u << b) - 1));
+    if (tid < N) {
+      if (k == 1 || k == 2) {
+        val[b] = g1[b] * s1[b];
+      } else if (k == 3) {
+        if (tid == z0[b]) isn |= 1u << b;
+        sm.vec[xq[b] * VMC_MAX_N + tid] = g1[b];
+        val[b] = (tid == z0[b]) ? s1[b] * g3[b] : s1[b] * g2[b];
+        bk[b] = (tid == z0[b]) ? (T)0 : g2[b] - g3[b];
+      }
+    }
+  }
+  __syncthreads();
+  // --- one pass over M^-1 for all exchanges: w_q = R_q^T M^-1 (column tid)
+  T wq[SPEC_MAX];
+#pragma unroll
+  for (int q = 0; q < SPEC_MAX; ++q) wq[q] = (T)0;
+  if (nex > 0 && tid < N) spec_gemv_n(nex, sm.minv, ldm, tid, sm.vec, N, wq);
+#pragma unroll
+  for (int b = 0; b < SPEC_MAX; ++b) {
+    if (xq[b] >= 0) {
+      const T w = sel_spec(wq, xq[b]);
+      val[SPEC_MAX + b] = w * bk[b];
+      val[2 * SPEC_MAX + b] = ((isn >> b) & 1u) ? w : (T)0;
+    }
+  }
+  const T tot = reduce32_transposed(val, lane);
+  T *part = sm.acc;
+  if (lane < 3 * SPEC_MAX) part[warp * 32 + lane] = tot;
+  __syncthreads();
+  // --- decisions in the stream's order (every warp takes the same ones)
+  bool acc = false;
+  T rpf = (T)0;
+  if (lane < B && kind != 0) {
+    T s0 = part[lane], s1 = part[SPEC_MAX + lane], s2 = part[2 * SPEC_MAX + lane];
+#pragma unroll
+    for (int k = 1; k < NWARP; ++k) {
+      s0 += part[k * 32 + lane];
+      s1 += part[k * 32 + SPEC_MAX + lane];
+      s2 += part[k * 32 + 2 * SPEC_MAX + lane];
+    }
+    T ratio;
+    if (kind == 3) {
+      // det [[K11, K12], [K21, K22]] with K21 = (M^-1)_{mn}
+      rpf = s2 * s0 - s1 * sm.minv[x1 * ldm + x0];
+      ratio = rpf;
+    } else {
+      rpf = s0;
+      ratio = rpf * cf;
+    }
+    acc = u < ratio * ratio;
+  }
+  const unsigned am = __ballot_sync(full, acc);
+  const int ka = am ? __ffs(am) - 1 : -1;
+  const int used = (ka >= 0) ? ka + 1 : B;
+  const unsigned usedm = (used >= 32) ? full : ((1u << used) - 1u);
+  mc.hop_t += __popc(hpm & usedm);
+  mc.ex_t += __popc(exm & usedm);
+  ctr += (unsigned long long)used;
+  rpos += used;
+  if (ka < 0) return used;
+  // --- the accepted proposal ka: its move, as propose() makes it
+  const int k = __shfl_sync(full, kind, ka);
+  const int y0 = __shfl_sync(full, x0, ka), y1 = __shfl_sync(full, x1, ka);
+  const int y2 = __shfl_sync(full, x2, ka), y3 = __shfl_sync(full, x3, ka);
+  const T rk = __shfl_sync(full, rpf, ka);
+  if (k == 3) {
+    const int n = y0, m = y1, i = y2, j = y3;
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (sm.mlo) {
+        exchange_update_df(S, sm, n, m, i, j, buf);
+        done = true;
+      }
+    }
+    if (!done) {
+      // the rank-2 update wants w = R^T M^-1, C and K as exchange_pf_ratio leaves them
+      T K[4], mlp;
+      const T r2 = exchange_pf_ratio(S, sm, n, m, i, j, buf, K, mlp, 0);
+      exchange_update(S, sm, n, m, j, K, r2);
+    }
+    if (tid == 0) {
+      sm.ele[n] = j;
+      sm.ele[N + m] = i;
+      sm.occ[i] = -1;
+      sm.occ[j] = n;
+      sm.occ[Ns + j] = -1;
+      sm.occ[Ns + i] = N + m;
+    }
+    __syncthreads();
+    mc.ex_a++;
+  } else {
+    const int s = k - 1, e = s ? y0 + N : y0, t = y1, rs = y2;
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+      if (sm.mlo) {
+        if (s == 0) row_update_df(S, sm, e, t);
+        else col_update_df(S, sm, e - N, t);
+        done = true;
+      }
+    }
+    if (!done) {
+      if (tid < N) sm.vec[tid] = s ? FT[(size_t)t * Ns + eup] : F[(size_t)t * Ns + edn];
+      __syncthreads();
+      if (s == 0) row_update(S, sm, e);
+      else col_update(S, sm, e - N);
+    }
+    // Jastrow field: h_x += v_{x t} - v_{x r}.
+    for (int x = tid; x < Ns; x += NT)
+      sm.jf[x] += vtab<T>(S)[(size_t)t * Ns + x] - vtab<T>(S)[(size_t)rs * Ns + x];
+    if (tid == 0) {
+      sm.ele[e] = t;
+      sm.occ[s * Ns + rs] = -1;
+      sm.occ[s * Ns + t] = e;
+    }
+    __syncthreads();
+    mc.hop_a++;
+  }
+  acc_since = (fabs((double)rk) < SMALL_RATIO) ? RECOMPUTE_NOW : acc_since + 1;
+  return used;
+}
+
 // Sum of eight per-lane values over the warp by a transposed butterfly
 // (nine shuffles instead of eight separate reductions): on return lane l
 // holds the total of value k = 4 bit4(l) + 2 bit3(l) + bit2(l).
@@ -1553,7 +1892,7 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
 // Kernels
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2 *work, int n_work,
+__global__ void __launch_bounds__(NT, 2) k_sample(const SysDev *systems, const int2 *work, int n_work,
                                                int *work_ctr, uint2 key, int n_first, int n_samples,
                                                int sweeps_between, int sample_base) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -1619,12 +1958,28 @@ __global__ void __launch_bounds__(NT) k_sample(const SysDev *systems, const int2
     __syncthreads();
     int np = 0;   // pending delayed updates
     const long long props_first = (long long)n_first * Ne;
-    for (long long p = 0; p < props_first; ++p)
-      propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf, np);
+    // proposals in batches where the MLP factor and delayed updates are off
+    const bool batched = S.spec_b > 1 && S.n_hidden == 0 && S.delay_k <= 1;
+    for (long long p = 0; p < props_first;) {
+      if (batched) {
+        p += propose_batch(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf,
+                           (int)(props_first - p < SPEC_MAX ? props_first - p : SPEC_MAX));
+      } else {
+        propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf, np);
+        ++p;
+      }
+    }
     for (int s = 0; s < n_samples; ++s) {
       const long long props = (long long)sweeps_between * Ne;
-      for (long long p = 0; p < props; ++p)
-        propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf, np);
+      for (long long p = 0; p < props;) {
+        if (batched) {
+          p += propose_batch(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf,
+                             (int)(props - p < SPEC_MAX ? props - p : SPEC_MAX));
+        } else {
+          propose(S, sm, key, key_w, ctr, rpos, mc, acc_since, buf, np);
+          ++p;
+        }
+      }
       __syncthreads();
       delayed_flush(S, sm, np);
       measure(S, sm, w, sample_base + s, buf, mc);

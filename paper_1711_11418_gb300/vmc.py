@@ -84,7 +84,8 @@ EXPORTS = ["vmc_create", "vmc_create_batch", "vmc_destroy", "vmc_strerror", "vmc
            "vmc_enable_timing", "vmc_kernel_times", "vmc_sr_force_static", "vmc_set_delay",
            "vmc_get_delay", "vmc_tune_delay", "vmc_sr_step_all", "vmc_measure_corr",
            "vmc_test_stall", "vmc_set_projection", "vmc_lanczos_moments", "vmc_lanczos_alpha",
-           "vmc_sweep_launch"]
+           "vmc_sweep_launch", "vmc_set_proposal_batch", "vmc_get_proposal_batch",
+           "vmc_tune_proposal_batch"]
 STALL_NONE, STALL_SAMPLE, STALL_S_BUILD = 0, 1, 2
 
 
@@ -129,6 +130,9 @@ def load(path: str = LIB_PATH):
     L.vmc_set_delay.argtypes = [P, C.c_int32]
     L.vmc_get_delay.argtypes = [P]
     L.vmc_tune_delay.argtypes = [P, C.c_int32, _I32P, C.c_int32, _I32P, _F64P]
+    L.vmc_set_proposal_batch.argtypes = [P, C.c_int32]
+    L.vmc_get_proposal_batch.argtypes = [P]
+    L.vmc_tune_proposal_batch.argtypes = [P, C.c_int32, _I32P, C.c_int32, _I32P, _F64P]
     L.vmc_test_stall.argtypes = [P, C.c_int32, C.c_int32, C.c_int32]
     L.vmc_set_projection.argtypes = [P, C.c_int32, _I32P, _I8P, _F64P]
     L.vmc_lanczos_moments.argtypes = [P, C.c_int32, _F64P, _F64P, _F64P]
@@ -398,6 +402,25 @@ class Context:
         _check(self._L.vmc_tune_delay(self._h, int(sweeps), _p(cand, _I32P), cand.size,
                                       _p(chosen, _I32P), _p(ms, _F64P)), "vmc_tune_delay")
         return int(chosen[0]), {int(k): (float(t) if t >= 0 else None) for k, t in zip(cand, ms)}
+
+    # -- proposals formed together by the sweep
+    def set_proposal_batch(self, b):
+        _check(self._L.vmc_set_proposal_batch(self._h, int(b)), "vmc_set_proposal_batch")
+
+    def get_proposal_batch(self):
+        return int(self._L.vmc_get_proposal_batch(self._h))
+
+    def tune_proposal_batch(self, sweeps=2, candidates=None):
+        """Time vmc_sample(sweeps, 0, 0) (sweeps only) per candidate batch
+        depth, keep the fastest.  Returns (chosen, {b: ms per sweep})."""
+        cand = np.ascontiguousarray(candidates if candidates is not None else (1, 2, 4, 8),
+                                    np.int32)
+        ms = np.zeros(cand.size)
+        chosen = np.zeros(1, np.int32)
+        _check(self._L.vmc_tune_proposal_batch(self._h, int(sweeps), _p(cand, _I32P), cand.size,
+                                               _p(chosen, _I32P), _p(ms, _F64P)),
+               "vmc_tune_proposal_batch")
+        return int(chosen[0]), {int(k): float(t) for k, t in zip(cand, ms)}
 
     def enable_timing(self, on=True):
         _check(self._L.vmc_enable_timing(self._h, 1 if on else 0), "vmc_enable_timing")
