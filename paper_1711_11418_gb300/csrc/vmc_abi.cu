@@ -635,6 +635,24 @@ int create_impl(vmc_ctx **out, int n_sys, const vmc_model *models, const int32_t
     if ((rc = dupload(c, (int **)&d.J_i, m.J_i, m.n_J))) return fail(rc);
     if ((rc = dupload(c, (int **)&d.J_j, m.J_j, m.n_J))) return fail(rc);
     if ((rc = dupload(c, (double **)&d.J_val, m.J_val, m.n_J))) return fail(rc);
+    {
+      // the exchange terms by site (each term under both of its sites), for
+      // the measurement's grouping by the site that receives the up electron
+      std::vector<int> jp(Ns + 1, 0);
+      std::vector<int2> ja(m.n_J ? 2 * (size_t)m.n_J : 1);
+      for (int k = 0; k < m.n_J; ++k) {
+        jp[m.J_i[k] + 1]++;
+        jp[m.J_j[k] + 1]++;
+      }
+      for (size_t i = 0; i < Ns; ++i) jp[i + 1] += jp[i];
+      std::vector<int> cur(jp.begin(), jp.end() - 1);
+      for (int k = 0; k < m.n_J; ++k) {
+        ja[cur[m.J_i[k]]++] = make_int2(k, m.J_j[k]);
+        ja[cur[m.J_j[k]]++] = make_int2(k, m.J_i[k]);
+      }
+      if ((rc = dupload(c, (int **)&d.jptr, jp.data(), Ns + 1))) return fail(rc);
+      if ((rc = dupload(c, (int2 **)&d.jadj, ja.data(), ja.size()))) return fail(rc);
+    }
     std::vector<int> gneg(Ns, -1), vneg;
     if ((rc = dupload(c, (int **)&d.g_idx, l.n_g ? l.g_idx : gneg.data(), Ns))) return fail(rc);
     if (!l.n_v) vneg.assign(n2, -1);

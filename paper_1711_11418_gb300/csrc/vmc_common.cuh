@@ -40,6 +40,8 @@ struct SysDev {
   const int *V_i, *V_j;
   const double *V_val;
   const int *J_i, *J_j;
+  const int *jptr;              // [Ns + 1] exchange terms by site (CSR)
+  const int2 *jadj;            // [2 n_J] {term, other site} of each site's terms
   const double *J_val;
   const int *g_idx, *v_idx, *f_idx;
   const signed char *f_sign;

@@ -1583,41 +1583,6 @@ __device__ __forceinline__ T reduce8_transposed(const T *p, int lane) {
 // ---------------------------------------------------------------------------
 // Measurement: E_loc (Eq. MC with A = H) and the O_k row (Sec. 3.3.1)
 // ---------------------------------------------------------------------------
-// Warp-level exchange ratio (same formula as exchange_pf_ratio) for the
-// Heisenberg S+S- terms of E_loc.  R, Wp: per-warp scratch vectors.
-template <typename T>
-__device__ T exchange_pf_ratio_warp(const SysDev &S, const WSmem<T> &sm, int n, int m, int i,
-                                    int j, T *R, T *Wp) {
-  const int N = S.N, Ns = S.Ns, ldm = S.ldm, lane = threadIdx.x & 31;
-  const T *F = ftab<T>(S);
-  const T *FT = fTtab<T>(S);
-  for (int l = lane; l < N; l += 32)
-    R[l] = (l == m) ? F[(size_t)j * Ns + i] : F[(size_t)j * Ns + sm.ele[N + l]];
-  __syncwarp();
-  T a22 = (T)0, a12 = (T)0;
-  for (int k = lane; k < N; k += 32) {
-    T w = (T)0;
-    for (int l = 0; l < N; ++l) w += R[l] * sm.minv[l * ldm + k];
-    Wp[k] = w;
-    const int site = (k == n) ? j : sm.ele[k];
-    const T c = FT[(size_t)i * Ns + site];
-    const T mkm = FT[(size_t)j * Ns + sm.ele[k]];
-    const T mrow = sm.minv[m * ldm + k];
-    if (k == n) {
-      a22 += mrow * mkm;
-    } else {
-      a22 += mrow * c;
-      a12 += w * (c - mkm);
-    }
-  }
-  a22 = warp_sum(a22);
-  a12 = warp_sum(a12);
-  __syncwarp();
-  const T r = Wp[n] * a22 - a12 * sm.minv[m * ldm + n];
-  __syncwarp();
-  return r;
-}
-
 template <typename T>
 __device__ __forceinline__ void acc_add(T *p, T v) { atomicAdd(p, v); }
 
@@ -1775,29 +1740,95 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
     tl = ntl;
     vl = nvl;
   }
-  // --- Heisenberg exchange: J/2 (S+_a S-_b + S-_a S+_b) = -J/2 x (labelled swap ratio)
+  // --- Heisenberg exchange: J/2 (S+_a S-_b + S-_a S+_b) = -J/2 x (labelled swap ratio).
+  // The terms are taken by the site b that receives the up electron (b holds
+  // exactly a down electron m, a exactly an up electron n).  The new row of
+  // every such term differs from f(b, r_dn) only in entry m, so
+  // w = R^T M^-1 = g_b + (f(b, a) - f(b, b)) M^-1[m,:] with g_b = f(b, r_dn)^T M^-1
+  // formed once per site by one warp (lanes over columns), and each term is
+  // the 2 x 2 determinant of exchange_pf_ratio in O(N).
   T *R = sm.vec + (2 * warp) * VMC_MAX_N;
-  T *Wp = sm.vec + (2 * warp + 1) * VMC_MAX_N;
   __syncthreads();   // vec area switches from proposal use to per-warp use
-  for (int k = warp; k < S.n_J; k += NWARP) {
-    int a = S.J_i[k], b = S.J_j[k];
-    int nu = sm.occ[a], md = sm.occ[Ns + b];
-    bool ok = nu >= 0 && md >= 0 && sm.occ[Ns + a] < 0 && sm.occ[b] < 0;
-    if (!ok) {
-      const int a2 = b, b2 = a;
-      nu = sm.occ[a2];
-      md = sm.occ[Ns + b2];
-      ok = nu >= 0 && md >= 0 && sm.occ[Ns + a2] < 0 && sm.occ[b2] < 0;
-      a = a2;
-      b = b2;
-    }
-    if (!ok || a == b) continue;
-    const T r = exchange_pf_ratio_warp(S, sm, nu, md - N, a, b, R, Wp);
-    const T lm =
-        S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, a + Ns, a, b, b + Ns, lane, 32)) : (T)0;
-    if (lane == 0) {
-      eo += (T)(-0.5 * S.J_val[k]) * r * (S.n_hidden ? exp_t<T>(lm) : (T)1);
-      mc.meas_ex++;
+  if (S.n_J > 0) {
+    const unsigned full = 0xffffffffu;
+    for (int b = warp; b < Ns; b += NWARP) {
+      const int md = sm.occ[Ns + b];
+      if (md < 0 || sm.occ[b] >= 0) continue;
+      const int q0 = S.jptr[b], q1 = S.jptr[b + 1];
+      bool any = false;
+      for (int q = q0 + lane; q < q1; q += 32) {
+        const int a = S.jadj[q].y;
+        any |= (sm.occ[a] >= 0 && sm.occ[Ns + a] < 0);
+      }
+      if (!__any_sync(full, any)) continue;
+      const int m = md - N;
+      for (int l = lane; l < N; l += 32) R[l] = F[(size_t)b * Ns + sm.ele[N + l]];
+      __syncwarp();
+      // lane holds columns k = lane + 32 u: g_b[k], (M^-1)_{mk}, r_k,up, f(r_k,up, b)
+      T g[4], mr[4], mk[4];
+      int ek[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = lane + 32 * u;
+        g[u] = (T)0;
+        mr[u] = (k < N) ? sm.minv[m * ldm + k] : (T)0;
+        ek[u] = (k < N) ? sm.ele[k] : 0;
+        mk[u] = (k < N) ? FT[(size_t)b * Ns + ek[u]] : (T)0;
+      }
+      int l = 0;
+      for (; l + 4 <= N; l += 4) {
+        T r0, r1, r2, r3;
+        ld4(R + l, r0, r1, r2, r3);
+        const T *m0 = sm.minv + l * ldm;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = lane + 32 * u;
+          if (k < N)
+            g[u] += r0 * m0[k] + r1 * m0[ldm + k] + r2 * m0[2 * ldm + k] + r3 * m0[3 * ldm + k];
+        }
+      }
+      for (; l < N; ++l) {
+        const T rl = R[l];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = lane + 32 * u;
+          if (k < N) g[u] += rl * sm.minv[l * ldm + k];
+        }
+      }
+      __syncwarp();   // R is written again for the warp's next site
+      const T fbb = F[(size_t)b * Ns + b];
+      for (int q = q0; q < q1; ++q) {
+        const int2 tq = S.jadj[q];
+        const int a = tq.y;
+        const int n = sm.occ[a];
+        if (n < 0 || sm.occ[Ns + a] >= 0) continue;
+        const T delta = F[(size_t)b * Ns + a] - fbb;
+        T a22 = (T)0, a12 = (T)0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = lane + 32 * u;
+          if (k < N) {
+            const T c = FT[(size_t)a * Ns + ((k == n) ? b : ek[u])];
+            if (k == n) {
+              a22 += mr[u] * mk[u];
+            } else {
+              a22 += mr[u] * c;
+              a12 += (g[u] + delta * mr[u]) * (c - mk[u]);
+            }
+          }
+        }
+        a22 = warp_sum(a22);
+        a12 = warp_sum(a12);
+        const T gn = __shfl_sync(full, sel4(g, n >> 5), n & 31);
+        const T A21 = sm.minv[m * ldm + n];
+        const T r = (gn + delta * A21) * a22 - a12 * A21;
+        const T lm =
+            S.n_hidden ? warp_sum(mlp_log_ratio_part(S, sm, a + Ns, a, b, b + Ns, lane, 32)) : (T)0;
+        if (lane == 0) {
+          eo += (T)(-0.5 * S.J_val[tq.x]) * r * (S.n_hidden ? exp_t<T>(lm) : (T)1);
+          mc.meas_ex++;
+        }
+      }
     }
   }
   const double etot = block_sum((double)ed + (double)eo, sm.dred, buf);
