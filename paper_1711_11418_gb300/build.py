@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvmc.so")
 SOURCES = ["vmc_walker.cu", "vmc_sr.cu", "vmc_tc.cu", "vmc_abi.cu", "vmc_noalloc.cu", "vmc_sr_mixed.cu",
-           "vmc_proj.cu", "vmc_lanczos.cu"]
+           "vmc_proj.cu", "vmc_lanczos.cu", "vmc_sweep3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -146,6 +146,13 @@ size_t vmc_walker_smem(int precision, int N, int Ns, int Np, int H, int kd, int 
                        int with_lo);
 size_t vmc_init_smem(int N, int Ns);
 int vmc_sample_occupancy(int precision, size_t smem);
+// the mixed form's 168-register sweep variant (vmc_sweep3.cu)
+int vmc_sample_occupancy_v3(size_t smem);
+cudaError_t vmc_sample_set_smem_v3(size_t s32);
+cudaError_t vmc_launch_sample_v3(const SysDev *d_sys, const int2 *d_work, int n_work,
+                                 int *d_work_ctr, uint2 key, int n_first, int n_samples,
+                                 int sweeps_between, int sample_base, int grid, size_t smem,
+                                 cudaStream_t st, long long *nl);
 cudaError_t vmc_walker_set_smem_limits(size_t smem_sample64, size_t smem_sample32,
                                        size_t smem_init);
 

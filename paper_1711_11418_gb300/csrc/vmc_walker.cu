@@ -1922,8 +1922,13 @@ __device__ void measure(const SysDev &S, const WSmem<T> &sm, int w, int row, int
 // ---------------------------------------------------------------------------
 // Kernels
 // ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NT, 2) k_sample(const SysDev *systems, const int2 *work, int n_work,
+// MINB: the CTAs per SM the register budget is sized for.  Walkers of large
+// systems fit two CTAs per SM in shared memory and get up to 255 registers
+// (MINB = 2); small systems fit three or more and get the 168-register budget
+// that keeps three resident (MINB = 3).  The host picks by shared-memory
+// occupancy (sample_variant3).
+template <typename T, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_sample(const SysDev *systems, const int2 *work, int n_work,
                                                int *work_ctr, uint2 key, int n_first, int n_samples,
                                                int sweeps_between, int sample_base) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -2051,6 +2056,7 @@ __global__ void __launch_bounds__(NT, 2) k_sample(const SysDev *systems, const i
   }
 }
 
+#ifndef VMC_SWEEP_V3_ONLY
 // Expand the parameter vector into dense tables (f, f^T in FP64 and FP32, v, g).
 __global__ void k_expand(SysDev S) {
   const int Ns = S.Ns;
@@ -2537,7 +2543,10 @@ __global__ void k_corr_reduce(const double *part, int n_part, const int *cnt, in
   }
 }
 
+#endif  // VMC_SWEEP_V3_ONLY
 }  // namespace
+
+#ifndef VMC_SWEEP_V3_ONLY
 
 // ---------------------------------------------------------------------------
 // Host-side launch wrappers
@@ -2555,20 +2564,31 @@ size_t vmc_init_smem(int N, int Ns) {
   return (size_t)N * ldm * sizeof(double) + sizeof(int) * (3 * N + 2 * Ns + 1) + 64;
 }
 
+// The mixed form's sweep variant for a shared-memory size: the 168-register
+// one (vmc_sweep3.cu) where it keeps three or more CTAs per SM resident,
+// else the other.
+static bool sample_variant3(size_t smem, int *nb3) {
+  const int nb = vmc_sample_occupancy_v3(smem);
+  if (nb3) *nb3 = nb;
+  return nb >= 3;
+}
+
 int vmc_sample_occupancy(int precision, size_t smem) {
   int nb = 0;
-  if (precision == 0)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<double>, NT, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<float>, NT, smem);
+  if (precision == 0) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<double, 3>, NT, smem);
+  } else if (!sample_variant3(smem, &nb)) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<float, 2>, NT, smem);
+  }
   return nb;
 }
 
 cudaError_t vmc_walker_set_smem_limits(size_t s64, size_t s32, size_t sinit) {
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(k_sample<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
+  if ((e = cudaFuncSetAttribute(k_sample<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
   if ((e = cudaFuncSetAttribute(k_eval_ratios<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
-  if ((e = cudaFuncSetAttribute(k_sample<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+  if ((e = cudaFuncSetAttribute(k_sample<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
+  if ((e = vmc_sample_set_smem_v3(s32))) return e;
   if ((e = cudaFuncSetAttribute(k_eval_ratios<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
   if ((e = cudaFuncSetAttribute(k_corr<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64))) return e;
   if ((e = cudaFuncSetAttribute(k_corr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32))) return e;
@@ -2628,11 +2648,14 @@ cudaError_t vmc_launch_sample(const SysDev *d_sys, const int2 *d_work, int n_wor
   if (grid > n_work) grid = n_work;
   if (grid < 1) return cudaSuccess;
   if (precision == 0)
-    k_sample<double><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
-                                             n_samples, sweeps_between, sample_base);
+    k_sample<double, 3><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
+                                                n_samples, sweeps_between, sample_base);
+  else if (sample_variant3(smem, nullptr))
+    return vmc_launch_sample_v3(d_sys, d_work, n_work, d_work_ctr, key, n_first, n_samples,
+                                sweeps_between, sample_base, grid, smem, st, nl);
   else
-    k_sample<float><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
-                                            n_samples, sweeps_between, sample_base);
+    k_sample<float, 2><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
+                                               n_samples, sweeps_between, sample_base);
   ++*nl;
   return cudaGetLastError();
 }
@@ -2691,3 +2714,27 @@ cudaError_t vmc_launch_corr_reduce(const double *part, int n_part, const int *cn
   ++*nl;
   return cudaGetLastError();
 }
+
+#else  // VMC_SWEEP_V3_ONLY: the mixed form's sweep kernel with the 168-register budget
+
+int vmc_sample_occupancy_v3(size_t smem) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sample<float, 3>, NT, smem);
+  return nb;
+}
+
+cudaError_t vmc_sample_set_smem_v3(size_t s32) {
+  return cudaFuncSetAttribute(k_sample<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)s32);
+}
+
+cudaError_t vmc_launch_sample_v3(const SysDev *d_sys, const int2 *d_work, int n_work,
+                                 int *d_work_ctr, uint2 key, int n_first, int n_samples,
+                                 int sweeps_between, int sample_base, int grid, size_t smem,
+                                 cudaStream_t st, long long *nl) {
+  k_sample<float, 3><<<grid, NT, smem, st>>>(d_sys, d_work, n_work, d_work_ctr, key, n_first,
+                                             n_samples, sweeps_between, sample_base);
+  ++*nl;
+  return cudaGetLastError();
+}
+#endif  // VMC_SWEEP_V3_ONLY
