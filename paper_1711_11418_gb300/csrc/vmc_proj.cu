@@ -52,6 +52,7 @@ struct PSmem {
   double *red;   // 2 x 16
   uint4 *rnd;    // NT Philox draws
   T *bc;         // broadcast scalars
+  int *map;      // NWARP x 2 x VMC_MAX_N: electron sites mapped by the warp's operation
 };
 
 __host__ __device__ inline size_t pal(size_t x) { return (x + 15) / 16 * 16; }
@@ -72,6 +73,7 @@ __host__ __device__ size_t proj_layout(int N, int Ns, int n_ops, unsigned char *
   const size_t o_red = take(sizeof(double) * 32);
   const size_t o_rnd = take(sizeof(uint4) * NT);
   const size_t o_bc = take(sizeof(T) * 4);
+  const size_t o_map = take(sizeof(int) * NWARP * 2 * VMC_MAX_N);
   if (sm) {
     sm->ele = (int *)(base + o_ele);
     sm->occ = (int *)(base + o_occ);
@@ -84,6 +86,7 @@ __host__ __device__ size_t proj_layout(int N, int Ns, int n_ops, unsigned char *
     sm->red = (double *)(base + o_red);
     sm->rnd = (uint4 *)(base + o_rnd);
     sm->bc = (T *)(base + o_bc);
+    sm->map = (int *)(base + o_map);
   }
   return off;
 }
@@ -625,28 +628,115 @@ __device__ void proj_measure(const SysDev &S, const PSmem<T> &sm, int w, int row
     const int sb = (sm.occ[b] >= 0) - (sm.occ[Ns + b] >= 0);
     ed += S.J_val[k] * 0.25 * (double)(sa * sb);
   }
-  // hopping: term k moves the spin-s electron on j = hop_j[k] to i = hop_i[k];
-  // one warp per (term, spin), the operations in turn
+  // hopping: term k moves the spin-s electron on j = hop_j[k] to i = hop_i[k].
+  // The (term, spin) pairs with a move are listed in order (q = 2k + s), then
+  // taken in chunks that fit the per-warp vector area: for every operation g
+  // in turn all warps of the CTA form their terms' ratios from the same M_g^-1
+  // (warp per term, lanes over the electrons), so M_g^-1 is read from DRAM
+  // once per chunk and then from L2, and each term's sum over g runs in g
+  // order in FP64 (its slot is owned by one warp).
   double eo = 0.0;
-  for (int q = warp; q < 2 * S.n_hop; q += NWARP) {
-    const int k = q >> 1, s = q & 1;
-    const int i = S.hop_i[k], j = S.hop_j[k];
-    const int e = sm.occ[s * Ns + j];
-    if (e < 0 || sm.occ[s * Ns + i] >= 0) continue;
-    if (S.local_spin && sm.occ[(1 - s) * Ns + i] >= 0) continue;
-    if (S.lsite && (S.lsite[i] | S.lsite[j])) continue;
-    double acc = 0.0;
-    for (int g = 0; g < Ng; ++g) {
-      const T rho = proj_hop_ratio(S, sm.ele, proj_minv<T>(S, w, g), g, e, i);
-      const signed char *sg = S.psgn + (size_t)g * Ns;
-      acc += sm.pi[g] * (double)((sg[i] * sg[j] < 0) ? -rho : rho);
+  {
+    const size_t vbytes = sizeof(T) * NWARP * PVEC * VMC_MAX_N;
+    const int cap = (int)(vbytes / (sizeof(double) + sizeof(int2)));
+    double *tacc = reinterpret_cast<double *>(sm.vec);
+    int2 *tdesc = reinterpret_cast<int2 *>(tacc + cap);
+    int *wcnt = reinterpret_cast<int *>(sm.red);   // per-warp counts of a listing round
+    const int nq = 2 * S.n_hop;
+    int q0 = 0;
+    while (q0 < nq) {
+      // ordered listing of the next pairs with a move, at most cap of them
+      int nt = 0;
+      __syncthreads();
+      while (q0 < nq) {
+        const int q = q0 + tid;
+        int e = -1;
+        if (q < nq) {
+          const int k = q >> 1, sp = q & 1;
+          const int i = S.hop_i[k], j = S.hop_j[k];
+          e = sm.occ[sp * Ns + j];
+          if (e >= 0 && sm.occ[sp * Ns + i] >= 0) e = -1;
+          if (e >= 0 && S.local_spin && sm.occ[(1 - sp) * Ns + i] >= 0) e = -1;
+          if (e >= 0 && S.lsite && (S.lsite[i] | S.lsite[j])) e = -1;
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, e >= 0);
+        if (lane == 0) wcnt[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int k = 0; k < NWARP; ++k) {
+          before += (k < warp) ? wcnt[k] : 0;
+          total += wcnt[k];
+        }
+        if (nt + total > cap) break;   // uniform: the round goes to the next chunk
+        if (e >= 0) tdesc[nt + before + __popc(bal & ((1u << lane) - 1))] = make_int2(q, e);
+        nt += total;
+        q0 += NT;
+        __syncthreads();   // wcnt is written again by the next round
+      }
+      for (int t = tid; t < nt; t += NT) tacc[t] = 0.0;
+      __syncthreads();
+      int *mup = sm.map + warp * 2 * VMC_MAX_N, *mdn = mup + VMC_MAX_N;
+      const T *F = ftab<T>(S);
+      const T *FT = fTtab<T>(S);
+      for (int g = 0; g < Ng; ++g) {
+        const T *Mg = proj_minv<T>(S, w, g);
+        const int *inv = S.pinv + (size_t)g * Ns;
+        const signed char *sg = S.psgn + (size_t)g * Ns;
+        const double pg = sm.pi[g];
+        // the electrons' sites mapped by g (g^-1 of each), once per operation
+        __syncwarp();
+        for (int l = lane; l < N; l += 32) {
+          mup[l] = inv[sm.ele[l]];
+          mdn[l] = inv[sm.ele[N + l]];
+        }
+        __syncwarp();
+        // two terms per iteration, their loads in flight together: an up
+        // electron e reads column e of M_g^-1 and f(g^-1 i, mapped down
+        // sites); a down electron m row m and f(mapped up sites, g^-1 i)
+        for (int t = warp; t < nt; t += 2 * NWARP) {
+          const int t2 = t + NWARP;
+          const bool two = t2 < nt;
+          const int2 d1 = tdesc[t], d2 = tdesc[two ? t2 : t];
+          const int i1 = S.hop_i[d1.x >> 1], i2 = S.hop_i[d2.x >> 1];
+          const bool up1 = d1.y < N, up2 = d2.y < N;
+          const T *tab1 = (up1 ? F : FT) + (size_t)inv[i1] * Ns;
+          const T *tab2 = (up2 ? F : FT) + (size_t)inv[i2] * Ns;
+          const int *mp1 = up1 ? mdn : mup, *mp2 = up2 ? mdn : mup;
+          const int st1 = up1 ? N : 1, st2 = up2 ? N : 1;
+          const T *m1 = Mg + (up1 ? d1.y : (d1.y - N) * N);
+          const T *m2 = Mg + (up2 ? d2.y : (d2.y - N) * N);
+          T s1 = (T)0, s2 = (T)0;
+          for (int l = lane; l < N; l += 32) {
+            const T a1 = tab1[mp1[l]], b1 = m1[(size_t)l * st1];
+            const T a2 = tab2[mp2[l]], b2 = m2[(size_t)l * st2];
+            s1 += a1 * b1;
+            s2 += a2 * b2;
+          }
+          s1 = warp_sum(s1);
+          s2 = warp_sum(s2);
+          if (lane == 0) {
+            const int j1 = S.hop_j[d1.x >> 1];
+            tacc[t] += pg * (double)((sg[i1] * sg[j1] < 0) ? -s1 : s1);
+            if (two) {
+              const int j2 = S.hop_j[d2.x >> 1];
+              tacc[t2] += pg * (double)((sg[i2] * sg[j2] < 0) ? -s2 : s2);
+            }
+          }
+        }
+      }
+      __syncthreads();
+      for (int t = tid; t < nt; t += NT) {
+        const int2 d = tdesc[t];
+        const int k = d.x >> 1, sp = d.x & 1;
+        const int i = S.hop_i[k], j = S.hop_j[k];
+        const T c = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, sp, j, i,
+                                              vtab<T>(S)[(size_t)j * Ns + i]));
+        eo += -S.hop_t[k] * tacc[t] * (double)c;
+      }
+      if (tid == 0) mc.meas_hop += nt;
     }
-    const T c = corr_factor<T>(corr_hop_v(sm.occ, sm.jf, sm.g, Ns, s, j, i,
-                                          vtab<T>(S)[(size_t)j * Ns + i]));
-    if (lane == 0) {
-      eo += -S.hop_t[k] * acc * (double)c;
-      mc.meas_hop++;
-    }
+    __syncthreads();   // the vector area is the exchange terms' scratch next
   }
   // Heisenberg exchange: J/2 (S+_a S-_b + S-_a S+_b) = -J/2 x (labelled swap ratio)
   for (int k = warp; k < S.n_J; k += NWARP) {
@@ -675,8 +765,12 @@ __device__ void proj_measure(const SysDev &S, const PSmem<T> &sm, int w, int row
   }
   const double etot = block_sum_d(ed + eo, sm.red, buf);
   if (tid == 0) S.E[(size_t)w * S.n_samples + row] = etot;
-  // O_k row (global accumulator)
-  T *O = (T *)S.O + ((size_t)w * S.n_samples + row) * S.ldO;
+  // O_k row: accumulated in the vector area (free again here) when it fits,
+  // else in the global row; then written to the global row.
+  T *Og = (T *)S.O + ((size_t)w * S.n_samples + row) * S.ldO;
+  const bool shared_o = (size_t)S.ldO * sizeof(T) <= sizeof(T) * NWARP * PVEC * VMC_MAX_N;
+  T *O = shared_o ? sm.vec : Og;
+  __syncthreads();   // the exchange terms' scratch is done with
   for (int k = tid; k < S.ldO; k += NT) O[k] = (T)0;
   for (int i = tid; i < Ns; i += NT) sm.mval[i] = (sm.occ[i] >= 0) + (sm.occ[Ns + i] >= 0) - 1;
   __syncthreads();
@@ -700,18 +794,34 @@ __device__ void proj_measure(const SysDev &S, const PSmem<T> &sm, int w, int row
     const T *Mg = proj_minv<T>(S, w, g);
     const int *inv = S.pinv + (size_t)g * Ns;
     const T pg = (T)sm.pi[g];
-    for (int n = 0; n < N; ++n) {
-      const int *frow = S.fcode + (size_t)inv[sm.ele[n]] * Ns;
-      for (int m = lane; m < N; m += 32) {
-        const int cd = frow[inv[sm.ele[N + m]]];
-        if (cd >= 0) {
-          const T v = pg * Mg[(size_t)m * N + n];
-          atomicAdd(O + base + (cd >> 1), (cd & 1) ? -v : v);
+    // rows m of M_g^-1 in turn (coalesced), lanes over the up electrons n
+    int rn[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int n = lane + 32 * u;
+      rn[u] = (n < N) ? inv[sm.ele[n]] * Ns : 0;
+    }
+    for (int m = 0; m < N; ++m) {
+      const int cm = inv[sm.ele[N + m]];
+      const T *mrow = Mg + (size_t)m * N;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int n = lane + 32 * u;
+        if (n < N) {
+          const int cd = S.fcode[(size_t)rn[u] + cm];
+          if (cd >= 0) {
+            const T v = pg * mrow[n];
+            atomicAdd(O + base + (cd >> 1), (cd & 1) ? -v : v);
+          }
         }
       }
     }
   }
   __syncthreads();
+  if (shared_o) {
+    for (int k = tid; k < S.ldO; k += NT) Og[k] = O[k];
+    __syncthreads();
+  }
 }
 
 template <typename T>
