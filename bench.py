@@ -275,12 +275,16 @@ def projected_sampling(vmc, torch, stream, inputs, W=608, calls=2):
     """Momentum projection at N_g = Ns on the 16x16 workload (mixed form):
     all 256 translations at K = 0 (Sec. 3.2.2, Eq. momP; App. A signs), one
     M_g^-1 per translation per walker in HBM (12.8 MB per walker; 608
-    walkers fill the kernel's four CTAs per SM).  Timed:
-    vmc_sample(0, 1, 1) calls (one sweep and one measurement per walker, with
-    the periodic rebuilds of every M_g^-1), CUDA events on the stream.
-    Roofline of the projected sweep kernel on its algorithmic bytes: every
-    proposal reads one column or row of each M_g^-1 (N_g N 4 B), every accepted
-    move reads and writes all of them (N_g 2 N^2 4 B)."""
+    walkers fill the kernel's four CTAs per SM).  Timed with CUDA events on
+    the stream: vmc_sample(0, 1, 1) calls (one sweep and one measurement per
+    walker, with the periodic rebuilds of every M_g^-1); then, per kernel
+    launch, one sweep-only and one measurement-only call.
+    Roofline of the projected sweep on its algorithmic bytes, what the fast
+    updates must move with every M_g^-1 in HBM (per operation g, 4-byte
+    words): a tested hop reads a row or column (N); a tested exchange forms
+    R^T M_g^-1 and reads row m (N^2 + 2N); an accepted hop reads M_g^-1 for
+    R^T M_g^-1 or M_g^-1 C, then reads and writes it in the update (3 N^2); an
+    accepted exchange forms both products (4 N^2 with the update)."""
     prob = inputs.square16_hubbard()
     perm, sign = inputs.translation_ops(prob.lat)
     G, N = perm.shape[0], prob.N
@@ -300,23 +304,37 @@ def projected_sampling(vmc, torch, stream, inputs, W=608, calls=2):
     ms = e0.elapsed_time(e1)
     kt = ctx.kernel_times()
     s1 = ctx.measure()
+    ctx.sample(1, 0, 0)                     # sweep only
+    kt_s = ctx.kernel_times()
+    s2 = ctx.measure()
+    ctx.sample(0, 1, 0)                     # measurement only
+    kt_m = ctx.kernel_times()
     grid, per_sm, smem = ctx.sweep_launch()
     ctx.close()
     props = s1["n_proposals"] - s0["n_proposals"]
     acc = s1["n_accepted"] - s0["n_accepted"]
-    sweep_ms, sweep_n = kt["sweep"]
-    b = 4.0 * G * N * props + 8.0 * G * N * N * acc
+    d = {k: s2[k] - s1[k] for k in ("n_hop_tested", "n_exchange_tested", "n_hop_accepted",
+                                    "n_exchange_accepted", "n_proposals")}
+    sweep_ms = kt_s["sweep"][0] / max(kt_s["sweep"][1], 1)
+    b = 4.0 * G * (N * d["n_hop_tested"] + (N * N + 2 * N) * d["n_exchange_tested"]
+                   + 3 * N * N * d["n_hop_accepted"] + 4 * N * N * d["n_exchange_accepted"])
     hbm, src = hbm_peak_gbs()
     ach = b / (sweep_ms * 1e-3) / 1e9
     return {"walkers": W, "operations": G, "characters": "K = 0", "calls": calls,
             "ms_per_call": ms / calls, "proposals_per_s": props / (ms * 1e-3),
-            "sweep_kernel_ms_per_launch": sweep_ms / max(sweep_n, 1),
+            "sweep_kernel_ms_per_launch": kt["sweep"][0] / max(kt["sweep"][1], 1),
+            "sweep_only_ms": sweep_ms,
+            "measurement_only_ms": kt_m["sweep"][0] / max(kt_m["sweep"][1], 1),
             "rebuild_ms_per_call": kt["init"][0] / calls,
             "acceptance": acc / max(props, 1), "sweep_launch": {"grid": grid, "ctas_per_sm": per_sm,
                                                                 "smem_bytes": smem},
+            "sweep_counts": d,
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                         "frac": ach / hbm, "traffic": None, "kernel": "k_proj_sample<float>",
-                         "bytes_rule": "N_g N 4 B per proposal + N_g 2 N^2 4 B per accepted move",
+                         "frac": ach / hbm, "traffic": None,
+                         "kernel": "k_proj_sample<float> (sweep-only launch)",
+                         "algorithmic_bytes_per_launch": b,
+                         "bytes_rule": "4 N_g (N hops tested + (N^2 + 2N) exchanges tested + "
+                                       "3 N^2 hops accepted + 4 N^2 exchanges accepted)",
                          "peak_source": src}}
 
 
