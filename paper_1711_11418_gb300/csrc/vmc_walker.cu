@@ -2392,87 +2392,122 @@ __global__ void __launch_bounds__(NT) k_corr(const SysDev *systems, int sys, dou
     int gb[CORR_G], gm[CORR_G];
 #pragma unroll
     for (int q = 0; q < CORR_G; ++q) gb[q] = gm[q] = 0;
-    for (int b = 0; b < Ns; ++b) {
-      T *gu = sm.vec + (size_t)(1 + ng) * VMC_MAX_N;   // G_up[b, k], k < N
-      if (tid < N) fb[tid] = F[(size_t)b * Ns + sm.ele[N + tid]];
-      __syncthreads();
+    // G_up[b, :] = f(b, r_dn)^T M^-1 for four sites b at a time: the rows
+    // f(b, r_l,dn) in vector slots 0, 5, 6, 7, thread k the column k, one
+    // shared load of M^-1 per four multiply-adds; the rows of down-occupied
+    // sites go to the group's slots 1..CORR_G.
+    T *fbs[4] = {fb, sm.vec + 5 * VMC_MAX_N, sm.vec + 6 * VMC_MAX_N, sm.vec + 7 * VMC_MAX_N};
+    for (int b0 = 0; b0 < Ns; b0 += 4) {
+      const int nbk = (Ns - b0 < 4) ? Ns - b0 : 4;
       if (tid < N) {
-        T s = (T)0;
-        for (int l = 0; l < N; ++l) s += fb[l] * sm.minv[l * ldm + tid];
-        gu[tid] = s;
+        const int el = sm.ele[N + tid];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          fbs[u][tid] = (u < nbk) ? F[(size_t)(b0 + u) * Ns + el] : (T)0;
       }
       __syncthreads();
-      const bool b_up = sm.occ[b] >= 0, b_dn = sm.occ[Ns + b] >= 0;
-      // kind 0 at (b, r_k,up)
-      if (tid < N && !b_up && !(S.local_spin && b_dn)) {
-        const int j = sm.ele[tid];
-        const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 0, j, b));
-        atomicAdd(&P0[(size_t)b * Ns + j], (double)(gu[tid] * c));
-      }
-      if (b_dn) {
+      T g4[4] = {(T)0, (T)0, (T)0, (T)0};
+      if (tid < N) {
+        int l = 0;
+        for (; l + 4 <= N; l += 4) {
+          const T m0 = sm.minv[l * ldm + tid], m1 = sm.minv[(l + 1) * ldm + tid];
+          const T m2 = sm.minv[(l + 2) * ldm + tid], m3 = sm.minv[(l + 3) * ldm + tid];
 #pragma unroll
-        for (int q = 0; q < CORR_G; ++q)
-          if (q == ng) {
-            gb[q] = b;
-            gm[q] = sm.occ[Ns + b] - N;
-          }
-        ++ng;
-      }
-      if (ng == CORR_G || (b == Ns - 1 && ng > 0)) {
-        // G_dn[a, m] and T[b, a] of the group's sites, two sites a per
-        // thread: each f(r_k,up, a) feeds 2 x CORR_G pairs of products.
-        const T *Bq[CORR_G], *Gq[CORR_G];
-#pragma unroll
-        for (int q = 0; q < CORR_G; ++q) {
-          Bq[q] = sm.minv + (size_t)gm[q] * ldm;       // unused slots: a valid row
-          Gq[q] = sm.vec + (size_t)(1 + q) * VMC_MAX_N;
-        }
-        for (int a0 = tid; a0 < Ns; a0 += 2 * NT) {
-          const int a1 = a0 + NT < Ns ? a0 + NT : a0;
-          T d0[CORR_G], t0[CORR_G], d1[CORR_G], t1[CORR_G];
-#pragma unroll
-          for (int q = 0; q < CORR_G; ++q) d0[q] = t0[q] = d1[q] = t1[q] = (T)0;
-          for (int k = 0; k < N; ++k) {
-            const T *Fk = F + (size_t)sm.ele[k] * Ns;
-            const T f0 = Fk[a0], f1 = Fk[a1];
-#pragma unroll
-            for (int q = 0; q < CORR_G; ++q) {
-              const T bk = Bq[q][k], gk = Gq[q][k];
-              d0[q] += bk * f0;
-              t0[q] += gk * f0;
-              d1[q] += bk * f1;
-              t1[q] += gk * f1;
-            }
-          }
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int a = h ? a1 : a0;
-            if (h && a1 == a0) break;
-            const bool a_up = sm.occ[a] >= 0, a_dn = sm.occ[Ns + a] >= 0;
-#pragma unroll
-            for (int q = 0; q < CORR_G; ++q) {
-              if (q >= ng) break;
-              const int bq = gb[q];
-              if (a == bq) continue;
-              const T accD = h ? d1[q] : d0[q], accT = h ? t1[q] : t0[q];
-              // kind 1 at (a, bq): down electron gm[q] hops bq -> a
-              if (!a_dn && !(S.local_spin && a_up)) {
-                const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, bq, a));
-                atomicAdd(&P1[(size_t)a * Ns + bq], (double)(accD * c));
-              }
-              // kind 4 at (bq, a): spin swap with up electron n on a
-              if (a_up && !a_dn && sm.occ[bq] < 0) {
-                const int n = sm.occ[a];
-                const T r = Gq[q][n] * accD - Bq[q][n] * (accT - F[(size_t)bq * Ns + a]);
-                atomicAdd(&P4[(size_t)bq * Ns + a], -(double)r);
-              }
-            }
+          for (int u = 0; u < 4; ++u) {
+            T x0, x1, x2, x3;
+            ld4(fbs[u] + l, x0, x1, x2, x3);
+            g4[u] += x0 * m0;
+            g4[u] += x1 * m1;
+            g4[u] += x2 * m2;
+            g4[u] += x3 * m3;
           }
         }
-        ng = 0;
+        for (; l < N; ++l) {
+          const T m0 = sm.minv[l * ldm + tid];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) g4[u] += fbs[u][l] * m0;
+        }
       }
-      __syncthreads();
+      __syncthreads();   // the block's rows are read; slots 0, 5..7 free
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u >= nbk) break;
+        const int b = b0 + u;
+        const bool b_up = sm.occ[b] >= 0, b_dn = sm.occ[Ns + b] >= 0;
+        // kind 0 at (b, r_k,up)
+        if (tid < N && !b_up && !(S.local_spin && b_dn)) {
+          const int j = sm.ele[tid];
+          const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 0, j, b));
+          atomicAdd(&P0[(size_t)b * Ns + j], (double)(g4[u] * c));
+        }
+        if (b_dn) {
+          if (tid < N) sm.vec[(size_t)(1 + ng) * VMC_MAX_N + tid] = g4[u];
+  #pragma unroll
+          for (int q = 0; q < CORR_G; ++q)
+            if (q == ng) {
+              gb[q] = b;
+              gm[q] = sm.occ[Ns + b] - N;
+            }
+          ++ng;
+        }
+        if (ng == CORR_G || (b == Ns - 1 && ng > 0)) {
+          __syncthreads();   // the group's G_up rows are in place
+          // G_dn[a, m] and T[b, a] of the group's sites, two sites a per
+          // thread: each f(r_k,up, a) feeds 2 x CORR_G pairs of products.
+          const T *Bq[CORR_G], *Gq[CORR_G];
+  #pragma unroll
+          for (int q = 0; q < CORR_G; ++q) {
+            Bq[q] = sm.minv + (size_t)gm[q] * ldm;       // unused slots: a valid row
+            Gq[q] = sm.vec + (size_t)(1 + q) * VMC_MAX_N;
+          }
+          for (int a0 = tid; a0 < Ns; a0 += 2 * NT) {
+            const int a1 = a0 + NT < Ns ? a0 + NT : a0;
+            T d0[CORR_G], t0[CORR_G], d1[CORR_G], t1[CORR_G];
+  #pragma unroll
+            for (int q = 0; q < CORR_G; ++q) d0[q] = t0[q] = d1[q] = t1[q] = (T)0;
+            for (int k = 0; k < N; ++k) {
+              const T *Fk = F + (size_t)sm.ele[k] * Ns;
+              const T f0 = Fk[a0], f1 = Fk[a1];
+  #pragma unroll
+              for (int q = 0; q < CORR_G; ++q) {
+                const T bk = Bq[q][k], gk = Gq[q][k];
+                d0[q] += bk * f0;
+                t0[q] += gk * f0;
+                d1[q] += bk * f1;
+                t1[q] += gk * f1;
+              }
+            }
+  #pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int a = h ? a1 : a0;
+              if (h && a1 == a0) break;
+              const bool a_up = sm.occ[a] >= 0, a_dn = sm.occ[Ns + a] >= 0;
+  #pragma unroll
+              for (int q = 0; q < CORR_G; ++q) {
+                if (q >= ng) break;
+                const int bq = gb[q];
+                if (a == bq) continue;
+                const T accD = h ? d1[q] : d0[q], accT = h ? t1[q] : t0[q];
+                // kind 1 at (a, bq): down electron gm[q] hops bq -> a
+                if (!a_dn && !(S.local_spin && a_up)) {
+                  const T c = corr_factor<T>(corr_hop<T>(S, sm.occ, sm.jf, 1, bq, a));
+                  atomicAdd(&P1[(size_t)a * Ns + bq], (double)(accD * c));
+                }
+                // kind 4 at (bq, a): spin swap with up electron n on a
+                if (a_up && !a_dn && sm.occ[bq] < 0) {
+                  const int n = sm.occ[a];
+                  const T r = Gq[q][n] * accD - Bq[q][n] * (accT - F[(size_t)bq * Ns + a]);
+                  atomicAdd(&P4[(size_t)bq * Ns + a], -(double)r);
+                }
+              }
+            }
+          }
+          ng = 0;
+          __syncthreads();   // the group's slots are written again
+        }
+      }
     }
+    __syncthreads();
   }
 }
 
