@@ -166,3 +166,30 @@ def test_projection_rejections(vmc):
             ctx.set_delay(4)
         ctx.set_projection(np.zeros((0, p.Ns)), np.zeros((0, p.Ns)), np.zeros(0))
         ctx.measure_corr()                         # unprojected again
+
+
+@pytest.mark.parametrize("precision,rtol", [("MIXED", 1e-5), ("FP64", 1e-10)])
+def test_identity_projection_equals_plain_state_full_size(vmc, precision, rtol):
+    """Projection onto the identity alone (N_g = 1, weight 1) is the plain
+    state.  On the 16x16 lattice with next-nearest hops (about 1000 hop
+    terms with a move per configuration: two chunks of the mixed form's
+    term listing) the projected measurement's E_loc and O_k equal the plain
+    measurement's on the same configurations."""
+    prec = getattr(vmc, precision)
+    p = I.make_problem("s16t2", I.square(16, 16, -1, -1), 224, U=8.0, t2=-0.3, sub=(2, 2),
+                       jastrow="distance", f_init="none", noise=0.5, seed=3)
+    p.params[:p.n_g + p.n_v] = np.random.default_rng(4).uniform(-0.3, 0.1, p.n_g + p.n_v)
+    W = 32
+    cfg = I.initial_configs(p.Ns, p.Ne, W, False, 77)
+    res = []
+    for proj in (False, True):
+        with vmc.Context(p, W, seed=5, precision=prec, max_samples=1) as ctx:
+            if proj:
+                ctx.set_projection(np.arange(p.Ns, dtype=np.int32)[None, :],
+                                   np.ones((1, p.Ns), np.int8), np.ones(1))
+            ctx.set_configs(cfg)
+            ctx.sample(0, 1, 0)
+            res.append(ctx.get_samples())
+    (E0, O0), (E1, O1) = res
+    assert np.allclose(E1, E0, rtol=rtol, atol=rtol * np.max(np.abs(E0)))
+    assert np.allclose(O1, O0, rtol=rtol, atol=rtol * max(1.0, np.max(np.abs(O0))))
