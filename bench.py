@@ -44,11 +44,11 @@ FP64_PEAK_TFLOPS = SMS * FP64_UNITS * 2 * SM_MAX_MHZ * 1e6 / 1e12
 # metrics) of the current kernels at 4096 walkers
 # (profiles/dram_k_sample_k_init_hubbard16x16_w4096.md): a sweep-only launch
 # of k_sample<float> and the full rebuild launch of k_init<float>.
-TRAFFIC_SWEEP_ONLY_4096 = 433.96e6 + 368.55e6
-TRAFFIC_INIT_4096 = 6.44e6 + 366.92e6
+TRAFFIC_SWEEP_ONLY_4096 = 434.15e6 + 368.07e6
+TRAFFIC_INIT_4096 = 5.54e6 + 366.87e6
 # k_corr<float> (pair correlations), DRAM read + write per launch at 4096
 # walkers (profiles/k_corr_float_hubbard16x16_w4096.md).
-TRAFFIC_CORR_4096 = 229.7047e6
+TRAFFIC_CORR_4096 = 230.7e6
 
 
 def hbm_peak_gbs():
