@@ -751,7 +751,8 @@ def run_ours(args):
             hp = torch.empty(prob.Np, dtype=torch.float64, pin_memory=True).numpy()
             hp[:] = params
             t0 = time.perf_counter()
-            p0 = ctx.measure()["n_proposals"]
+            m0 = ctx.measure()
+            p0 = m0["n_proposals"]
             for _ in range(args.steps):
                 ctx.set_params(hp)
                 ctx.sample(0, args.samples, 1)
@@ -760,10 +761,15 @@ def run_ours(args):
                 _ = ctx.measure()["energy"]
             torch.cuda.synchronize()
             dt = reduce_over_ranks(torch, time.perf_counter() - t0, "max")
-            props = reduce_over_ranks(torch, ctx.measure()["n_proposals"] - p0, "sum")
+            m1 = ctx.measure()
+            props = reduce_over_ranks(torch, m1["n_proposals"] - p0, "sum")
+            # run after the timed region, further along the SR trajectory:
+            # its acceptance (accepted moves are the costly part) beside it
             e2e = {"value": props / dt, "unit": "proposals/s",
                    "h2d_bytes_per_step": 8 * prob.Np,
-                   "d2h_bytes_per_step": 8 * prob.Np + 8 * args.walkers * args.samples + 64}
+                   "d2h_bytes_per_step": 8 * prob.Np + 8 * args.walkers * args.samples + 64,
+                   "ms_per_step": 1e3 * dt / args.steps,
+                   "acceptance": (m1["n_accepted"] - m0["n_accepted"]) / max(m1["n_proposals"] - p0, 1)}
         # Pair correlations of the walkers' configurations (measurement mode;
         # not part of the optimisation step timed above): device time of the
         # whole measurement and of its ratio kernel, CUDA events on the stream.
