@@ -449,7 +449,9 @@ int vmc_tune_delay(vmc_ctx *ctx, int32_t sweeps, const int32_t *cand, int32_t n_
  * are formed again against the updated state.  The chain (configurations,
  * counters, samples) is the one b = 1 gives, up to the ratios' summation
  * order.  Applies while the MLP factor and delayed updates are off (the
- * sweep makes proposals one at a time otherwise).  Default 1.  What pays
+ * sweep makes proposals one at a time otherwise) and not to a projected
+ * context's sweep (vmc_tune_proposal_batch returns VMC_EINVAL there).
+ * Default 1.  What pays
  * depends on the workload: where most proposals are tested exchanges (spin
  * models) the shared pass over M^-1 wins; where the FP64 pipe or the
  * inverse updates bound the sweep, the proposals formed past an accepted one

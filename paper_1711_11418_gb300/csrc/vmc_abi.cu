@@ -1625,7 +1625,7 @@ int32_t vmc_get_proposal_batch(vmc_ctx *c) { return c ? c->spec_b : -1; }
 int vmc_tune_proposal_batch(vmc_ctx *c, int32_t sweeps, const int32_t *cand, int32_t n_cand,
                             int32_t *chosen, double *ms) {
   static const int32_t def[] = {1, 2, 4, 8};
-  if (!c || sweeps < 1 || (cand && n_cand < 1) || !chosen) return VMC_EINVAL;
+  if (!c || sweeps < 1 || (cand && n_cand < 1) || !chosen || projected(c)) return VMC_EINVAL;
   if (!cand) {
     cand = def;
     n_cand = 4;

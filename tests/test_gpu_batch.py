@@ -138,3 +138,13 @@ def test_batched_chain_full_size_spin_model(vmc):
     same = np.all(a[0] == b[0], axis=1)
     assert same.mean() >= 0.9
     assert np.allclose(a[2][same], b[2][same], rtol=1e-6, atol=1e-6)
+
+
+def test_tuner_refuses_projected_context(vmc):
+    """The projected sweep makes its proposals one at a time: nothing to tune."""
+    p = I.ring8_hubbard()
+    with vmc.Context(p, 4, seed=3, max_samples=1) as ctx:
+        perm = np.array([np.roll(np.arange(p.Ns), k) for k in range(2)], np.int32)
+        ctx.set_projection(perm, np.ones_like(perm, dtype=np.int8), np.full(2, 0.5))
+        with pytest.raises(vmc.VmcError):
+            ctx.tune_proposal_batch(sweeps=1)
